@@ -1,0 +1,108 @@
+"""The benchmark workloads as seeded synthetic problems.
+
+Each config mirrors one of the five workload descriptions of this project
+(2D sine-perturbed Q2 16x16 S4; 2D random-smooth Q3 128x128 S8; 3D twisted Q2 32^3 S8;
+a batch of 256 uneven 2D problems; 3D random-smooth Q2 48^3 S12).  `n` overrides
+the grid size so that the same recipe yields small test cases.
+"""
+from dataclasses import dataclass
+import numpy as np
+from .mesh import structured_mesh, disp_sine_2d, disp_random_smooth, disp_twist, disp_random_smooth_3d
+from .quadrature import level_symmetric
+
+
+@dataclass
+class Problem:
+    name: str
+    mesh: object
+    p: int
+    omega: np.ndarray        # [M][3]
+    w: np.ndarray            # [M]
+    sigma_t: np.ndarray      # [n_elem]
+    sigma_s: np.ndarray      # [n_elem]
+    q: np.ndarray            # [n_elem][N] nodal isotropic source
+    q_dir: np.ndarray = None     # [M][n_elem][N] nodal direction-dependent source, or None
+    psi_inc: np.ndarray = None   # [M][n_bdr_faces][N_f] nodal incident flux, or None (vacuum)
+    sn_order: int = 0
+
+    @property
+    def dim(self):
+        return self.mesh.dim
+
+    @property
+    def n_dofs(self):
+        return (self.p + 1) ** self.mesh.dim
+
+
+CONFIGS = {
+    "2d_sine_q2_p1_s4": dict(dim=2, n=16, r=2, p=1, sn=4),
+    "2d_smooth_q3_p3_s8": dict(dim=2, n=128, r=3, p=3, sn=8),
+    "3d_twist_q2_p2_s8": dict(dim=3, n=32, r=2, p=2, sn=8),
+    "3d_smooth_q2_p2_s12": dict(dim=3, n=48, r=2, p=2, sn=12),
+}
+
+
+def make_config(name, n=None, sn=None, p=None, reorient_seed=None):
+    """Build one workload (optionally at a reduced grid size n)."""
+    c = dict(CONFIGS[name])
+    if n is not None:
+        c["n"] = n
+    if sn is not None:
+        c["sn"] = sn
+    if p is not None:
+        c["p"] = p
+    dim, n, r, p_, sn_ = c["dim"], c["n"], c["r"], c["p"], c["sn"]
+    h = 1.0 / n
+    if name == "2d_sine_q2_p1_s4":
+        mesh = structured_mesh((n, n), r, disp_sine_2d(0.05))
+        ne = mesh.n_elem
+        st = np.ones(ne)
+        ss = 0.5 * np.ones(ne)
+    elif name == "2d_smooth_q3_p3_s8":
+        mesh = structured_mesh((n, n), r, disp_random_smooth(h, seed=11))
+        ne = mesh.n_elem
+        rng = np.random.default_rng(12)
+        st = rng.uniform(0.5, 5.0, size=ne)
+        ss = 0.9 * st
+    elif name == "3d_twist_q2_p2_s8":
+        mesh = structured_mesh((n, n, n), r, disp_twist(np.pi / 3))
+        ne = mesh.n_elem
+        st = np.ones(ne)
+        ss = 0.8 * np.ones(ne)
+    elif name == "3d_smooth_q2_p2_s12":
+        mesh = structured_mesh((n, n, n), r, disp_random_smooth_3d(h, seed=41))
+        ne = mesh.n_elem
+        rng = np.random.default_rng(42)
+        st = np.exp(rng.normal(0.0, 1.0, size=ne))
+        ss = 0.99 * st
+    else:
+        raise KeyError(name)
+    if reorient_seed is not None:
+        from .mesh import reorient_elements
+        mesh = reorient_elements(mesh, reorient_seed)
+    om, w = level_symmetric(sn_, dim)
+    N = (p_ + 1) ** dim
+    q = np.ones((mesh.n_elem, N))
+    return Problem(name=name, mesh=mesh, p=p_, omega=om, w=w, sigma_t=st, sigma_s=ss, q=q, sn_order=sn_)
+
+
+def batch_problems(count=256, seed=31, nmin=8, nmax=64):
+    """Many independent uneven 2D problems: n ~ U{nmin..nmax}, p ~ U{1,2,3}, r ~ U{2,3},
+    S_N ~ U{4,6,8}, sigma_t ~ U[0.1,10] per element, scattering ratio c ~ U[0.5,0.95] per problem.
+    Problem i draws from numpy PCG64 substream (seed, i)."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng([seed, i])
+        n = int(rng.integers(nmin, nmax + 1))
+        p = int(rng.integers(1, 4))
+        r = int(rng.integers(2, 4))
+        sn = int(rng.choice([4, 6, 8]))
+        c = float(rng.uniform(0.5, 0.95))
+        mseed = int(rng.integers(0, 2**31 - 1))
+        mesh = structured_mesh((n, n), r, disp_random_smooth(1.0 / n, seed=mseed))
+        st = rng.uniform(0.1, 10.0, size=mesh.n_elem)
+        om, w = level_symmetric(sn, 2)
+        N = (p + 1) ** 2
+        out.append(Problem(name=f"batch{i}", mesh=mesh, p=p, omega=om, w=w, sigma_t=st, sigma_s=c * st,
+                           q=np.ones((mesh.n_elem, N)), sn_order=sn))
+    return out

@@ -1,0 +1,301 @@
+"""Structured curved-mesh generators with explicit, general connectivity.
+
+The generators only place control points and build topology: a Cartesian grid of
+Q_r elements whose geometry nodes are displaced by a smooth field.  Connectivity
+(neighbour, neighbour face, orientation) is derived from global node ids, so an
+element's local numbering may be any rotation of the reference element.
+"""
+from dataclasses import dataclass, field
+import itertools
+import numpy as np
+
+
+@dataclass
+class Mesh:
+    dim: int
+    r: int                      # geometry order (Q_r)
+    ctrl: np.ndarray            # [n_elem][(r+1)^dim][dim] float64 control points
+    face_nbr: np.ndarray        # [n_elem][2 dim] int64, -1 = domain boundary
+    nbr_face: np.ndarray        # [n_elem][2 dim] int32
+    orient: np.ndarray          # [n_elem][2 dim] int32 (see package docstring)
+    nodes: np.ndarray = field(repr=False, default=None)       # [n_nodes][dim] global node positions
+    elem_nodes: np.ndarray = field(repr=False, default=None)  # [n_elem][(r+1)^dim] global node ids
+    shape: tuple = ()           # logical grid size (nx, ny[, nz])
+
+    @property
+    def n_elem(self):
+        return self.ctrl.shape[0]
+
+
+def _local_index(idx, r):
+    m = 0
+    for k in reversed(range(len(idx))):
+        m = m * (r + 1) + idx[k]
+    return m
+
+
+def structured_mesh(shape, r, disp=None, domain=None, fast_connectivity=True):
+    """Cartesian grid of Q_r elements on [0,1]^dim (or `domain` = [(lo,hi),...]).
+
+    shape : (nx, ny) or (nx, ny, nz) elements.  Element index e = i + nx j (+ nx ny k).
+    disp  : callable X[n,dim] -> displacement[n,dim] applied to every geometry node, or None.
+    fast_connectivity : use the grid's own neighbour structure (all orientation codes 0)
+                        instead of matching faces by global node ids.
+    """
+    dim = len(shape)
+    if domain is None:
+        domain = [(0.0, 1.0)] * dim
+    counts = [s * r + 1 for s in shape]
+    axes = [np.array([lo + (hi - lo) * g / (s * r) for g in range(c)], dtype=np.float64)
+            for (lo, hi), s, c in zip(domain, shape, counts)]
+    grids = np.meshgrid(*axes, indexing="ij")
+    # global node id: g0 + c0 g1 + c0 c1 g2
+    X = np.stack([g.transpose(tuple(reversed(range(dim)))).reshape(-1) for g in grids], axis=1)
+    if disp is not None:
+        X = X + disp(X.copy())
+    n_elem = int(np.prod(shape))
+    strides = [1]
+    for c in counts[:-1]:
+        strides.append(strides[-1] * c)
+    # element grid indices (i, j[, k]) in element order, local node offsets (a, b[, c]) in local order
+    eg = np.stack(np.meshgrid(*[np.arange(s) for s in reversed(shape)], indexing="ij"), -1)
+    eg = eg.reshape(-1, dim)[:, ::-1]
+    lg = np.stack(np.meshgrid(*[np.arange(r + 1)] * dim, indexing="ij"), -1).reshape(-1, dim)[:, ::-1]
+    gidx = eg[:, None, :] * r + lg[None, :, :]
+    elem_nodes = (gidx * np.array(strides)[None, None, :]).sum(-1).astype(np.int64)
+    if fast_connectivity:
+        ctrl = np.ascontiguousarray(X[elem_nodes])
+        face_nbr, nbr_face, orient = _structured_connectivity(shape)
+        return Mesh(dim=dim, r=r, ctrl=ctrl, face_nbr=face_nbr, nbr_face=nbr_face, orient=orient,
+                    nodes=X, elem_nodes=elem_nodes, shape=tuple(shape))
+    return _finish(dim, r, X, elem_nodes, tuple(shape))
+
+
+def _structured_connectivity(shape):
+    dim = len(shape)
+    n_elem = int(np.prod(shape))
+    e = np.arange(n_elem, dtype=np.int64)
+    idx = []
+    rem = e.copy()
+    for s in shape:
+        idx.append(rem % s)
+        rem = rem // s
+    stride = 1
+    face_nbr = -np.ones((n_elem, 2 * dim), dtype=np.int64)
+    nbr_face = -np.ones((n_elem, 2 * dim), dtype=np.int32)
+    for a, s in enumerate(shape):
+        lo = idx[a] > 0
+        hi = idx[a] < s - 1
+        face_nbr[lo, 2 * a] = e[lo] - stride
+        nbr_face[lo, 2 * a] = 2 * a + 1
+        face_nbr[hi, 2 * a + 1] = e[hi] + stride
+        nbr_face[hi, 2 * a + 1] = 2 * a
+        stride *= s
+    return face_nbr, nbr_face, np.zeros((n_elem, 2 * dim), dtype=np.int32)
+
+
+def _finish(dim, r, X, elem_nodes, shape):
+    ctrl = np.ascontiguousarray(X[elem_nodes])
+    face_nbr, nbr_face, orient = connectivity_from_nodes(dim, r, elem_nodes)
+    return Mesh(dim=dim, r=r, ctrl=ctrl, face_nbr=face_nbr, nbr_face=nbr_face, orient=orient,
+                nodes=X, elem_nodes=elem_nodes, shape=shape)
+
+
+def _face_node_grid(dim, r, f):
+    """Global-local node indices of face f as an array indexed [s1][s0] (2D faces: [s0])."""
+    axis, side = f // 2, f % 2
+    others = [a for a in range(dim) if a != axis]
+    if dim == 2:
+        out = np.zeros(r + 1, dtype=np.int64)
+        for i in range(r + 1):
+            loc = [0, 0]
+            loc[axis] = side * r
+            loc[others[0]] = i
+            out[i] = _local_index(loc, r)
+        return out
+    out = np.zeros((r + 1, r + 1), dtype=np.int64)
+    for j in range(r + 1):
+        for i in range(r + 1):
+            loc = [0, 0, 0]
+            loc[axis] = side * r
+            loc[others[0]] = i
+            loc[others[1]] = j
+            out[j, i] = _local_index(loc, r)
+    return out
+
+
+def orient_apply(code, i, j, n):
+    """Map face-node grid indices (i along s0, j along s1) of one side to the other side's.
+
+    n = number of nodes per face axis minus one (equispaced/symmetric node sets).
+    """
+    u0, u1 = (j, i) if code & 4 else (i, j)
+    t0 = n - u0 if code & 1 else u0
+    t1 = n - u1 if code & 2 else u1
+    return t0, t1
+
+
+def connectivity_from_nodes(dim, r, elem_nodes):
+    n_elem = elem_nodes.shape[0]
+    nf = 2 * dim
+    face_nbr = -np.ones((n_elem, nf), dtype=np.int64)
+    nbr_face = -np.ones((n_elem, nf), dtype=np.int32)
+    orient = np.zeros((n_elem, nf), dtype=np.int32)
+    grids = [_face_node_grid(dim, r, f) for f in range(nf)]
+    table = {}
+    for e in range(n_elem):
+        for f in range(nf):
+            ids = elem_nodes[e][grids[f]]
+            key = frozenset(ids.reshape(-1).tolist())
+            table.setdefault(key, []).append((e, f))
+    codes = [0, 1] if dim == 2 else list(range(8))
+    for key, lst in table.items():
+        if len(lst) == 1:
+            continue
+        if len(lst) != 2:
+            raise ValueError("non-conforming mesh: a face is shared by more than two elements")
+        (e, f), (e2, f2) = lst
+        for (a, fa, b, fb) in ((e, f, e2, f2), (e2, f2, e, f)):
+            ga = elem_nodes[a][grids[fa]]
+            gb = elem_nodes[b][grids[fb]]
+            found = None
+            for c in codes:
+                ok = True
+                if dim == 2:
+                    for i in range(r + 1):
+                        t0, _ = orient_apply(c, i, 0, r)
+                        if ga[i] != gb[t0]:
+                            ok = False
+                            break
+                else:
+                    for j in range(r + 1):
+                        for i in range(r + 1):
+                            t0, t1 = orient_apply(c, i, j, r)
+                            if ga[j, i] != gb[t1, t0]:
+                                ok = False
+                                break
+                        if not ok:
+                            break
+                if ok:
+                    found = c
+                    break
+            if found is None:
+                raise ValueError("could not match face orientation")
+            face_nbr[a, fa] = b
+            nbr_face[a, fa] = fb
+            orient[a, fa] = found
+    return face_nbr, nbr_face, orient
+
+
+def _rotations(dim):
+    """Orientation-preserving symmetries of [0,1]^dim as (perm, flips):
+    new_xi[k] = 1 - old_xi[perm[k]] if flips[k] else old_xi[perm[k]]."""
+    out = []
+    for perm in itertools.permutations(range(dim)):
+        psign = np.linalg.det(np.eye(dim)[list(perm)])
+        for flips in itertools.product((0, 1), repeat=dim):
+            s = psign * np.prod([-1 if fl else 1 for fl in flips])
+            if s > 0:
+                out.append((perm, flips))
+    return out
+
+
+def reorient_elements(mesh, seed):
+    """Renumber every element's local nodes by a random rotation of the reference element.
+
+    The physical mesh is unchanged; local face numbering and neighbour orientation
+    codes change, which exercises the general face-matching logic of any consumer.
+    """
+    rng = np.random.default_rng(seed)
+    rots = _rotations(mesh.dim)
+    dim, r = mesh.dim, mesh.r
+    new_nodes = np.empty_like(mesh.elem_nodes)
+    for e in range(mesh.n_elem):
+        perm, flips = rots[rng.integers(len(rots))]
+        for loc in itertools.product(*[range(r + 1)] * dim):
+            loc = tuple(reversed(loc))              # new local index tuple
+            old = [0] * dim
+            # new_xi[k] = f(old_xi[perm[k]])  =>  old_xi[perm[k]] = f^-1(new_xi[k])
+            for k in range(dim):
+                old[perm[k]] = r - loc[k] if flips[k] else loc[k]
+            new_nodes[e, _local_index(loc, r)] = mesh.elem_nodes[e, _local_index(old, r)]
+    return _finish(dim, r, mesh.nodes, new_nodes, mesh.shape)
+
+
+# ---------------------------------------------------------------- displacement fields
+
+def disp_sine_2d(amp=0.05):
+    """x' = x + amp sin(2 pi x) sin(2 pi y), y' = y + the same (zero on the unit-square boundary)."""
+    def f(X):
+        d = amp * np.sin(2 * np.pi * X[:, 0]) * np.sin(2 * np.pi * X[:, 1])
+        return np.stack([d, d], axis=1)
+    return f
+
+
+def disp_random_smooth(h, seed, amp_frac=0.1, n_modes=8, kmax=None):
+    """Seeded smooth random displacement of amplitude <= amp_frac*h, zero on the boundary.
+
+    Each component: A * sin(pi x) sin(pi y) * sum_j a_j sin(2 pi k_j . x + phi_j) / sum_j |a_j|
+    with A = amp_frac*h, integer wavevectors k_j in [1, kmax]^dim (kmax = max(1, 1/(4h))),
+    a_j ~ U[-1,1], phi_j ~ U[0, 2 pi), drawn from numpy PCG64(seed).
+    """
+    rng = np.random.default_rng(seed)
+    if kmax is None:
+        kmax = max(1, int(round(1.0 / (4.0 * h))))
+    params = []
+    for _comp in range(2):
+        k = rng.integers(1, kmax + 1, size=(n_modes, 2)).astype(np.float64)
+        a = rng.uniform(-1.0, 1.0, size=n_modes)
+        ph = rng.uniform(0.0, 2 * np.pi, size=n_modes)
+        params.append((k, a, ph))
+    A = amp_frac * h
+
+    def f(X):
+        env = np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1])
+        out = np.zeros_like(X)
+        for c, (k, a, ph) in enumerate(params):
+            s = np.zeros(X.shape[0])
+            for j in range(len(a)):
+                s += a[j] * np.sin(2 * np.pi * (k[j, 0] * X[:, 0] + k[j, 1] * X[:, 1]) + ph[j])
+            out[:, c] = A * env * s / np.abs(a).sum()
+        return out
+    return f
+
+
+def disp_random_smooth_3d(h, seed, amp_frac=0.1, n_modes=8, kmax=None):
+    """3D version of disp_random_smooth (envelope sin(pi x) sin(pi y) sin(pi z), 3 components)."""
+    rng = np.random.default_rng(seed)
+    if kmax is None:
+        kmax = max(1, int(round(1.0 / (4.0 * h))))
+    params = []
+    for _comp in range(3):
+        k = rng.integers(1, kmax + 1, size=(n_modes, 3)).astype(np.float64)
+        a = rng.uniform(-1.0, 1.0, size=n_modes)
+        ph = rng.uniform(0.0, 2 * np.pi, size=n_modes)
+        params.append((k, a, ph))
+    A = amp_frac * h
+
+    def f(X):
+        env = np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1]) * np.sin(np.pi * X[:, 2])
+        out = np.zeros_like(X)
+        for c, (k, a, ph) in enumerate(params):
+            s = np.zeros(X.shape[0])
+            for j in range(len(a)):
+                s += a[j] * np.sin(2 * np.pi * (X @ k[j]) + ph[j])
+            out[:, c] = A * env * s / np.abs(a).sum()
+        return out
+    return f
+
+
+def disp_twist(total_angle=np.pi / 3):
+    """Rotate (x, y) about (1/2, 1/2) by theta = total_angle * z (a z-dependent twist)."""
+    def f(X):
+        th = total_angle * X[:, 2]
+        x, y = X[:, 0] - 0.5, X[:, 1] - 0.5
+        xn = np.cos(th) * x - np.sin(th) * y
+        yn = np.sin(th) * x + np.cos(th) * y
+        out = np.zeros_like(X)
+        out[:, 0] = xn - x
+        out[:, 1] = yn - y
+        return out
+    return f
