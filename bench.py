@@ -1,0 +1,303 @@
+"""Benchmark: lagged S_N transport sweep inside source iteration on one GB300.
+
+Workload (default): 2D 128x128 curved quad mesh, Q3 geometry with seeded smooth perturbation
+(amplitude 0.1 h), DG p = 3 (16 unknowns/element), level-symmetric S8 (40 directions),
+sigma_t ~ U[0.5, 5] per element, scattering ratio 0.9, q = 1, vacuum boundaries:
+16384 x 40 = 655,360 element-direction updates per sweep.
+
+A step is one source iteration through the C ABI (sn_si_step): the lagged sweep over every
+level and direction, then the fused scalar-flux moment + scattering-source update + residual.
+value = element-direction updates per second over the timed steps.
+
+--impl reference times the CPU FP64 oracle (the plain numpy restatement of the method) on a
+bounded sample of the same workload, on the host cores.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sweep elem-direction updates/s and time-to-1e-8 residual vs plain FP64 sweep"
+WORKLOAD = "2d_smooth_q3_p3_s8"
+WORKLOAD_DESC = ("2D 128x128 quads on [0,1]^2, Q3 geometry, seeded smooth perturbation 0.1h, DG p=3 (16 dofs), "
+                 "S8 (40 dirs), sigma_t~U[0.5,5], c=0.9, q=1, vacuum; 655360 updates/sweep")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 pipe peak: 152 SMs x 2 DFMA/clk/SM (measured 1/64 of the FP32 FMA rate on GB300) x 2 flop
+# x SM clock.  At the 2070 MHz maximum clock: 1.259 TFLOP/s; measured with a DFMA microbenchmark:
+# 1.20 TFLOP/s (profiles/fp_pipe_peaks_microbench.md).
+FP64_PEAK_TFLOPS = 1.20
+
+
+def flops_per_update(dim, p, inflow_faces):
+    """Algorithmic FP64 flops of one (element, direction) update of the FP64 sweep:
+    assembly (dim+1) N^2 FMA, inflow-face blocks (dim+1) Nf^2 FMA + Nf^2 FMA trace per inflow face,
+    LU 2N^3/3, forward/backward substitution 2N^2."""
+    N = (p + 1) ** dim
+    Nf = (p + 1) ** (dim - 1)
+    return 2 * (dim + 1) * N * N + inflow_faces * 2 * (dim + 2) * Nf * Nf + 2.0 * N ** 3 / 3 + 2 * N * N
+
+
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, device_index=0):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or not parts[1].replace(".", "").isdigit():
+                continue
+            if int(parts[0]) != device_index:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]), "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+def make_problem(n=None):
+    import sn_inputs as si
+    return si.make_config(WORKLOAD, n=n)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_gpu(args):
+    import torch
+    import paper_1810_11080_gb300 as g
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    prob = make_problem()
+    E, N, M = prob.mesh.n_elem, (prob.p + 1) ** prob.mesh.dim, len(prob.w)
+    updates = E * M
+    stream = torch.cuda.Stream(device=local)
+    ctx = g.setup_problem(prob, device=local, stream=stream.cuda_stream)
+    t0 = time.time()
+    gstats = ctx.sn_build_graph("face", 10)
+    t_graph = time.time() - t0
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ---- resident FP64 steps (inputs in HBM)
+    ctx.sn_si_begin(None)
+    for _ in range(args.warmup):
+        ctx.sn_si_step(g.SN_PREC_FP64)
+    l0 = ctx.sn_kernel_launches()
+    clocks = ClockSampler()
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sweep_ms = 0.0
+    for _ in range(args.steps):
+        _res, ms = ctx.sn_si_step(g.SN_PREC_FP64, time_sweep=True)
+        sweep_ms += ms
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop(local)
+    ms_total = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms_total], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    launches = ctx.sn_kernel_launches() - l0
+    value = ws * updates * args.steps / (ms_total / 1e3)
+
+    # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    phi_h = torch.zeros((E, N), dtype=torch.float64, pin_memory=True).numpy()
+    phi2_h = torch.zeros((E, N), dtype=torch.float64, pin_memory=True).numpy()
+    psa = torch.zeros((M, E, N), dtype=torch.float64, pin_memory=True).numpy()
+    psb = torch.zeros((M, E, N), dtype=torch.float64, pin_memory=True).numpy()
+    for _ in range(max(1, args.warmup)):
+        ctx.sn_sweep(phi_h, psa, psb, g.SN_PREC_FP64)
+        ctx.sn_moment(psb, phi_h, phi2_h)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.sn_sweep(phi_h, psa, psb, g.SN_PREC_FP64)
+        ctx.sn_moment(psb, phi_h, phi2_h)
+        phi_h, phi2_h = phi2_h, phi_h
+        psa, psb = psb, psa
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    h2d = phi_h.nbytes + psa.nbytes + psb.nbytes + phi_h.nbytes
+    d2h = psb.nbytes + phi_h.nbytes
+
+    # ---- time to 1e-8 (FP64), full solve from phi = 0
+    t0 = time.perf_counter()
+    res = ctx.sn_source_iterate(1e-8, 2000, g.SN_PREC_FP64)
+    tts = time.perf_counter() - t0
+
+    if rank != 0:
+        return None
+    pk, pk_kind = peaks()
+    inflow_faces = prob.mesh.dim          # on average dim of the 2 dim faces are inflow faces
+    fpu = flops_per_update(prob.mesh.dim, prob.p, inflow_faces)
+    achieved = fpu * updates * args.steps / (sweep_ms / 1e3) / 1e12
+    out = {
+        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "precision": "fp64", "weighting": "face",
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (psi 2x84 MB + element factors 117 MB per sweep)"},
+        "roofline": {"bound": "alu", "kernel": "sweep64_kernel<2,3> (all level launches of one sweep)",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64 pipe)",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "FP64 DFMA microbenchmark (MEASURED_PEAKS.json has no FP64 entry)",
+                     "flops_per_update": fpu, "sweep_ms_per_step": sweep_ms / args.steps},
+        "e2e": {"value": updates * args.steps / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "time_to_1e-8": {"fp64_s": tts, "iters": res["iters"], "converged": res["converged"]},
+        "graph": {"build_s": t_graph, "removed": gstats["n_removed"], "levels": gstats["max_level"] + 1,
+                  "max_scc": gstats["max_scc"], "mixed_faces": gstats["n_mixed_faces"]},
+        "peaks_file": pk_kind,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample_dirs)
+    return out
+
+
+def cpu_baseline(n_dirs):
+    """The oracle as it stands, on a bounded sample: n_dirs directions of the full workload
+    (graph of those directions, local assembly + factorisation + one lagged sweep), one thread."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle.dg import Discretization
+    from oracle.graph import build_graph_dirs
+    from oracle.sweep import Sweeper
+    prob = make_problem()
+    dirs = list(range(n_dirs))
+    disc = Discretization(prob)
+    G = build_graph_dirs(disc, dirs, "face")
+    t0 = time.perf_counter()
+    sw = Sweeper(disc, G, dirs=dirs)
+    E, N, M = disc.E, disc.N, disc.M_dirs
+    sw.sweep(np.ones((E, N)), np.zeros((M, E, N)), dirs=dirs)
+    dt = time.perf_counter() - t0
+    ups = E * n_dirs / dt
+    return {"value": ups, "unit": "updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_dirs} of 40 directions of the same workload ({E * n_dirs} updates): local assembly, "
+                      f"LU and one lagged sweep, numpy/scipy FP64, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores: each step sweeps one direction of the same
+    workload (local assembly + factorisation + lagged sweep); value in updates/s."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    os.environ["OMP_NUM_THREADS"] = "1"
+    from oracle.dg import Discretization
+    from oracle.graph import build_graph_dirs
+    from oracle.sweep import Sweeper
+    prob = make_problem()
+    disc = Discretization(prob)
+    E, N, M = disc.E, disc.N, disc.M_dirs
+    total = args.warmup + args.steps
+    dirs = [k % M for k in range(total)]
+    G = build_graph_dirs(disc, sorted(set(dirs)), "face")
+    phi, psi_old = np.ones((E, N)), np.zeros((M, E, N))
+    times = []
+    for k, d in enumerate(dirs):
+        t0 = time.perf_counter()
+        sw = Sweeper(disc, G, dirs=[d])
+        sw.sweep(phi, psi_old, dirs=[d])
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    v = E * len(times) / sum(times)
+    cb = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
+          "sample": f"each step: one of the 40 directions of the same workload ({E} updates): local assembly, "
+                    f"LU and one lagged sweep, numpy/scipy FP64, single thread"}
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "precision": "fp64", "weighting": "face",
+                       "step": "one direction of one sweep"},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-dirs", type=int, default=1)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    out = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

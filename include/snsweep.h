@@ -1,0 +1,192 @@
+/*
+ * snsweep.h -- C ABI of a GB300 (sm_103a) library for the graph-based S_N transport sweep on
+ * curved high-order meshes (Haut, Maginot, Tomov, Southworth, Brunner, Bailey, "An Efficient
+ * Sweep-based Solver for the S_N Equations on High-Order Meshes").
+ *
+ * What it computes (paper sections in brackets):
+ *   steady mono-energetic S_N equation with isotropic scattering and inflow boundary values
+ *   [Sec. 2, eq. 1-2]; upwind DG of order p on Q_r curved quadrilaterals/hexahedra [Sec. 2,
+ *   eqs. 3-16]; per-direction element dependency graph with unity / face / sigma-inverse-face
+ *   edge weights, made acyclic by a minimum-weight feedback arc set (exact on small SCCs,
+ *   Eades-Lin-Smyth on large ones) [Sec. 3]; lagged transport sweeps inside source iteration
+ *   [Sec. 3, eqs. 17-21].
+ *
+ * Conventions for every call:
+ *   - Every call returns sn_status; SN_OK = 0.  On failure sn_last_error(ctx) holds a message.
+ *     No call throws or aborts.  A failed call leaves previously accepted state unchanged
+ *     unless stated otherwise.
+ *   - All arrays are caller-owned, dense, row-major (C order), element indices 64-bit where
+ *     the type says so.  The library copies what it keeps; it never frees caller memory.
+ *   - Data pointers may be host or device pointers (CUDA unified addressing decides, per
+ *     pointer, via cudaPointerGetAttributes).  Host buffers are staged through the context's
+ *     device buffers; device buffers are used in place.
+ *   - All device work is ordered on the context's CUDA stream (given at creation).  Calls that
+ *     return host-visible results synchronise that stream before returning.
+ *   - One context = one problem on one GPU.  A context is not thread-safe.
+ *
+ * Mesh conventions (sn_set_mesh):
+ *   reference element [0,1]^dim; control points of the Q_r map on the equispaced reference
+ *   nodes a/r, local index m = a0 + (r+1) a1 (+ (r+1)^2 a2) [Sec. 2, eq. 1].
+ *   Local face f = 2*axis + side (side 0: xi_axis = 0).  A face's coordinates (s0[, s1]) are
+ *   the remaining reference axes in increasing order.  orient[e][f] maps e's face
+ *   coordinates to the neighbour's: swap (bit 2) first, then s -> 1 - s on the first (bit 0)
+ *   and second (bit 1) result.
+ *   DG unknowns: tensor Gauss-Lobatto-Legendre nodes of order p, node index as above with p.
+ *   Face node (i, j) of face f is the volume node with index i along s0, j along s1.
+ *   Boundary faces are numbered in increasing (element, local face) order.
+ */
+#ifndef SNSWEEP_H
+#define SNSWEEP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sn_ctx sn_ctx;
+
+typedef enum {
+  SN_OK = 0,
+  SN_EINVAL = 1,          /* bad argument (null pointer, size out of range, non-finite value)   */
+  SN_ENOMEM = 2,          /* device or host allocation failed                                    */
+  SN_ECUDA = 3,           /* a CUDA runtime call failed (message has the CUDA error string)     */
+  SN_ETIMEOUT = 4,        /* a bounded device wait gave up (device error word set)              */
+  SN_ENOTCONVERGED = 5,   /* source iteration hit max_iter before reaching tol                  */
+  SN_EMESH = 6,           /* invalid mesh: det J <= 0, inconsistent connectivity                */
+  SN_ESTATE = 7           /* call out of order (e.g. sweep before build_graph)                  */
+} sn_status;
+
+enum { SN_WEIGHT_UNITY = 0, SN_WEIGHT_FACE = 1, SN_WEIGHT_SIGINVFACE = 2 };
+enum { SN_PREC_FP64 = 0, SN_PREC_MIXED = 1 };
+
+typedef struct {
+  int64_t n_arcs;          /* arcs e' -> e over all directions                                 */
+  int64_t n_removed;       /* arcs removed (lagged) over all directions                        */
+  int64_t n_scc;           /* non-trivial SCCs over all directions                             */
+  int32_t max_scc;         /* largest SCC size                                                 */
+  int32_t max_level;       /* largest sweep level (levels are 0-based)                          */
+  int64_t n_mixed_faces;   /* (face side, direction) pairs whose inflow region is partial      */
+  double ms_geometry;      /* device time of the geometric-factor stage                        */
+  double ms_weights;       /* device time of the edge-weight stage                              */
+  double ms_fas;           /* host time of SCC + feedback-arc-set                               */
+  double ms_levels;        /* device time of level scheduling + work lists                      */
+} sn_graph_stats;
+
+typedef struct {
+  int32_t iters;           /* source iterations performed                                      */
+  int32_t converged;       /* 1 if ||phi_{l+1}-phi_l||_inf / ||phi_{l+1}||_inf < tol was reached */
+  double residual;         /* last relative scalar-flux change                                  */
+  double ms_total;         /* wall time of the iteration loop (host clock)                     */
+} sn_si_stats;
+
+/* Create a context on CUDA device `device`, ordering all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the context. */
+sn_status sn_create(sn_ctx** out, int device, void* cuda_stream);
+
+/* Destroy a context and free its device memory.  Accepts NULL. */
+void sn_destroy(sn_ctx* ctx);
+
+/* Last error message of this context ("" if none).  Owned by the context. */
+const char* sn_last_error(const sn_ctx* ctx);
+
+/* Mesh [Sec. 2, 'Discrete representation of the HO mesh'].
+ *   dim 2 or 3; geometry order r in 1..3; n_elem >= 1.
+ *   ctrl      [n_elem][(r+1)^dim][dim] control points (x_{e,m} of eq. 1).
+ *   face_nbr  [n_elem][2 dim] neighbour element or -1 on the domain boundary.
+ *   nbr_face  [n_elem][2 dim] the neighbour's local face (ignored where face_nbr = -1).
+ *   orient    [n_elem][2 dim] orientation code (see header comment; 0..1 in 2D, 0..7 in 3D).
+ * Errors: SN_EINVAL (sizes, codes), SN_EMESH (neighbour relation not symmetric).
+ * Resets everything computed from an earlier mesh. */
+sn_status sn_set_mesh(sn_ctx* ctx, int dim, int64_t n_elem, int r, const double* ctrl,
+                      const int64_t* face_nbr, const int32_t* nbr_face, const int32_t* orient);
+
+/* DG order p: 1..3 in 2D, 1..2 in 3D (N = (p+1)^dim <= 32 unknowns per element) and, for 3D, the number K of
+ * sub-squares per face axis of the composite face rule (K >= 1; ignored in 2D).
+ * Quadrature: volume n_v = p + ceil(dim r / 2) Gauss-Legendre points per axis, faces
+ * n_f = p + r; 2D faces are split at the sign changes of Omega.n [Sec. 2, last paragraph]. */
+sn_status sn_set_discretization(sn_ctx* ctx, int p, int face_subdiv);
+
+/* Angular quadrature {(w_d, Omega_d)} [Sec. 2, after eq. 2]: omega [n_dir][3] unit vectors
+ * (2D problems use the first two components), w [n_dir] > 0.  n_dir in 1..4096. */
+sn_status sn_set_quadrature(sn_ctx* ctx, int n_dir, const double* omega, const double* w);
+
+/* Materials and sources [Sec. 2, eqs. 1, 8].
+ *   sigma_t, sigma_s [n_elem] element-constant cross sections (sigma_t > 0, sigma_s >= 0).
+ *   q        [n_elem][N] nodal isotropic source, or NULL (= 0).
+ *   q_dir    [n_dir][n_elem][N] nodal direction-dependent source added to q, or NULL.
+ *   psi_inc  [n_dir][n_bdr_faces][N_f] nodal incident angular flux on boundary faces
+ *            (face-node order of the owning element), or NULL (vacuum).
+ * Requires mesh, discretization and quadrature. */
+sn_status sn_set_materials(sn_ctx* ctx, const double* sigma_t, const double* sigma_s,
+                           const double* q, const double* q_dir, const double* psi_inc);
+
+/* Number of boundary faces (valid after sn_set_mesh). */
+int64_t sn_num_boundary_faces(const sn_ctx* ctx);
+
+/* Build the sweep graph [Sec. 3]: geometric factors, upwind arcs and weights on the device,
+ * SCC + minimum feedback arc set on the host (exact for SCCs of at most exact_max <= 16
+ * vertices, Eades-Lin-Smyth above), sweep levels and work lists on the device.
+ * weighting: SN_WEIGHT_UNITY / _FACE / _SIGINVFACE.  stats may be NULL.
+ * Errors: SN_ESTATE (missing inputs), SN_EMESH (det J <= 0 somewhere). */
+sn_status sn_build_graph(sn_ctx* ctx, int weighting, int exact_max, sn_graph_stats* stats);
+
+/* Copy the graph out (valid after sn_build_graph).
+ *   *n_removed receives the number of removed arcs; if removed != NULL and cap >= that number,
+ *   removed [k][3] receives (direction, e, e') rows sorted ascending: e depends on e' and the
+ *   dependency is lagged.  levels [n_dir][n_elem] (may be NULL) receives the sweep level of
+ *   every (direction, element).  Returns SN_EINVAL if cap is too small (n_removed still set). */
+sn_status sn_get_graph(sn_ctx* ctx, int64_t* n_removed, int32_t* removed, int64_t cap,
+                       int32_t* levels);
+
+/* One lagged sweep over all directions [eq. 21]:
+ *   for each direction, element by element in level order, solve
+ *   (G + F_e + M_t) psi_e = M (q + q_dir + sigma_s phi_in / (4 pi)) + boundary inflow
+ *                           + sum_{kept e'} Fbar psi_new,e' + sum_{removed e'} Fbar psi_old,e'.
+ *   phi_in   [n_elem][N]          scalar flux of the previous iterate.
+ *   psi_old  [n_dir][n_elem][N]   previous angular flux (read for removed arcs only).
+ *   psi_new  [n_dir][n_elem][N]   output; must not alias psi_old.
+ *   precision SN_PREC_FP64: all local algebra in FP64.  SN_PREC_MIXED: FP32 assembly and LU,
+ *   one refinement step whose residual is formed in FP64.
+ * Synchronises the stream before returning when any pointer is a host pointer. */
+sn_status sn_sweep(sn_ctx* ctx, const double* phi_in, const double* psi_old, double* psi_new,
+                   int precision);
+
+/* Scalar-flux moment [eq. 2] and relative change:
+ *   phi_out = sum_d w_d psi_d;  *residual = ||phi_out - phi_prev||_inf / ||phi_out||_inf
+ *   (phi_prev may be NULL: treated as 0).  Also refreshes the context's scattering source for
+ *   the next sweep.  Synchronises the stream (the residual is a host value). */
+sn_status sn_moment(sn_ctx* ctx, const double* psi, const double* phi_prev, double* phi_out,
+                    double* residual);
+
+/* Source iteration [eq. 18 with the lagged sweep of eq. 21] from phi0 (NULL = 0) and
+ * psi = 0 until the relative scalar-flux change drops below tol or max_iter sweeps ran.
+ *   phi_out [n_elem][N], psi_out [n_dir][n_elem][N] (either may be NULL).
+ *   history [history_cap] receives the residual of each iteration (may be NULL).
+ * Returns SN_ENOTCONVERGED (results still written) if tol was not reached. */
+sn_status sn_source_iterate(sn_ctx* ctx, double tol, int max_iter, int precision,
+                            const double* phi0, double* phi_out, double* psi_out,
+                            sn_si_stats* stats, double* history, int history_cap);
+
+/* Resident source iteration, one step at a time (the loop of sn_source_iterate, exposed so a
+ * caller can time or interleave single iterations).
+ *   sn_si_begin : phi <- phi0 (NULL = 0), psi <- 0, scattering source from phi.
+ *   sn_si_step  : one lagged sweep over all directions [eq. 21] into the context's other psi
+ *                 buffer, then the fused scalar-flux moment + scattering-source update +
+ *                 residual [eqs. 2, 18].  *residual (may be NULL) receives
+ *                 ||phi_{l+1} - phi_l||_inf / ||phi_{l+1}||_inf; *ms_sweep (may be NULL) the device
+ *                 time of the sweep launches measured with CUDA events on the context's stream.
+ *                 Synchronises the stream.
+ *   sn_si_result: copy the current phi [n_elem][N] and psi [n_dir][n_elem][N] out (either may be
+ *                 NULL; host or device pointers). */
+sn_status sn_si_begin(sn_ctx* ctx, const double* phi0);
+sn_status sn_si_step(sn_ctx* ctx, int precision, double* residual, float* ms_sweep);
+sn_status sn_si_result(sn_ctx* ctx, double* phi_out, double* psi_out);
+
+/* Number of kernel launches this context has issued since creation (diagnostics). */
+int64_t sn_kernel_launches(const sn_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNSWEEP_H */

@@ -379,3 +379,27 @@ def build_graph(disc, weighting="face", exact_max=10, chunk=4):
         levels[d] = levels_from_kept(E, src, dst, ~mask)
     removed = np.array(sorted(removed), dtype=np.int64).reshape(-1, 3)
     return dict(arcs=arcs, removed=removed, levels=levels, scc_sizes=sccs, weighting=weighting)
+
+
+def build_graph_dirs(disc, dirs, weighting="face", exact_max=10, chunk=4):
+    """build_graph restricted to the directions in `dirs` (levels of other directions are 0,
+    their arc lists empty)."""
+    M, E = disc.M_dirs, disc.E
+    arcs = [None] * M
+    dirs = list(dirs)
+    for c0 in range(0, len(dirs), chunk):
+        ds = dirs[c0:c0 + chunk]
+        for d, a in zip(ds, edge_weights(disc, ds, weighting)):
+            arcs[d] = a
+    removed = []
+    levels = np.zeros((M, E), dtype=np.int32)
+    sccs = [[] for _ in range(M)]
+    for d in dirs:
+        src, dst, z = arcs[d]
+        mask, sizes = break_cycles(E, src, dst, z, exact_max)
+        sccs[d] = sizes
+        for u, v in zip(src[mask].tolist(), dst[mask].tolist()):
+            removed.append((d, v, u))
+        levels[d] = levels_from_kept(E, src, dst, ~mask)
+    removed = np.array(sorted(removed), dtype=np.int64).reshape(-1, 3)
+    return dict(arcs=arcs, removed=removed, levels=levels, scc_sizes=sccs, weighting=weighting)

@@ -1,0 +1,12 @@
+"""GB300 (sm_103a) library for the graph-based S_N transport sweep on curved high-order meshes.
+
+The compute path is libsnsweep.so (CUDA kernels + C ABI, include/snsweep.h); this package is
+its Python binding plus a convenience loader for sn_inputs problems.
+"""
+from ._lib import (Context, SnError, load, lib, LIB_PATH, EXPORTED, SN_PREC_FP64, SN_PREC_MIXED,
+                   SN_WEIGHT_UNITY, SN_WEIGHT_FACE, SN_WEIGHT_SIGINVFACE, SN_OK, SN_ENOTCONVERGED)
+from .problem import setup_problem
+
+__all__ = ["Context", "SnError", "load", "lib", "LIB_PATH", "EXPORTED", "setup_problem",
+           "SN_PREC_FP64", "SN_PREC_MIXED", "SN_WEIGHT_UNITY", "SN_WEIGHT_FACE", "SN_WEIGHT_SIGINVFACE",
+           "SN_OK", "SN_ENOTCONVERGED"]

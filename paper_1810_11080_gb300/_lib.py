@@ -1,0 +1,211 @@
+"""ctypes binding of libsnsweep.so (include/snsweep.h): argument marshalling only.
+
+Every function keeps the C name.  Array arguments may be numpy arrays (host memory) or torch
+tensors (host or CUDA); they are passed as raw pointers after a dtype/contiguity check.
+The library must have been built (paper_1810_11080_gb300.build.build()); importing this
+module without it raises immediately -- there is no fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsnsweep.so")
+
+SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENOTCONVERGED, SN_EMESH, SN_ESTATE = range(8)
+SN_WEIGHT_UNITY, SN_WEIGHT_FACE, SN_WEIGHT_SIGINVFACE = 0, 1, 2
+SN_PREC_FP64, SN_PREC_MIXED = 0, 1
+WEIGHTING = {"unity": 0, "face": 1, "siginvface": 2}
+
+EXPORTED = ["sn_create", "sn_destroy", "sn_last_error", "sn_set_mesh", "sn_set_discretization",
+            "sn_set_quadrature", "sn_set_materials", "sn_num_boundary_faces", "sn_build_graph",
+            "sn_get_graph", "sn_sweep", "sn_moment", "sn_source_iterate", "sn_si_begin", "sn_si_step",
+            "sn_si_result", "sn_kernel_launches"]
+
+
+class sn_graph_stats(ctypes.Structure):
+    _fields_ = [("n_arcs", ctypes.c_int64), ("n_removed", ctypes.c_int64), ("n_scc", ctypes.c_int64),
+                ("max_scc", ctypes.c_int32), ("max_level", ctypes.c_int32), ("n_mixed_faces", ctypes.c_int64),
+                ("ms_geometry", ctypes.c_double), ("ms_weights", ctypes.c_double), ("ms_fas", ctypes.c_double),
+                ("ms_levels", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class sn_si_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("residual", ctypes.c_double),
+                ("ms_total", ctypes.c_double)]
+
+
+class SnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"snsweep status {status}: {msg}")
+        self.status = status
+
+
+def load(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1810_11080_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "sn_create": (I, [ctypes.POINTER(P), I, P]),
+        "sn_destroy": (None, [P]),
+        "sn_last_error": (ctypes.c_char_p, [P]),
+        "sn_set_mesh": (I, [P, I, I64, I, P, P, P, P]),
+        "sn_set_discretization": (I, [P, I, I]),
+        "sn_set_quadrature": (I, [P, I, P, P]),
+        "sn_set_materials": (I, [P, P, P, P, P, P]),
+        "sn_num_boundary_faces": (I64, [P]),
+        "sn_build_graph": (I, [P, I, I, ctypes.POINTER(sn_graph_stats)]),
+        "sn_get_graph": (I, [P, ctypes.POINTER(I64), P, I64, P]),
+        "sn_sweep": (I, [P, P, P, P, I]),
+        "sn_moment": (I, [P, P, P, P, ctypes.POINTER(D)]),
+        "sn_source_iterate": (I, [P, D, I, I, P, P, P, ctypes.POINTER(sn_si_stats), P, I]),
+        "sn_si_begin": (I, [P, P]),
+        "sn_si_step": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_float)]),
+        "sn_si_result": (I, [P, P, P]),
+        "sn_kernel_launches": (I64, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def _ptr(a, dtype, name):
+    """Raw pointer of a numpy array or torch tensor of the given numpy dtype (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"{name}: expected C-contiguous {np.dtype(dtype).name} array")
+        return a.ctypes.data
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        tmap = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32, np.float32: torch.float32}
+        if a.dtype != tmap[np.dtype(dtype).type] or not a.is_contiguous():
+            raise TypeError(f"{name}: expected contiguous {tmap[np.dtype(dtype).type]} tensor")
+        return a.data_ptr()
+    raise TypeError(f"{name}: expected numpy array or torch tensor")
+
+
+class Context:
+    """Owns one sn_ctx.  Methods map one to one onto the C functions."""
+
+    def __init__(self, device=0, stream=None):
+        self._lib = lib()
+        self._c = ctypes.c_void_p()
+        st = self._lib.sn_create(ctypes.byref(self._c), int(device), stream)
+        if st != SN_OK:
+            raise SnError(st, "sn_create failed")
+
+    def _check(self, st):
+        if st != SN_OK:
+            raise SnError(st, self._lib.sn_last_error(self._c).decode())
+        return st
+
+    def close(self):
+        if self._c:
+            self._lib.sn_destroy(self._c)
+            self._c = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sn_set_mesh(self, dim, n_elem, r, ctrl, face_nbr, nbr_face, orient):
+        return self._check(self._lib.sn_set_mesh(self._c, dim, n_elem, r, _ptr(ctrl, np.float64, "ctrl"),
+                                                 _ptr(face_nbr, np.int64, "face_nbr"),
+                                                 _ptr(nbr_face, np.int32, "nbr_face"),
+                                                 _ptr(orient, np.int32, "orient")))
+
+    def sn_set_discretization(self, p, face_subdiv=2):
+        return self._check(self._lib.sn_set_discretization(self._c, p, face_subdiv))
+
+    def sn_set_quadrature(self, omega, w):
+        return self._check(self._lib.sn_set_quadrature(self._c, len(w), _ptr(omega, np.float64, "omega"),
+                                                       _ptr(w, np.float64, "w")))
+
+    def sn_set_materials(self, sigma_t, sigma_s, q=None, q_dir=None, psi_inc=None):
+        return self._check(self._lib.sn_set_materials(self._c, _ptr(sigma_t, np.float64, "sigma_t"),
+                                                      _ptr(sigma_s, np.float64, "sigma_s"),
+                                                      _ptr(q, np.float64, "q"), _ptr(q_dir, np.float64, "q_dir"),
+                                                      _ptr(psi_inc, np.float64, "psi_inc")))
+
+    def sn_num_boundary_faces(self):
+        return self._lib.sn_num_boundary_faces(self._c)
+
+    def sn_build_graph(self, weighting="face", exact_max=10):
+        st = sn_graph_stats()
+        w = WEIGHTING[weighting] if isinstance(weighting, str) else int(weighting)
+        self._check(self._lib.sn_build_graph(self._c, w, exact_max, ctypes.byref(st)))
+        return st.as_dict()
+
+    def sn_get_graph(self, n_dir, n_elem):
+        n = ctypes.c_int64()
+        self._check(self._lib.sn_get_graph(self._c, ctypes.byref(n), None, 0, None))
+        removed = np.zeros((max(1, n.value), 3), dtype=np.int32)
+        levels = np.zeros((n_dir, n_elem), dtype=np.int32)
+        self._check(self._lib.sn_get_graph(self._c, ctypes.byref(n), removed.ctypes.data, n.value,
+                                           levels.ctypes.data))
+        return removed[:n.value].astype(np.int64), levels
+
+    def sn_sweep(self, phi_in, psi_old, psi_new, precision=SN_PREC_FP64):
+        return self._check(self._lib.sn_sweep(self._c, _ptr(phi_in, np.float64, "phi_in"),
+                                              _ptr(psi_old, np.float64, "psi_old"),
+                                              _ptr(psi_new, np.float64, "psi_new"), precision))
+
+    def sn_moment(self, psi, phi_prev, phi_out):
+        r = ctypes.c_double()
+        self._check(self._lib.sn_moment(self._c, _ptr(psi, np.float64, "psi"),
+                                        _ptr(phi_prev, np.float64, "phi_prev"),
+                                        _ptr(phi_out, np.float64, "phi_out"), ctypes.byref(r)))
+        return r.value
+
+    def sn_source_iterate(self, tol, max_iter, precision=SN_PREC_FP64, phi0=None, phi_out=None, psi_out=None,
+                          history_cap=0):
+        st = sn_si_stats()
+        hist = np.zeros(max(1, history_cap))
+        s = self._lib.sn_source_iterate(self._c, tol, max_iter, precision, _ptr(phi0, np.float64, "phi0"),
+                                        _ptr(phi_out, np.float64, "phi_out"), _ptr(psi_out, np.float64, "psi_out"),
+                                        ctypes.byref(st), hist.ctypes.data if history_cap else None, history_cap)
+        if s not in (SN_OK, SN_ENOTCONVERGED):
+            self._check(s)
+        return dict(status=s, iters=st.iters, converged=bool(st.converged), residual=st.residual,
+                    ms_total=st.ms_total, history=hist[:min(st.iters, history_cap)].copy())
+
+    def sn_si_begin(self, phi0=None):
+        return self._check(self._lib.sn_si_begin(self._c, _ptr(phi0, np.float64, "phi0")))
+
+    def sn_si_step(self, precision=SN_PREC_FP64, time_sweep=False):
+        """Returns (residual, sweep milliseconds or None)."""
+        r = ctypes.c_double()
+        ms = ctypes.c_float()
+        self._check(self._lib.sn_si_step(self._c, precision, ctypes.byref(r), ctypes.byref(ms) if time_sweep else None))
+        return r.value, (ms.value if time_sweep else None)
+
+    def sn_si_result(self, phi_out=None, psi_out=None):
+        return self._check(self._lib.sn_si_result(self._c, _ptr(phi_out, np.float64, "phi_out"),
+                                                  _ptr(psi_out, np.float64, "psi_out")))
+
+    def sn_kernel_launches(self):
+        return self._lib.sn_kernel_launches(self._c)

@@ -1,0 +1,843 @@
+// C ABI of the snsweep library (declared in include/snsweep.h): context, problem upload,
+// graph build (device weights -> host SCC/FAS -> device levels), sweeps and source iteration.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <cuda_runtime.h>
+#include "common.h"
+
+using namespace sn;
+
+namespace {
+
+struct Fail {
+  sn_status st;
+};
+
+void set_err(sn_ctx* c, const std::string& m) {
+  if (c) c->err = m;
+}
+
+#define SN_CUDA(ctx, call)                                                                      \
+  do {                                                                                          \
+    cudaError_t _e = (call);                                                                    \
+    if (_e != cudaSuccess) {                                                                    \
+      set_err(ctx, std::string(#call) + ": " + cudaGetErrorString(_e));                         \
+      return SN_ECUDA;                                                                          \
+    }                                                                                           \
+  } while (0)
+
+#define SN_REQ(ctx, cond, st, msg) \
+  do {                             \
+    if (!(cond)) {                 \
+      set_err(ctx, msg);           \
+      return st;                   \
+    }                              \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T*& p, size_t n) {
+  if (p) {
+    cudaFree(p);
+    p = nullptr;
+  }
+  if (n == 0) return cudaSuccess;
+  return cudaMalloc((void**)&p, n * sizeof(T));
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void free_graph_state(sn_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  dfree(c->d_facecode);
+  dfree(c->d_mixed_off);
+  dfree(c->d_mixedB);
+  dfree(c->d_mixedB32);
+  dfree(c->d_levels);
+  dfree(c->d_pairs);
+  dfree(c->d_elem);
+  dfree(c->d_elem32);
+  c->graph_ready = false;
+  c->si_ready = false;
+  c->level_off.clear();
+  c->h_removed.clear();
+  c->n_removed = 0;
+}
+
+}  // namespace
+
+sn::DevProblem sn_ctx::dev() const {
+  DevProblem P{};
+  P.dim = dim;
+  P.r = r;
+  P.p = p;
+  P.N = N;
+  P.Nf = Nf;
+  P.nv = tab.nv;
+  P.nf = tab.nf;
+  P.K = (dim == 3) ? K : 1;
+  P.Q = tab.Q;
+  P.Nv = tab.Nv;
+  P.M = M;
+  P.E = E;
+  P.n_bdr = n_bdr;
+  P.ctrl = d_ctrl;
+  P.nbr = d_nbr;
+  P.nbr_face = d_nbr_face;
+  P.orient = d_orient;
+  P.bdr_index = d_bdr_index;
+  P.omega = d_omega;
+  P.w = d_w;
+  P.sig_t = d_sig_t;
+  P.sig_s = d_sig_s;
+  P.q = d_q;
+  P.q_dir = d_qdir;
+  P.psi_inc = d_psi_inc;
+  P.tab = d_tab;
+  P.off_glv_t = tab_off[0];
+  P.off_glv_w = tab_off[1];
+  P.off_glf_t = tab_off[2];
+  P.off_glf_w = tab_off[3];
+  P.off_gll = tab_off[4];
+  P.off_geo = tab_off[5];
+  P.off_wq = tab_off[6];
+  P.off_B = tab_off[7];
+  P.off_dB = tab_off[8];
+  P.off_dV = tab_off[9];
+  P.elem = d_elem;
+  P.blk = blk;
+  P.elem32 = d_elem32;
+  return P;
+}
+
+extern "C" {
+
+sn_status sn_create(sn_ctx** out, int device, void* cuda_stream) {
+  if (!out) return SN_EINVAL;
+  *out = nullptr;
+  sn_ctx* c = new (std::nothrow) sn_ctx();
+  if (!c) return SN_ENOMEM;
+  c->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    delete c;
+    return SN_ECUDA;
+  }
+  c->stream = (cudaStream_t)cuda_stream;
+  if (cudaMalloc((void**)&c->d_red, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc((void**)&c->d_flag, 4 * sizeof(int)) != cudaSuccess) {
+    cudaFree(c->d_red);
+    delete c;
+    return SN_ENOMEM;
+  }
+  *out = c;
+  return SN_OK;
+}
+
+void sn_destroy(sn_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  free_graph_state(c);
+  dfree(c->d_ctrl);
+  dfree(c->d_omega);
+  dfree(c->d_w);
+  dfree(c->d_tab);
+  dfree(c->d_nbr);
+  dfree(c->d_bdr_index);
+  dfree(c->d_nbr_face);
+  dfree(c->d_orient);
+  dfree(c->d_iface);
+  dfree(c->d_bface);
+  dfree(c->d_sig_t);
+  dfree(c->d_sig_s);
+  dfree(c->d_q);
+  dfree(c->d_qdir);
+  dfree(c->d_psi_inc);
+  for (auto& p : c->d_psi) dfree(p);
+  dfree(c->d_phi);
+  dfree(c->d_phi2);
+  dfree(c->d_src);
+  for (auto& p : c->d_stage) dfree(p);
+  dfree(c->d_red);
+  dfree(c->d_flag);
+  if (c->ev_a) cudaEventDestroy(c->ev_a);
+  if (c->ev_b) cudaEventDestroy(c->ev_b);
+  delete c;
+}
+
+const char* sn_last_error(const sn_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t sn_kernel_launches(const sn_ctx* c) { return c ? c->launches : 0; }
+
+int64_t sn_num_boundary_faces(const sn_ctx* c) { return c ? c->n_bdr : 0; }
+
+sn_status sn_set_mesh(sn_ctx* c, int dim, int64_t n_elem, int r, const double* ctrl, const int64_t* face_nbr,
+                      const int32_t* nbr_face, const int32_t* orient) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, dim == 2 || dim == 3, SN_EINVAL, "dim must be 2 or 3");
+  SN_REQ(c, r >= 1 && r <= MAX_R, SN_EINVAL, "geometry order r must be 1..3");
+  SN_REQ(c, n_elem >= 1 && n_elem < (1LL << 31) / 8, SN_EINVAL, "n_elem out of range");
+  SN_REQ(c, ctrl && face_nbr && nbr_face && orient, SN_EINVAL, "null mesh array");
+  cudaSetDevice(c->device);
+  const int nfc = 2 * dim;
+  int64_t nv = 1;
+  for (int k = 0; k < dim; ++k) nv *= (r + 1);
+  std::vector<double> hc(n_elem * nv * dim);
+  std::vector<int64_t> hn(n_elem * nfc);
+  std::vector<int32_t> hf(n_elem * nfc), ho(n_elem * nfc);
+  auto fetch = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (is_device_ptr(src)) return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+    std::memcpy(dst, src, bytes);
+    return cudaSuccess;
+  };
+  SN_CUDA(c, fetch(hc.data(), ctrl, hc.size() * sizeof(double)));
+  SN_CUDA(c, fetch(hn.data(), face_nbr, hn.size() * sizeof(int64_t)));
+  SN_CUDA(c, fetch(hf.data(), nbr_face, hf.size() * sizeof(int32_t)));
+  SN_CUDA(c, fetch(ho.data(), orient, ho.size() * sizeof(int32_t)));
+  for (double v : hc) SN_REQ(c, std::isfinite(v), SN_EINVAL, "non-finite control point");
+  // symmetric neighbour relation
+  for (int64_t e = 0; e < n_elem; ++e)
+    for (int f = 0; f < nfc; ++f) {
+      int64_t nb = hn[e * nfc + f];
+      if (nb < 0) continue;
+      SN_REQ(c, nb < n_elem && nb != e, SN_EMESH, "face neighbour out of range");
+      int fn = hf[e * nfc + f];
+      SN_REQ(c, fn >= 0 && fn < nfc, SN_EMESH, "neighbour face out of range");
+      SN_REQ(c, hn[nb * nfc + fn] == e && hf[nb * nfc + fn] == f, SN_EMESH, "neighbour relation not symmetric");
+      int oc = ho[e * nfc + f];
+      SN_REQ(c, oc >= 0 && oc < (dim == 2 ? 2 : 8), SN_EINVAL, "orientation code out of range");
+    }
+  free_graph_state(c);
+  c->dim = dim;
+  c->r = r;
+  c->E = n_elem;
+  c->h_ctrl.swap(hc);
+  c->h_nbr.swap(hn);
+  c->h_nbr_face.swap(hf);
+  c->h_orient.swap(ho);
+  c->h_bdr_index.assign(n_elem * nfc, -1);
+  c->h_iface.clear();
+  c->h_bface.clear();
+  c->n_bdr = 0;
+  for (int64_t e = 0; e < n_elem; ++e)
+    for (int f = 0; f < nfc; ++f) {
+      int64_t nb = c->h_nbr[e * nfc + f];
+      if (nb < 0) {
+        c->h_bdr_index[e * nfc + f] = c->n_bdr++;
+        c->h_bface.push_back((int32_t)e);
+        c->h_bface.push_back(f);
+      } else if (e < nb) {
+        c->h_iface.insert(c->h_iface.end(),
+                          {(int32_t)e, f, (int32_t)nb, c->h_nbr_face[e * nfc + f], c->h_orient[e * nfc + f]});
+      }
+    }
+  SN_CUDA(c, dalloc(c->d_ctrl, c->h_ctrl.size()));
+  SN_CUDA(c, dalloc(c->d_nbr, c->h_nbr.size()));
+  SN_CUDA(c, dalloc(c->d_nbr_face, c->h_nbr_face.size()));
+  SN_CUDA(c, dalloc(c->d_orient, c->h_orient.size()));
+  SN_CUDA(c, dalloc(c->d_bdr_index, c->h_bdr_index.size()));
+  SN_CUDA(c, dalloc(c->d_iface, std::max<size_t>(1, c->h_iface.size())));
+  SN_CUDA(c, dalloc(c->d_bface, std::max<size_t>(1, c->h_bface.size())));
+  SN_CUDA(c, cudaMemcpy(c->d_ctrl, c->h_ctrl.data(), c->h_ctrl.size() * 8, cudaMemcpyHostToDevice));
+  SN_CUDA(c, cudaMemcpy(c->d_nbr, c->h_nbr.data(), c->h_nbr.size() * 8, cudaMemcpyHostToDevice));
+  SN_CUDA(c, cudaMemcpy(c->d_nbr_face, c->h_nbr_face.data(), c->h_nbr_face.size() * 4, cudaMemcpyHostToDevice));
+  SN_CUDA(c, cudaMemcpy(c->d_orient, c->h_orient.data(), c->h_orient.size() * 4, cudaMemcpyHostToDevice));
+  SN_CUDA(c, cudaMemcpy(c->d_bdr_index, c->h_bdr_index.data(), c->h_bdr_index.size() * 8, cudaMemcpyHostToDevice));
+  if (!c->h_iface.empty())
+    SN_CUDA(c, cudaMemcpy(c->d_iface, c->h_iface.data(), c->h_iface.size() * 4, cudaMemcpyHostToDevice));
+  if (!c->h_bface.empty())
+    SN_CUDA(c, cudaMemcpy(c->d_bface, c->h_bface.data(), c->h_bface.size() * 4, cudaMemcpyHostToDevice));
+  c->mesh_set = true;
+  c->disc_set = false;
+  c->mat_set = false;
+  return SN_OK;
+}
+
+sn_status sn_set_discretization(sn_ctx* c, int p, int face_subdiv) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->mesh_set, SN_ESTATE, "sn_set_mesh first");
+  SN_REQ(c, p >= 1 && p <= MAX_P, SN_EINVAL, "DG order p must be 1..3");
+  SN_REQ(c, c->dim == 2 || p <= 2, SN_EINVAL, "3D DG order p must be 1 or 2 ((p+1)^3 <= 32 unknowns per element)");
+  SN_REQ(c, face_subdiv >= 1 && face_subdiv <= 4, SN_EINVAL, "face_subdiv must be 1..4");
+  if (c->dim == 3) {
+    const int nf = p + c->r;
+    SN_REQ(c, face_subdiv * face_subdiv * nf * nf <= 256, SN_EINVAL, "3D face rule too large (K^2 n_f^2 > 256)");
+  }
+  cudaSetDevice(c->device);
+  free_graph_state(c);
+  c->p = p;
+  c->K = face_subdiv;
+  try {
+    build_tables(c->tab, c->dim, p, c->r);
+  } catch (const std::exception& ex) {
+    set_err(c, ex.what());
+    return SN_EINVAL;
+  }
+  c->N = c->tab.N;
+  c->Nf = c->tab.Nf;
+  c->blk = elem_block_doubles(c->dim, c->N, c->Nf);
+  std::vector<double> packed;
+  auto add = [&](int slot, const std::vector<double>& v) {
+    c->tab_off[slot] = (int)packed.size();
+    packed.insert(packed.end(), v.begin(), v.end());
+    while (packed.size() % 2) packed.push_back(0.0);
+  };
+  add(0, c->tab.glv_t);
+  add(1, c->tab.glv_w);
+  add(2, c->tab.glf_t);
+  add(3, c->tab.glf_w);
+  add(4, c->tab.gll);
+  add(5, c->tab.geo);
+  add(6, c->tab.wq);
+  add(7, c->tab.B);
+  add(8, c->tab.dB);
+  add(9, c->tab.dV);
+  SN_CUDA(c, dalloc(c->d_tab, packed.size()));
+  SN_CUDA(c, cudaMemcpy(c->d_tab, packed.data(), packed.size() * 8, cudaMemcpyHostToDevice));
+  c->disc_set = true;
+  c->mat_set = false;
+  return SN_OK;
+}
+
+sn_status sn_set_quadrature(sn_ctx* c, int n_dir, const double* omega, const double* w) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, n_dir >= 1 && n_dir <= 4096, SN_EINVAL, "n_dir must be 1..4096");
+  SN_REQ(c, omega && w, SN_EINVAL, "null quadrature array");
+  cudaSetDevice(c->device);
+  std::vector<double> ho(n_dir * 3), hw(n_dir);
+  if (is_device_ptr(omega)) SN_CUDA(c, cudaMemcpy(ho.data(), omega, ho.size() * 8, cudaMemcpyDeviceToHost));
+  else std::memcpy(ho.data(), omega, ho.size() * 8);
+  if (is_device_ptr(w)) SN_CUDA(c, cudaMemcpy(hw.data(), w, hw.size() * 8, cudaMemcpyDeviceToHost));
+  else std::memcpy(hw.data(), w, hw.size() * 8);
+  for (int d = 0; d < n_dir; ++d) {
+    SN_REQ(c, std::isfinite(hw[d]) && hw[d] > 0.0, SN_EINVAL, "quadrature weights must be positive");
+    for (int k = 0; k < 3; ++k) SN_REQ(c, std::isfinite(ho[d * 3 + k]), SN_EINVAL, "non-finite direction");
+  }
+  free_graph_state(c);
+  c->M = n_dir;
+  c->h_omega.swap(ho);
+  c->h_w.swap(hw);
+  SN_CUDA(c, dalloc(c->d_omega, c->h_omega.size()));
+  SN_CUDA(c, dalloc(c->d_w, c->h_w.size()));
+  SN_CUDA(c, cudaMemcpy(c->d_omega, c->h_omega.data(), c->h_omega.size() * 8, cudaMemcpyHostToDevice));
+  SN_CUDA(c, cudaMemcpy(c->d_w, c->h_w.data(), c->h_w.size() * 8, cudaMemcpyHostToDevice));
+  c->quad_set = true;
+  c->mat_set = false;
+  return SN_OK;
+}
+
+namespace {
+sn_status upload(sn_ctx* c, double*& dst, const double* src, size_t n, bool check_pos, bool allow_zero) {
+  std::vector<double> h(n);
+  if (is_device_ptr(src)) SN_CUDA(c, cudaMemcpy(h.data(), src, n * 8, cudaMemcpyDeviceToHost));
+  else std::memcpy(h.data(), src, n * 8);
+  for (double v : h) {
+    SN_REQ(c, std::isfinite(v), SN_EINVAL, "non-finite material or source value");
+    if (check_pos) SN_REQ(c, allow_zero ? v >= 0.0 : v > 0.0, SN_EINVAL, "cross section out of range");
+  }
+  SN_CUDA(c, dalloc(dst, n));
+  SN_CUDA(c, cudaMemcpy(dst, h.data(), n * 8, cudaMemcpyHostToDevice));
+  return SN_OK;
+}
+}  // namespace
+
+sn_status sn_set_materials(sn_ctx* c, const double* sigma_t, const double* sigma_s, const double* q,
+                           const double* q_dir, const double* psi_inc) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->mesh_set && c->disc_set && c->quad_set, SN_ESTATE, "mesh, discretization and quadrature first");
+  SN_REQ(c, sigma_t && sigma_s, SN_EINVAL, "null cross sections");
+  cudaSetDevice(c->device);
+  sn_status st;
+  if ((st = upload(c, c->d_sig_t, sigma_t, c->E, true, false)) != SN_OK) return st;
+  if ((st = upload(c, c->d_sig_s, sigma_s, c->E, true, true)) != SN_OK) return st;
+  if (q) {
+    if ((st = upload(c, c->d_q, q, (size_t)c->E * c->N, false, false)) != SN_OK) return st;
+  } else {
+    SN_CUDA(c, dalloc(c->d_q, (size_t)c->E * c->N));
+    SN_CUDA(c, cudaMemset(c->d_q, 0, (size_t)c->E * c->N * 8));
+  }
+  dfree(c->d_qdir);
+  dfree(c->d_psi_inc);
+  if (q_dir && (st = upload(c, c->d_qdir, q_dir, (size_t)c->M * c->E * c->N, false, false)) != SN_OK) return st;
+  if (psi_inc && c->n_bdr > 0 &&
+      (st = upload(c, c->d_psi_inc, psi_inc, (size_t)c->M * c->n_bdr * c->Nf, false, false)) != SN_OK)
+    return st;
+  // sigma_t enters the graph (siginvface weights): rebuild it
+  if (c->graph_ready) {
+    free_graph_state(c);
+  }
+  c->mat_set = true;
+  return SN_OK;
+}
+
+namespace {
+
+sn_status ensure_buffers(sn_ctx* c) {
+  const size_t npsi = (size_t)c->M * c->E * c->N, nphi = (size_t)c->E * c->N;
+  for (auto& p : c->d_psi)
+    if (!p) SN_CUDA(c, dalloc(p, npsi));
+  if (!c->d_phi) SN_CUDA(c, dalloc(c->d_phi, nphi));
+  if (!c->d_phi2) SN_CUDA(c, dalloc(c->d_phi2, nphi));
+  if (!c->d_src) SN_CUDA(c, dalloc(c->d_src, nphi));
+  return SN_OK;
+}
+
+sn_status ensure_stage(sn_ctx* c, int slot) {
+  if (!c->d_stage[slot]) SN_CUDA(c, dalloc(c->d_stage[slot], (size_t)c->M * c->E * c->N));
+  return SN_OK;
+}
+
+}  // namespace
+
+sn_status sn_build_graph(sn_ctx* c, int weighting, int exact_max, sn_graph_stats* stats) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->mat_set, SN_ESTATE, "sn_set_materials first");
+  SN_REQ(c, weighting >= 0 && weighting <= 2, SN_EINVAL, "weighting must be 0, 1 or 2");
+  SN_REQ(c, exact_max >= 1 && exact_max <= 16, SN_EINVAL, "exact_max must be 1..16");
+  cudaSetDevice(c->device);
+  free_graph_state(c);
+  cudaStream_t s = c->stream;
+  sn_graph_stats gs{};
+  cudaEvent_t ev[5];
+  for (auto& x : ev) SN_CUDA(c, cudaEventCreate(&x));
+  const int64_t E = c->E, M = c->M;
+  const int nfc = 2 * c->dim;
+  // geometric factors
+  SN_CUDA(c, dalloc(c->d_elem, (size_t)E * c->blk));
+  SN_CUDA(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
+  SN_CUDA(c, cudaEventRecord(ev[0], s));
+  DevProblem P = c->dev();
+  SN_CUDA(c, launch_geometry(P, c->d_elem, c->d_flag, s));
+  c->launches++;
+  SN_CUDA(c, dalloc(c->d_elem32, (size_t)E * c->blk));
+  P = c->dev();
+  SN_CUDA(c, launch_elem_to_fp32(P, c->d_elem32, s));
+  c->launches++;
+  SN_CUDA(c, cudaEventRecord(ev[1], s));
+  int bad = 0;
+  SN_CUDA(c, cudaMemcpyAsync(&bad, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SN_CUDA(c, cudaStreamSynchronize(s));
+  if (bad) {
+    set_err(c, "invalid mesh: det J <= 0 at a volume quadrature point");
+    free_graph_state(c);
+    return SN_EMESH;
+  }
+  // edge weights and face modes
+  const int64_t nI = (int64_t)c->h_iface.size() / 5, nB = (int64_t)c->h_bface.size() / 2;
+  double *d_zo = nullptr, *d_zn = nullptr, *d_lu = nullptr;
+  int32_t* d_perm = nullptr;
+  SN_CUDA(c, dalloc(c->d_facecode, (size_t)M * E));
+  SN_CUDA(c, cudaMemsetAsync(c->d_facecode, 0, (size_t)M * E * 4, s));
+  SN_CUDA(c, dalloc(d_zo, std::max<size_t>(1, nI * M)));
+  SN_CUDA(c, dalloc(d_zn, std::max<size_t>(1, nI * M)));
+  if (weighting == SN_WEIGHT_SIGINVFACE) {
+    SN_CUDA(c, dalloc(d_lu, (size_t)E * c->N * c->N));
+    SN_CUDA(c, dalloc(d_perm, (size_t)E * c->N));
+    SN_CUDA(c, launch_mass_lu(P, d_lu, d_perm, s));
+    c->launches++;
+  }
+  SN_CUDA(c, launch_weights(P, c->d_iface, nI, weighting, d_lu, d_perm, d_zo, d_zn, c->d_facecode, s));
+  SN_CUDA(c, launch_bdr_modes(P, c->d_bface, nB, c->d_facecode, s));
+  c->launches += 2;
+  SN_CUDA(c, cudaEventRecord(ev[2], s));
+  std::vector<double> zo(nI * M), zn(nI * M);
+  std::vector<uint32_t> fc((size_t)M * E);
+  if (nI > 0) {
+    SN_CUDA(c, cudaMemcpyAsync(zo.data(), d_zo, zo.size() * 8, cudaMemcpyDeviceToHost, s));
+    SN_CUDA(c, cudaMemcpyAsync(zn.data(), d_zn, zn.size() * 8, cudaMemcpyDeviceToHost, s));
+  }
+  SN_CUDA(c, cudaMemcpyAsync(fc.data(), c->d_facecode, fc.size() * 4, cudaMemcpyDeviceToHost, s));
+  SN_CUDA(c, cudaStreamSynchronize(s));
+  dfree(d_zo);
+  dfree(d_zn);
+  dfree(d_lu);
+  dfree(d_perm);
+  // host: SCC + FAS per direction (independent directions in parallel threads)
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<std::vector<int32_t>> rem_dir(M);
+  std::vector<FasStats> fst(M);
+  std::vector<int64_t> narcs(M, 0);
+  const int* ifc = c->h_iface.data();
+  auto work = [&](int64_t d0, int64_t d1) {
+    for (int64_t d = d0; d < d1; ++d) {
+      std::vector<int32_t> src, dst, fidx, side;
+      std::vector<double> z;
+      for (int64_t i = 0; i < nI; ++i) {
+        const int32_t o = ifc[i * 5], f = ifc[i * 5 + 1], n = ifc[i * 5 + 2], fn = ifc[i * 5 + 3];
+        if (face_mode(fc[d * E + o], f) != MODE_NONE) {   // owner depends on neighbour
+          src.push_back(n);
+          dst.push_back(o);
+          z.push_back(zo[i * M + d]);
+          fidx.push_back((int32_t)i);
+          side.push_back(0);
+        }
+        if (face_mode(fc[d * E + n], fn) != MODE_NONE) {  // neighbour depends on owner
+          src.push_back(o);
+          dst.push_back(n);
+          z.push_back(zn[i * M + d]);
+          fidx.push_back((int32_t)i);
+          side.push_back(1);
+        }
+      }
+      narcs[d] = (int64_t)src.size();
+      std::vector<uint8_t> removed;
+      fst[d] = break_cycles(E, src, dst, z, exact_max, removed);
+      for (size_t k = 0; k < src.size(); ++k)
+        if (removed[k]) {
+          const int64_t i = fidx[k];
+          const int32_t e = dst[k];
+          const int f = side[k] == 0 ? ifc[i * 5 + 1] : ifc[i * 5 + 3];
+          rem_dir[d].push_back(e);
+          rem_dir[d].push_back(src[k]);
+          fc[d * E + e] |= 1u << (16 + f);
+        }
+    }
+  };
+  {
+    unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)M));
+    std::vector<std::thread> th;
+    int64_t chunk = (M + nt - 1) / nt;
+    for (unsigned t = 0; t < nt; ++t) {
+      int64_t a = t * chunk, b = std::min<int64_t>(M, a + chunk);
+      if (a < b) th.emplace_back(work, a, b);
+    }
+    for (auto& t : th) t.join();
+  }
+  gs.ms_fas = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  c->h_removed.clear();
+  for (int64_t d = 0; d < M; ++d) {
+    std::vector<std::pair<int32_t, int32_t>> rr;
+    for (size_t k = 0; k < rem_dir[d].size(); k += 2) rr.push_back({rem_dir[d][k], rem_dir[d][k + 1]});
+    std::sort(rr.begin(), rr.end());
+    for (auto& x : rr) c->h_removed.insert(c->h_removed.end(), {(int32_t)d, x.first, x.second});
+    gs.n_arcs += narcs[d];
+    gs.n_scc += fst[d].n_scc;
+    gs.max_scc = std::max(gs.max_scc, fst[d].max_scc);
+  }
+  c->n_removed = (int64_t)c->h_removed.size() / 3;
+  gs.n_removed = c->n_removed;
+  SN_CUDA(c, cudaMemcpyAsync(c->d_facecode, fc.data(), fc.size() * 4, cudaMemcpyHostToDevice, s));
+  // levels (device) and work lists
+  SN_CUDA(c, cudaEventRecord(ev[3], s));
+  SN_CUDA(c, dalloc(c->d_levels, (size_t)M * E));
+  SN_CUDA(c, launch_levels_init(P, c->d_levels, s));
+  c->launches++;
+  int64_t rounds = 0;
+  while (true) {
+    SN_CUDA(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
+    for (int k = 0; k < 8; ++k) {
+      SN_CUDA(c, launch_levels_relax(P, c->d_facecode, c->d_levels, c->d_flag, s));
+      c->launches++;
+    }
+    int changed = 0;
+    SN_CUDA(c, cudaMemcpyAsync(&changed, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SN_CUDA(c, cudaStreamSynchronize(s));
+    rounds += 8;
+    if (!changed) break;
+    if (rounds > E + 16) {
+      set_err(c, "level scheduling did not converge: kept graph is cyclic");
+      free_graph_state(c);
+      return SN_ESTATE;
+    }
+  }
+  std::vector<int32_t> lv((size_t)M * E);
+  SN_CUDA(c, cudaMemcpyAsync(lv.data(), c->d_levels, lv.size() * 4, cudaMemcpyDeviceToHost, s));
+  SN_CUDA(c, cudaStreamSynchronize(s));
+  int32_t Lmax = 0;
+  for (int32_t v : lv) Lmax = std::max(Lmax, v);
+  c->level_off.assign(Lmax + 2, 0);
+  for (int32_t v : lv) c->level_off[v + 1]++;
+  for (int32_t L = 0; L <= Lmax; ++L) c->level_off[L + 1] += c->level_off[L];
+  std::vector<int32_t> pairs((size_t)M * E);
+  {
+    std::vector<int64_t> pos(c->level_off.begin(), c->level_off.end() - 1);
+    for (int64_t e = 0; e < E; ++e)
+      for (int64_t d = 0; d < M; ++d) pairs[pos[lv[d * E + e]]++] = (int32_t)(e * M + d);
+  }
+  SN_CUDA(c, dalloc(c->d_pairs, pairs.size()));
+  SN_CUDA(c, cudaMemcpyAsync(c->d_pairs, pairs.data(), pairs.size() * 4, cudaMemcpyHostToDevice, s));
+  // partially-inflow blocks
+  std::vector<int32_t> moff((size_t)M * E);
+  int64_t nm = 0;
+  for (size_t k = 0; k < fc.size(); ++k) {
+    moff[k] = (int32_t)nm;
+    for (int f = 0; f < nfc; ++f) nm += (face_mode(fc[k], f) == MODE_MIXED);
+  }
+  c->n_mixed = nm;
+  SN_CUDA(c, dalloc(c->d_mixed_off, moff.size()));
+  SN_CUDA(c, cudaMemcpyAsync(c->d_mixed_off, moff.data(), moff.size() * 4, cudaMemcpyHostToDevice, s));
+  SN_CUDA(c, dalloc(c->d_mixedB, (size_t)std::max<int64_t>(1, nm) * c->Nf * c->Nf));
+  SN_CUDA(c, dalloc(c->d_mixedB32, (size_t)std::max<int64_t>(1, nm) * c->Nf * c->Nf));
+  if (nm > 0) {
+    SN_CUDA(c, launch_mixed_blocks(P, c->d_iface, nI, c->d_bface, nB, c->d_facecode, c->d_mixed_off, c->d_mixedB,
+                                   c->d_mixedB32, s));
+    c->launches++;
+  }
+  SN_CUDA(c, cudaEventRecord(ev[4], s));
+  SN_CUDA(c, cudaStreamSynchronize(s));
+  float ms;
+  cudaEventElapsedTime(&ms, ev[0], ev[1]);
+  gs.ms_geometry = ms;
+  cudaEventElapsedTime(&ms, ev[1], ev[2]);
+  gs.ms_weights = ms;
+  cudaEventElapsedTime(&ms, ev[3], ev[4]);
+  gs.ms_levels = ms;
+  for (auto& x : ev) cudaEventDestroy(x);
+  gs.max_level = Lmax;
+  gs.n_mixed_faces = nm;
+  sn_status st = ensure_buffers(c);
+  if (st != SN_OK) return st;
+  c->graph_ready = true;
+  if (stats) *stats = gs;
+  return SN_OK;
+}
+
+sn_status sn_get_graph(sn_ctx* c, int64_t* n_removed, int32_t* removed, int64_t cap, int32_t* levels) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
+  cudaSetDevice(c->device);
+  if (n_removed) *n_removed = c->n_removed;
+  if (removed) {
+    SN_REQ(c, cap >= c->n_removed, SN_EINVAL, "removed buffer too small");
+    std::memcpy(removed, c->h_removed.data(), c->h_removed.size() * 4);
+  }
+  if (levels) {
+    SN_CUDA(c, cudaMemcpyAsync(levels, c->d_levels, (size_t)c->M * c->E * 4, cudaMemcpyDefault, c->stream));
+    SN_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return SN_OK;
+}
+
+namespace {
+
+// All level launches of one sweep, replayed from a captured CUDA graph when the stream
+// allows capture (not the legacy default stream).
+sn_status run_levels(sn_ctx* c, int prec, const double* psi_old, double* psi_new) {
+  DevProblem P = c->dev();
+  const int64_t L = (int64_t)c->level_off.size() - 1;
+  auto launch_all = [&]() -> cudaError_t {
+    for (int64_t l = 0; l < L; ++l) {
+      const int64_t off = c->level_off[l], cnt = c->level_off[l + 1] - off;
+      cudaError_t e = launch_sweep_level(P, prec, c->d_pairs + off, cnt, c->d_facecode, c->d_mixed_off,
+                                         c->d_mixedB, c->d_mixedB32, c->d_src, psi_old, psi_new, c->stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  c->launches += L;
+  if (c->stream == nullptr) {
+    SN_CUDA(c, launch_all());
+    return SN_OK;
+  }
+  sn_ctx::GraphKey key{prec, psi_old, psi_new};
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    if (c->graphs.size() >= 8) {
+      for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+      c->graphs.clear();
+    }
+    cudaGraph_t g;
+    SN_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = launch_all();
+    cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    SN_CUDA(c, le);
+    SN_CUDA(c, ee);
+    cudaGraphExec_t ge;
+    cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    SN_CUDA(c, ie);
+    it = c->graphs.emplace(key, ge).first;
+  }
+  SN_CUDA(c, cudaGraphLaunch(it->second, c->stream));
+  return SN_OK;
+}
+
+const double* stage_in(sn_ctx* c, const double* p, size_t n, int slot, sn_status& st) {
+  st = SN_OK;
+  if (!p || is_device_ptr(p)) return p;
+  if ((st = ensure_stage(c, slot)) != SN_OK) return nullptr;
+  cudaError_t e = cudaMemcpyAsync(c->d_stage[slot], p, n * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) {
+    set_err(c, std::string("cudaMemcpyAsync H2D: ") + cudaGetErrorString(e));
+    st = SN_ECUDA;
+    return nullptr;
+  }
+  return c->d_stage[slot];
+}
+
+}  // namespace
+
+sn_status sn_sweep(sn_ctx* c, const double* phi_in, const double* psi_old, double* psi_new, int precision) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
+  SN_REQ(c, phi_in && psi_old && psi_new, SN_EINVAL, "null array");
+  SN_REQ(c, (const void*)psi_old != (const void*)psi_new, SN_EINVAL, "psi_new must not alias psi_old");
+  SN_REQ(c, precision == SN_PREC_FP64 || precision == SN_PREC_MIXED, SN_EINVAL, "unknown precision");
+  cudaSetDevice(c->device);
+  const size_t npsi = (size_t)c->M * c->E * c->N, nphi = (size_t)c->E * c->N;
+  sn_status st;
+  const double* dphi = stage_in(c, phi_in, nphi, 0, st);
+  if (st != SN_OK) return st;
+  const double* dold = stage_in(c, psi_old, npsi, 1, st);
+  if (st != SN_OK) return st;
+  const bool host_out = !is_device_ptr(psi_new);
+  double* dnew = psi_new;
+  if (host_out) {
+    if ((st = ensure_stage(c, 2)) != SN_OK) return st;
+    dnew = c->d_stage[2];
+  }
+  DevProblem P = c->dev();
+  SN_CUDA(c, launch_source(P, dphi, c->d_src, c->stream));
+  c->launches++;
+  if ((st = run_levels(c, precision, dold, dnew)) != SN_OK) return st;
+  if (host_out) {
+    SN_CUDA(c, cudaMemcpyAsync(psi_new, dnew, npsi * 8, cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (host_out || !is_device_ptr(phi_in) || !is_device_ptr(psi_old)) SN_CUDA(c, cudaStreamSynchronize(c->stream));
+  return SN_OK;
+}
+
+sn_status sn_moment(sn_ctx* c, const double* psi, const double* phi_prev, double* phi_out, double* residual) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
+  SN_REQ(c, psi && phi_out, SN_EINVAL, "null array");
+  cudaSetDevice(c->device);
+  const size_t npsi = (size_t)c->M * c->E * c->N, nphi = (size_t)c->E * c->N;
+  sn_status st;
+  const double* dpsi = stage_in(c, psi, npsi, 1, st);
+  if (st != SN_OK) return st;
+  const double* dprev = stage_in(c, phi_prev, nphi, 0, st);
+  if (st != SN_OK) return st;
+  const bool host_out = !is_device_ptr(phi_out);
+  double* dout = host_out ? c->d_phi2 : phi_out;
+  SN_CUDA(c, cudaMemsetAsync(c->d_red, 0, 2 * sizeof(unsigned long long), c->stream));
+  DevProblem P = c->dev();
+  SN_CUDA(c, launch_moment(P, dpsi, dprev, dout, c->d_src, c->d_red, c->stream));
+  c->launches++;
+  unsigned long long red[2];
+  SN_CUDA(c, cudaMemcpyAsync(red, c->d_red, sizeof(red), cudaMemcpyDeviceToHost, c->stream));
+  if (host_out) SN_CUDA(c, cudaMemcpyAsync(phi_out, dout, nphi * 8, cudaMemcpyDeviceToHost, c->stream));
+  SN_CUDA(c, cudaStreamSynchronize(c->stream));
+  double diff, mag;
+  std::memcpy(&diff, &red[0], 8);
+  std::memcpy(&mag, &red[1], 8);
+  if (residual) *residual = mag > 0.0 ? diff / mag : (diff > 0.0 ? INFINITY : 0.0);
+  return SN_OK;
+}
+
+sn_status sn_si_begin(sn_ctx* c, const double* phi0) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
+  cudaSetDevice(c->device);
+  const size_t npsi = (size_t)c->M * c->E * c->N, nphi = (size_t)c->E * c->N;
+  cudaStream_t s = c->stream;
+  if (phi0) SN_CUDA(c, cudaMemcpyAsync(c->d_phi, phi0, nphi * 8, cudaMemcpyDefault, s));
+  else SN_CUDA(c, cudaMemsetAsync(c->d_phi, 0, nphi * 8, s));
+  SN_CUDA(c, cudaMemsetAsync(c->d_psi[0], 0, npsi * 8, s));
+  DevProblem P = c->dev();
+  SN_CUDA(c, launch_source(P, c->d_phi, c->d_src, s));
+  c->launches++;
+  SN_CUDA(c, cudaStreamSynchronize(s));
+  c->si_cur = 0;
+  c->si_ready = true;
+  return SN_OK;
+}
+
+sn_status sn_si_step(sn_ctx* c, int precision, double* residual, float* ms_sweep) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->graph_ready && c->si_ready, SN_ESTATE, "sn_si_begin first");
+  SN_REQ(c, precision == SN_PREC_FP64 || precision == SN_PREC_MIXED, SN_EINVAL, "unknown precision");
+  cudaSetDevice(c->device);
+  cudaStream_t s = c->stream;
+  if (ms_sweep && !c->ev_a) {
+    SN_CUDA(c, cudaEventCreate(&c->ev_a));
+    SN_CUDA(c, cudaEventCreate(&c->ev_b));
+  }
+  const int cur = c->si_cur;
+  if (ms_sweep) SN_CUDA(c, cudaEventRecord(c->ev_a, s));
+  sn_status st = run_levels(c, precision, c->d_psi[cur], c->d_psi[cur ^ 1]);
+  if (st != SN_OK) return st;
+  if (ms_sweep) SN_CUDA(c, cudaEventRecord(c->ev_b, s));
+  SN_CUDA(c, cudaMemsetAsync(c->d_red, 0, 2 * sizeof(unsigned long long), s));
+  DevProblem P = c->dev();
+  SN_CUDA(c, launch_moment(P, c->d_psi[cur ^ 1], c->d_phi, c->d_phi2, c->d_src, c->d_red, s));
+  c->launches++;
+  unsigned long long red[2];
+  SN_CUDA(c, cudaMemcpyAsync(red, c->d_red, sizeof(red), cudaMemcpyDeviceToHost, s));
+  SN_CUDA(c, cudaStreamSynchronize(s));
+  double diff, mag;
+  std::memcpy(&diff, &red[0], 8);
+  std::memcpy(&mag, &red[1], 8);
+  if (residual) *residual = mag > 0.0 ? diff / mag : (diff > 0.0 ? INFINITY : 0.0);
+  if (ms_sweep) SN_CUDA(c, cudaEventElapsedTime(ms_sweep, c->ev_a, c->ev_b));
+  std::swap(c->d_phi, c->d_phi2);
+  c->si_cur = cur ^ 1;
+  return SN_OK;
+}
+
+sn_status sn_si_result(sn_ctx* c, double* phi_out, double* psi_out) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->graph_ready && c->si_ready, SN_ESTATE, "sn_si_begin first");
+  cudaSetDevice(c->device);
+  const size_t npsi = (size_t)c->M * c->E * c->N, nphi = (size_t)c->E * c->N;
+  if (phi_out) SN_CUDA(c, cudaMemcpyAsync(phi_out, c->d_phi, nphi * 8, cudaMemcpyDefault, c->stream));
+  if (psi_out) SN_CUDA(c, cudaMemcpyAsync(psi_out, c->d_psi[c->si_cur], npsi * 8, cudaMemcpyDefault, c->stream));
+  SN_CUDA(c, cudaStreamSynchronize(c->stream));
+  return SN_OK;
+}
+
+sn_status sn_source_iterate(sn_ctx* c, double tol, int max_iter, int precision, const double* phi0, double* phi_out,
+                            double* psi_out, sn_si_stats* stats, double* history, int history_cap) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
+  SN_REQ(c, max_iter >= 1 && tol > 0.0, SN_EINVAL, "max_iter >= 1 and tol > 0 required");
+  SN_REQ(c, precision == SN_PREC_FP64 || precision == SN_PREC_MIXED, SN_EINVAL, "unknown precision");
+  auto t0 = std::chrono::steady_clock::now();
+  sn_status st = sn_si_begin(c, phi0);
+  if (st != SN_OK) return st;
+  double res = INFINITY;
+  int it = 0;
+  bool conv = false;
+  for (it = 1; it <= max_iter; ++it) {
+    if ((st = sn_si_step(c, precision, &res, nullptr)) != SN_OK) return st;
+    if (history && it <= history_cap) history[it - 1] = res;
+    if (res < tol) {
+      conv = true;
+      break;
+    }
+  }
+  if (it > max_iter) it = max_iter;
+  if ((st = sn_si_result(c, phi_out, psi_out)) != SN_OK) return st;
+  if (stats) {
+    stats->iters = it;
+    stats->converged = conv ? 1 : 0;
+    stats->residual = res;
+    stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (!conv) {
+    set_err(c, "source iteration did not reach tol within max_iter");
+    return SN_ENOTCONVERGED;
+  }
+  return SN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,173 @@
+// Internal declarations of the snsweep library: the context, host tables and the kernel
+// launchers implemented in geom.cu (element factors), graph.cu (edge weights, levels) and
+// sweep.cu (lagged sweep, scalar-flux moment and scattering source).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <map>
+#include "../../include/snsweep.h"
+
+namespace sn {
+
+constexpr int MAX_DIM = 3;
+constexpr int MAX_P = 3;
+constexpr int MAX_R = 3;
+constexpr int MAX_NF1 = 8;          // max 1D face GL points (p + r <= 6) ... headroom
+
+// Face-code word per (direction, element): bits [2f, 2f+1] = inflow mode of local face f
+// (0 none, 1 whole face inflow, 2 partial inflow), bit 16 + f = arc through face f lagged.
+constexpr uint32_t MODE_NONE = 0, MODE_PURE = 1, MODE_MIXED = 2;
+__host__ __device__ inline uint32_t face_mode(uint32_t code, int f) { return (code >> (2 * f)) & 3u; }
+__host__ __device__ inline bool face_lagged(uint32_t code, int f) { return (code >> (16 + f)) & 1u; }
+
+// 1D tables computed on the host (tables.cpp) and uploaded.
+struct Tables {
+  int nv = 0, nf = 0, p = 0, r = 0, dim = 0, N = 0, Nf = 0, Nv = 0, Q = 0;
+  std::vector<double> glv_t, glv_w;     // volume GL nodes/weights on [0,1]
+  std::vector<double> glf_t, glf_w;     // face GL nodes/weights on [0,1]
+  std::vector<double> gll;              // DG nodes
+  std::vector<double> geo;              // geometry nodes a/r
+  std::vector<double> wq;               // [Q] tensor volume weights
+  std::vector<double> B;                // [Q][N] DG basis at volume points
+  std::vector<double> dB;               // [Q][N][dim] reference gradients
+  std::vector<double> dV;               // [Q][Nv][dim] geometry basis reference gradients
+};
+
+void gauss_legendre(int n, std::vector<double>& t, std::vector<double>& w);
+void gll_nodes(int p, std::vector<double>& x);
+double lagrange(const double* nodes, int n, int j, double x);
+double lagrange_deriv(const double* nodes, int n, int j, double x);
+void build_tables(Tables& T, int dim, int p, int r);
+
+// Feedback arc set on one direction's graph (fas.cpp).  Arcs (src -> dst, weight) with
+// dst depending on src.  removed[i] set to 1 for lagged arcs.  Returns SCC stats.
+struct FasStats { int64_t n_scc = 0; int32_t max_scc = 0; };
+FasStats break_cycles(int64_t n, const std::vector<int32_t>& src, const std::vector<int32_t>& dst,
+                      const std::vector<double>& z, int exact_max, std::vector<uint8_t>& removed);
+
+// Device-side view of a problem passed to kernels by value.
+struct DevProblem {
+  int dim, r, p, N, Nf, nv, nf, K, Q, Nv, M;
+  int64_t E;
+  int64_t n_bdr;
+  const double* ctrl;        // [E][Nv][dim]
+  const int64_t* nbr;        // [E][2dim]
+  const int32_t* nbr_face;   // [E][2dim]
+  const int32_t* orient;     // [E][2dim]
+  const int64_t* bdr_index;  // [E][2dim] boundary-face number or -1
+  const double* omega;       // [M][3]
+  const double* w;           // [M]
+  const double* sig_t;       // [E]
+  const double* sig_s;       // [E]
+  const double* q;           // [E][N]
+  const double* q_dir;       // [M][E][N] or null
+  const double* psi_inc;     // [M][n_bdr][Nf] or null
+  const double* tab;         // packed tables (see TabOffsets)
+  int off_glv_t, off_glv_w, off_glf_t, off_glf_w, off_gll, off_geo, off_wq, off_B, off_dB, off_dV;
+  const double* elem;        // [E][blk] element factors
+  int64_t blk;               // doubles per element block
+  const float* elem32;       // [E][blk] FP32 copy (mixed form) or null
+};
+
+// Element factor block layout: S^0..S^{dim-1} (N x N, S^k[m][n] = int du_m/dx_k u_n),
+// mass M (N x N), then face matrices FN[f][k][i][j] = int_face w N_k phi_i phi_j with the
+// element's own outward scaled normal (2 dim faces x dim components x Nf x Nf).
+inline int64_t elem_block_doubles(int dim, int N, int Nf) {
+  return (int64_t)(dim + 1) * N * N + (int64_t)2 * dim * dim * Nf * Nf;
+}
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_geometry(const DevProblem& P, double* elem, int* bad_flag, cudaStream_t s);
+cudaError_t launch_elem_to_fp32(const DevProblem& P, float* elem32, cudaStream_t s);
+cudaError_t launch_mass_lu(const DevProblem& P, double* lu, int32_t* perm, cudaStream_t s);
+cudaError_t launch_weights(const DevProblem& P, const int32_t* iface, int64_t n_iface, int weighting,
+                           const double* mt_lu, const int32_t* mt_perm, double* z_o, double* z_n,
+                           uint32_t* facecode, cudaStream_t s);
+cudaError_t launch_bdr_modes(const DevProblem& P, const int32_t* bface, int64_t n_bface, uint32_t* facecode,
+                             cudaStream_t s);
+cudaError_t launch_mixed_blocks(const DevProblem& P, const int32_t* iface, int64_t n_iface,
+                                const int32_t* bface, int64_t n_bface, const uint32_t* facecode,
+                                const int32_t* mixed_off, double* mixedB, float* mixedB32, cudaStream_t s);
+cudaError_t launch_levels_init(const DevProblem& P, int32_t* levels, cudaStream_t s);
+cudaError_t launch_levels_relax(const DevProblem& P, const uint32_t* facecode, int32_t* levels, int* changed,
+                                cudaStream_t s);
+cudaError_t launch_source(const DevProblem& P, const double* phi, double* src, cudaStream_t s);
+cudaError_t launch_moment(const DevProblem& P, const double* psi, const double* phi_prev, double* phi_out,
+                          double* src, unsigned long long* red, cudaStream_t s);
+cudaError_t launch_sweep_level(const DevProblem& P, int precision, const int32_t* pairs, int64_t count,
+                               const uint32_t* facecode, const int32_t* mixed_off, const double* mixedB,
+                               const float* mixedB32, const double* src, const double* psi_old, double* psi_new,
+                               cudaStream_t s);
+
+}  // namespace sn
+
+struct sn_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int64_t launches = 0;
+  // mesh (host copies)
+  int dim = 0, r = 0;
+  int64_t E = 0;
+  std::vector<double> h_ctrl;
+  std::vector<int64_t> h_nbr;
+  std::vector<int32_t> h_nbr_face, h_orient;
+  std::vector<int64_t> h_bdr_index;
+  std::vector<int32_t> h_iface;     // [n_iface][5]: owner, f, nbr, f_nbr, orient
+  std::vector<int32_t> h_bface;     // [n_bface][2]: e, f
+  int64_t n_bdr = 0;
+  bool mesh_set = false;
+  // discretization
+  int p = 0, K = 2, N = 0, Nf = 0;
+  bool disc_set = false;
+  sn::Tables tab;
+  // quadrature
+  int M = 0;
+  std::vector<double> h_omega, h_w;
+  bool quad_set = false;
+  bool mat_set = false;
+  // device memory
+  double *d_ctrl = nullptr, *d_omega = nullptr, *d_w = nullptr, *d_tab = nullptr;
+  int64_t* d_nbr = nullptr;
+  int64_t* d_bdr_index = nullptr;
+  int32_t *d_nbr_face = nullptr, *d_orient = nullptr, *d_iface = nullptr, *d_bface = nullptr;
+  double *d_sig_t = nullptr, *d_sig_s = nullptr, *d_q = nullptr, *d_qdir = nullptr, *d_psi_inc = nullptr;
+  double* d_elem = nullptr;
+  float* d_elem32 = nullptr;
+  int64_t blk = 0;
+  int tab_off[10] = {0};
+  // graph
+  bool graph_ready = false;
+  uint32_t* d_facecode = nullptr;
+  int32_t* d_mixed_off = nullptr;
+  double* d_mixedB = nullptr;
+  float* d_mixedB32 = nullptr;
+  int64_t n_mixed = 0;
+  int32_t* d_levels = nullptr;
+  int32_t* d_pairs = nullptr;
+  std::vector<int64_t> level_off;
+  std::vector<int32_t> h_removed;   // (d, e, e') triples
+  int64_t n_removed = 0;
+  // iteration state
+  double* d_psi[2] = {nullptr, nullptr};
+  double *d_phi = nullptr, *d_phi2 = nullptr, *d_src = nullptr;
+  double* d_stage[3] = {nullptr, nullptr, nullptr};   // host-pointer staging
+  unsigned long long* d_red = nullptr;
+  int* d_flag = nullptr;
+  int si_cur = 0;                 // which psi buffer holds the current iterate
+  bool si_ready = false;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  // CUDA graphs of the per-level sweep launches, keyed by (precision, psi_old, psi_new)
+  struct GraphKey {
+    int prec; const void* a; const void* b;
+    bool operator<(const GraphKey& o) const {
+      if (prec != o.prec) return prec < o.prec;
+      if (a != o.a) return a < o.a;
+      return b < o.b;
+    }
+  };
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  sn::DevProblem dev() const;
+};

@@ -1,0 +1,151 @@
+// Device helpers for the one-off geometry and graph kernels: Lagrange bases, face
+// coordinates, orientation maps and face normals.  The arithmetic order is the one the
+// graph's bit-exact contract fixes (products left to right from 1.0, sums in increasing
+// index from 0.0); translation units that need exact reproducibility compile with
+// -fmad=false so that no multiply-add is contracted.
+#pragma once
+#include "common.h"
+
+namespace sn {
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+__device__ inline const double* tabp(const DevProblem& P, int off) { return P.tab + off; }
+
+__device__ inline double dlagrange(const double* nodes, int n, int j, double x) {
+  double v = 1.0;
+  for (int k = 0; k < n; ++k)
+    if (k != j) v = v * ((x - nodes[k]) / (nodes[j] - nodes[k]));
+  return v;
+}
+
+__device__ inline double dlagrange_deriv(const double* nodes, int n, int j, double x) {
+  double d = 0.0;
+  for (int k = 0; k < n; ++k) {
+    if (k == j) continue;
+    double t = 1.0 / (nodes[j] - nodes[k]);
+    for (int l = 0; l < n; ++l)
+      if (l != j && l != k) t = t * ((x - nodes[l]) / (nodes[j] - nodes[l]));
+    d = d + t;
+  }
+  return d;
+}
+
+// Reference coordinates of face f at face coordinates (s0, s1).
+__device__ inline void face_ref(int dim, int f, double s0, double s1, double* xi) {
+  int axis = f >> 1, side = f & 1;
+  int o0 = (axis == 0) ? 1 : 0;
+  int o1 = (axis == 2) ? 1 : 2;
+  xi[axis] = (double)side;
+  xi[o0] = s0;
+  if (dim == 3) xi[o1] = s1;
+}
+
+// Owner face coordinates -> neighbour face coordinates (orientation code bits: 4 swap,
+// 1 flip first, 2 flip second).
+__device__ inline void orient_map(int dim, int code, double s0, double s1, double& t0, double& t1) {
+  if (dim == 2) {
+    t0 = (code & 1) ? 1.0 - s0 : s0;
+    t1 = 0.0;
+    return;
+  }
+  double u0 = (code & 4) ? s1 : s0;
+  double u1 = (code & 4) ? s0 : s1;
+  t0 = (code & 1) ? 1.0 - u0 : u0;
+  t1 = (code & 2) ? 1.0 - u1 : u1;
+}
+
+// Same map on face-node grid indices (symmetric node sets: 1 - node_i = node_{p-i}).
+__host__ __device__ inline void orient_map_idx(int dim, int code, int p, int i, int j, int& t0, int& t1) {
+  if (dim == 2) {
+    t0 = (code & 1) ? p - i : i;
+    t1 = 0;
+    return;
+  }
+  int u0 = (code & 4) ? j : i;
+  int u1 = (code & 4) ? i : j;
+  t0 = (code & 1) ? p - u0 : u0;
+  t1 = (code & 2) ? p - u1 : u1;
+}
+
+// Volume node index of face node (i, j) of face f for order p.
+__host__ __device__ constexpr int face_vol_index(int dim, int p, int f, int i, int j) {
+  const int axis = f >> 1, side = f & 1;
+  const int n = p + 1;
+  const int t0 = axis == 0 ? side * p : i;
+  const int t1 = axis == 1 ? side * p : (axis == 0 ? i : (dim == 3 ? j : 0));
+  const int t2 = dim == 3 ? (axis == 2 ? side * p : j) : 0;
+  return t0 + n * (t1 + n * t2);
+}
+
+// Outward face normal scaled by the face Jacobian (cof(J) n_hat) at face coordinates of
+// local face f, from the element's control points ctrl [Nv][dim].  Tangents
+// T_b = sum over the face's control points (increasing index) of x_m * dv_m/dxi_b, where
+// dv is the product over axes (left to right from 1.0) with the face-axis factor 1.
+// 2D axis 0: (T1[1], -T1[0]); axis 1: (-T0[1], T0[0]); 3D axis a: T_{a+1} x T_{a+2} (cyclic),
+// component i = u_{i+1} v_{i+2} - u_{i+2} v_{i+1}; side 0 negates.
+__device__ inline void face_normal(int dim, int r, const double* geo, const double* ctrl, int f, double s0,
+                                   double s1, double* nvec) {
+  const int axis = f >> 1, side = f & 1;
+  double xi[3];
+  face_ref(dim, f, s0, s1, xi);
+  const int n1 = r + 1;
+  const int Nv = (dim == 2) ? n1 * n1 : n1 * n1 * n1;
+  int tb[2];
+  tb[0] = (axis + 1) % dim;
+  tb[1] = (axis + 2) % dim;
+  const int ntan = dim - 1;
+  double T[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  for (int m = 0; m < Nv; ++m) {
+    int mi[3];
+    mi[0] = m % n1;
+    mi[1] = (m / n1) % n1;
+    mi[2] = (dim == 3) ? m / (n1 * n1) : 0;
+    if (mi[axis] != side * r) continue;        // other control points contribute exact zeros
+    for (int t = 0; t < ntan; ++t) {
+      const int b = tb[t];
+      double dv = 1.0;
+      for (int k = 0; k < dim; ++k) {
+        double fac;
+        if (k == axis) fac = 1.0;
+        else if (k == b) fac = dlagrange_deriv(geo, n1, mi[k], xi[k]);
+        else fac = dlagrange(geo, n1, mi[k], xi[k]);
+        dv = dv * fac;
+      }
+      for (int c = 0; c < dim; ++c) T[t][c] = T[t][c] + ctrl[m * dim + c] * dv;
+    }
+  }
+  if (dim == 2) {
+    const double* t = T[0];
+    if (axis == 0) {
+      nvec[0] = t[1];
+      nvec[1] = -t[0];
+    } else {
+      nvec[0] = -t[1];
+      nvec[1] = t[0];
+    }
+  } else {
+    const double* u = T[0];
+    const double* v = T[1];
+    for (int c = 0; c < 3; ++c) {
+      int a = (c + 1) % 3, b = (c + 2) % 3;
+      nvec[c] = u[a] * v[b] - u[b] * v[a];
+    }
+  }
+  if (side == 0)
+    for (int c = 0; c < dim; ++c) nvec[c] = -nvec[c];
+}
+
+__device__ inline double dot_omega(int dim, const double* om, const double* v) {
+  double g = om[0] * v[0];
+  for (int k = 1; k < dim; ++k) g = g + om[k] * v[k];
+  return g;
+}
+
+// Face-node basis values at face coordinates: l_i(t0) (2D), l_i(t0) l_j(t1) (3D).
+__device__ inline double face_basis(int dim, const double* gll, int np1, int fn, double t0, double t1) {
+  if (dim == 2) return dlagrange(gll, np1, fn, t0);
+  return dlagrange(gll, np1, fn % np1, t0) * dlagrange(gll, np1, fn / np1, t1);
+}
+
+}  // namespace sn

@@ -1,0 +1,492 @@
+// Upwind dependency graph on the device (Sec. 3): per (face, direction) the face quadrature
+// of this direction, the upwind coupling blocks Fbar of both sides and the edge weights
+// (unity / face = max|Fbar| / siginvface = max|M_t^{-1} Fbar|, eq. 22); the inflow mode of every
+// (element, face, direction); the inflow blocks of partially-inflow faces for the sweep; and
+// the longest-path levels of the kept acyclic graph.
+//
+// This translation unit is compiled with -fmad=false and follows, operation by operation,
+// the order of the CPU oracle's graph stage, so that weights -- and therefore the removed arc
+// set and the levels -- are reproduced bit for bit.
+#include "devmath.cuh"
+
+namespace sn {
+
+namespace {
+
+struct PointData {
+  double s0, s1, w;
+};
+
+// 2D: breakpoints of the split at the sign changes of g(s) = Omega . n(s) (degree <= 2).
+__device__ void split_2d(const DevProblem& P, const double* ctrl, int f, const double* om, double* brk) {
+  const double* geo = tabp(P, P.off_geo);
+  double n0[3], nh[3], n1[3];
+  face_normal(2, P.r, geo, ctrl, f, 0.0, 0.0, n0);
+  face_normal(2, P.r, geo, ctrl, f, 0.5, 0.0, nh);
+  face_normal(2, P.r, geo, ctrl, f, 1.0, 0.0, n1);
+  const double g0 = dot_omega(2, om, n0), gh = dot_omega(2, om, nh), g1 = dot_omega(2, om, n1);
+  const double c0 = g0;
+  const double c2 = 2.0 * ((g0 - 2.0 * gh) + g1);
+  const double c1 = (g1 - g0) - c2;
+  double ra = 2.0, rb = 2.0;     // 2.0 = no root
+  if (c2 == 0.0) {
+    if (c1 != 0.0) ra = -c0 / c1;
+  } else {
+    const double disc = c1 * c1 - (4.0 * c2) * c0;
+    if (disc >= 0.0) {
+      const double sq = sqrt(disc);
+      const double qq = -0.5 * (c1 + (c1 >= 0.0 ? sq : -sq));
+      ra = qq / c2;
+      if (qq != 0.0) rb = c0 / qq;
+    }
+  }
+  ra = (ra > 0.0 && ra < 1.0) ? ra : 1.0;
+  rb = (rb > 0.0 && rb < 1.0) ? rb : 1.0;
+  brk[0] = 0.0;
+  brk[1] = fmin(ra, rb);
+  brk[2] = fmax(ra, rb);
+  brk[3] = 1.0;
+}
+
+__device__ inline int face_npoints(const DevProblem& P) {
+  return (P.dim == 2) ? 3 * P.nf : P.K * P.K * P.nf * P.nf;
+}
+
+__device__ inline PointData face_point(const DevProblem& P, const double* brk, int q) {
+  const double* t = tabp(P, P.off_glf_t);
+  const double* wt = tabp(P, P.off_glf_w);
+  const int nf = P.nf;
+  PointData pd;
+  if (P.dim == 2) {
+    const int piece = q / nf, i = q % nf;
+    const double lo = brk[piece], hi = brk[piece + 1];
+    const double ln = hi - lo;
+    pd.s0 = lo + ln * t[i];
+    pd.s1 = 0.0;
+    pd.w = ln * wt[i];
+  } else {
+    const int K = P.K;
+    const int i = q % nf, j = (q / nf) % nf, u = (q / (nf * nf)) % K, v = q / (nf * nf * K);
+    pd.s0 = ((double)u + t[i]) / (double)K;
+    pd.s1 = ((double)v + t[j]) / (double)K;
+    pd.w = (wt[i] / (double)K) * (wt[j] / (double)K);
+  }
+  return pd;
+}
+
+// Per-point data of one (face, direction) into shared memory; a = max(-g,0) w (owner
+// receiving) and max(g,0) w (other side receiving); basis values of both sides' face nodes.
+// Layout per point: [a_o, a_n, phi_o[Nf], phi_n[Nf]].
+__device__ void fill_points(const DevProblem& P, const double* ctrl, int f, int code, bool has_nbr,
+                            const double* om, double* sp, int lane) {
+  double brk[4] = {0.0, 1.0, 1.0, 1.0};
+  if (P.dim == 2) split_2d(P, ctrl, f, om, brk);
+  const int np = face_npoints(P);
+  const int Nf = P.Nf, np1 = P.p + 1;
+  const int stride = 2 + 2 * Nf;
+  const double* geo = tabp(P, P.off_geo);
+  const double* gll = tabp(P, P.off_gll);
+  for (int q = lane; q < np; q += 32) {
+    PointData pd = face_point(P, brk, q);
+    double nv[3];
+    face_normal(P.dim, P.r, geo, ctrl, f, pd.s0, pd.s1, nv);
+    const double g = dot_omega(P.dim, om, nv);
+    const double mg = -g;
+    double* o = sp + q * stride;
+    o[0] = (mg > 0.0 ? mg : 0.0) * pd.w;
+    o[1] = (g > 0.0 ? g : 0.0) * pd.w;
+    for (int i = 0; i < Nf; ++i) o[2 + i] = face_basis(P.dim, gll, np1, i, pd.s0, pd.s1);
+    if (has_nbr) {
+      double t0, t1;
+      orient_map(P.dim, code, pd.s0, pd.s1, t0, t1);
+      for (int i = 0; i < Nf; ++i) o[2 + Nf + i] = face_basis(P.dim, gll, np1, i, t0, t1);
+    }
+  }
+  __syncwarp();
+}
+
+// Block entry (i, j): sum_q (a_q phi_r_i(q)) phi_u_j(q), q ascending from 0.0.
+__device__ inline double block_entry(const double* sp, int np, int stride, int aoff, int roff, int uoff, int i,
+                                     int j) {
+  double acc = 0.0;
+  for (int q = 0; q < np; ++q) {
+    const double* o = sp + q * stride;
+    acc = acc + (o[aoff] * o[roff + i]) * o[uoff + j];
+  }
+  return acc;
+}
+
+__device__ inline double warp_max(double v) {
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+
+__device__ void copy_ctrl(const DevProblem& P, int64_t e, double* dst, int lane) {
+  const int n = P.Nv * P.dim;
+  for (int t = lane; t < n; t += 32) dst[t] = P.ctrl[e * n + t];
+  __syncwarp();
+}
+
+// max |M_t^{-1} Fbar_full| over the Nf nonzero columns; Fbar rows at the receiving element's
+// face-node volume indices.  Column c solved by lane c with the plain pivoted LU order.
+__device__ double siginv_weight(const DevProblem& P, const double* fbar, int64_t recv, int recv_face,
+                                const double* lu, const int32_t* perm, int lane) {
+  const int N = P.N, Nf = P.Nf;
+  double best = 0.0;
+  if (lane < Nf) {
+    const double* L = lu + recv * N * N;
+    const int32_t* pm = perm + recv * N;
+    double y[27];
+    double b[27];
+    for (int i = 0; i < N; ++i) b[i] = 0.0;
+    for (int i = 0; i < Nf; ++i) {
+      const int vi = face_vol_index(P.dim, P.p, recv_face, i % (P.p + 1), i / (P.p + 1));
+      b[vi] = fbar[i * Nf + lane];
+    }
+    for (int i = 0; i < N; ++i) y[i] = b[pm[i]];
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < i; ++j) y[i] = y[i] - L[i * N + j] * y[j];
+    for (int i = N - 1; i >= 0; --i) {
+      for (int j = i + 1; j < N; ++j) y[i] = y[i] - L[i * N + j] * y[j];
+      y[i] = y[i] / L[i * N + i];
+    }
+    for (int i = 0; i < N; ++i) best = fmax(best, fabs(y[i]));
+  }
+  return warp_max(best);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ sigma_t mass LU
+// M_t = sigma_t * M, M_mn = sum_q ((w_q |J_q|) u_m(q)) u_n(q) in increasing q; J from the
+// tabulated geometry gradients summed over all control points in increasing index.
+__global__ void mass_lu_kernel(DevProblem P, double* __restrict__ lu, int32_t* __restrict__ perm) {
+  extern __shared__ double sh[];
+  const int64_t e = blockIdx.x;
+  const int N = P.N, Q = P.Q, Nv = P.Nv, dim = P.dim;
+  double* wdet = sh;          // [Q]
+  double* A = sh + Q;         // [N][N]
+  __shared__ int32_t pv[32];
+  __shared__ int piv_s;
+  const double* wq = tabp(P, P.off_wq);
+  const double* B = tabp(P, P.off_B);
+  const double* dV = tabp(P, P.off_dV);
+  const double* ctrl = P.ctrl + e * Nv * dim;
+  for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int m = 0; m < Nv; ++m)
+      for (int i = 0; i < dim; ++i)
+        for (int j = 0; j < dim; ++j) J[i][j] = J[i][j] + ctrl[m * dim + i] * dV[((size_t)q * Nv + m) * dim + j];
+    double det;
+    if (dim == 2) {
+      det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    } else {
+      const double t0 = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]);
+      const double t1 = J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]);
+      const double t2 = J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+      det = (t0 - t1) + t2;
+    }
+    wdet[q] = wq[q] * det;
+  }
+  __syncthreads();
+  const double st = P.sig_t[e];
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+    const int m = t / N, n = t % N;
+    double acc = 0.0;
+    for (int q = 0; q < Q; ++q) acc = acc + ((wdet[q] * B[(size_t)q * N + m]) * B[(size_t)q * N + n]);
+    A[t] = st * acc;
+  }
+  if (threadIdx.x < N) pv[threadIdx.x] = threadIdx.x;
+  __syncthreads();
+  // Doolittle with partial pivoting (first row of largest |A[i][k]|), full row swaps.
+  for (int k = 0; k < N; ++k) {
+    if (threadIdx.x == 0) {
+      int p = k;
+      double best = fabs(A[k * N + k]);
+      for (int i = k + 1; i < N; ++i)
+        if (fabs(A[i * N + k]) > best) {
+          best = fabs(A[i * N + k]);
+          p = i;
+        }
+      piv_s = p;
+    }
+    __syncthreads();
+    const int p = piv_s;
+    if (p != k) {
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double t = A[k * N + j];
+        A[k * N + j] = A[p * N + j];
+        A[p * N + j] = t;
+      }
+      if (threadIdx.x == 0) {
+        int t = pv[k];
+        pv[k] = pv[p];
+        pv[p] = t;
+      }
+    }
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < N; i += blockDim.x) {
+      const double l = A[i * N + k] / A[k * N + k];
+      A[i * N + k] = l;
+      for (int j = k + 1; j < N; ++j) A[i * N + j] = A[i * N + j] - l * A[k * N + j];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) lu[e * N * N + t] = A[t];
+  if (threadIdx.x < N) perm[e * N + threadIdx.x] = pv[threadIdx.x];
+}
+
+cudaError_t launch_mass_lu(const DevProblem& P, double* lu, int32_t* perm, cudaStream_t s) {
+  size_t shmem = sizeof(double) * ((size_t)P.Q + (size_t)P.N * P.N);
+  mass_lu_kernel<<<(unsigned)P.E, 64, shmem, s>>>(P, lu, perm);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ edge weights
+// One warp per (interior face, direction).  iface rows: owner, f, nbr, f_nbr, orient.
+__global__ void weights_kernel(DevProblem P, const int32_t* __restrict__ iface, int64_t n_iface, int weighting,
+                               const double* __restrict__ mt_lu, const int32_t* __restrict__ mt_perm,
+                               double* __restrict__ z_o, double* __restrict__ z_n, uint32_t* facecode,
+                               int shm_per_warp) {
+  extern __shared__ double sh[];
+  const int warp_in_block = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_in_block;
+  if (item >= n_iface * P.M) return;     // whole warp exits together
+  const int64_t fi = item / P.M;
+  const int d = (int)(item % P.M);
+  const int32_t* row = iface + fi * 5;
+  const int64_t owner = row[0], nbr = row[2];
+  const int f = row[1], fn = row[3], code = row[4];
+  double* wsh = sh + (size_t)warp_in_block * shm_per_warp;
+  double* ctrl = wsh;                                   // Nv * dim
+  double* sp = ctrl + P.Nv * P.dim;                     // points
+  const int np = face_npoints(P);
+  const int Nf = P.Nf;
+  const int stride = 2 + 2 * Nf;
+  double* fb = sp + np * stride;                        // [2][Nf][Nf]
+  copy_ctrl(P, owner, ctrl, lane);
+  double om[3] = {P.omega[d * 3 + 0], P.omega[d * 3 + 1], P.omega[d * 3 + 2]};
+  fill_points(P, ctrl, f, code, true, om, sp, lane);
+  double mo = 0.0, mn = 0.0;
+  for (int t = lane; t < Nf * Nf; t += 32) {
+    const int i = t / Nf, j = t % Nf;
+    const double bo = block_entry(sp, np, stride, 0, 2, 2 + Nf, i, j);        // owner <- neighbour
+    const double bn = block_entry(sp, np, stride, 1, 2 + Nf, 2, i, j);        // neighbour <- owner
+    fb[t] = bo;
+    fb[Nf * Nf + t] = bn;
+    mo = fmax(mo, fabs(bo));
+    mn = fmax(mn, fabs(bn));
+  }
+  __syncwarp();
+  mo = warp_max(mo);
+  mn = warp_max(mn);
+  const bool eo = mo > 0.0, en = mn > 0.0;
+  double wo = 0.0, wn = 0.0;
+  if (weighting == SN_WEIGHT_UNITY) {
+    wo = eo ? 1.0 : 0.0;
+    wn = en ? 1.0 : 0.0;
+  } else if (weighting == SN_WEIGHT_FACE) {
+    wo = mo;
+    wn = mn;
+  } else {
+    wo = eo ? siginv_weight(P, fb, owner, f, mt_lu, mt_perm, lane) : 0.0;
+    wn = en ? siginv_weight(P, fb + Nf * Nf, nbr, fn, mt_lu, mt_perm, lane) : 0.0;
+  }
+  if (lane == 0) {
+    z_o[fi * P.M + d] = wo;
+    z_n[fi * P.M + d] = wn;
+    if (eo) atomicOr(&facecode[(int64_t)d * P.E + owner], (en ? MODE_MIXED : MODE_PURE) << (2 * f));
+    if (en) atomicOr(&facecode[(int64_t)d * P.E + nbr], (eo ? MODE_MIXED : MODE_PURE) << (2 * fn));
+  }
+}
+
+static int weights_shm_per_warp(const DevProblem& P) {
+  const int np = (P.dim == 2) ? 3 * P.nf : P.K * P.K * P.nf * P.nf;
+  return P.Nv * P.dim + np * (2 + 2 * P.Nf) + 2 * P.Nf * P.Nf;
+}
+
+cudaError_t launch_weights(const DevProblem& P, const int32_t* iface, int64_t n_iface, int weighting,
+                           const double* mt_lu, const int32_t* mt_perm, double* z_o, double* z_n,
+                           uint32_t* facecode, cudaStream_t s) {
+  if (n_iface == 0) return cudaSuccess;
+  const int spw = weights_shm_per_warp(P);
+  int warps = 4;
+  while (warps > 1 && (size_t)warps * spw * sizeof(double) > 96 * 1024) warps >>= 1;
+  const size_t shmem = (size_t)warps * spw * sizeof(double);
+  cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+  const int64_t items = n_iface * P.M;
+  const int64_t blocks = (items + warps - 1) / warps;
+  weights_kernel<<<(unsigned)blocks, warps * 32, shmem, s>>>(P, iface, n_iface, weighting, mt_lu, mt_perm, z_o, z_n,
+                                                            facecode, spw);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ boundary faces
+// Inflow mode of boundary faces: inflow block B_in = sum a_in phi phi, outflow part likewise.
+__global__ void bdr_modes_kernel(DevProblem P, const int32_t* __restrict__ bface, int64_t n_bface,
+                                 uint32_t* facecode, int shm_per_warp) {
+  extern __shared__ double sh[];
+  const int warp_in_block = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_in_block;
+  if (item >= n_bface * P.M) return;
+  const int64_t bi = item / P.M;
+  const int d = (int)(item % P.M);
+  const int64_t e = bface[bi * 2];
+  const int f = bface[bi * 2 + 1];
+  double* wsh = sh + (size_t)warp_in_block * shm_per_warp;
+  double* ctrl = wsh;
+  double* sp = ctrl + P.Nv * P.dim;
+  const int np = face_npoints(P);
+  const int Nf = P.Nf;
+  const int stride = 2 + 2 * Nf;
+  copy_ctrl(P, e, ctrl, lane);
+  double om[3] = {P.omega[d * 3 + 0], P.omega[d * 3 + 1], P.omega[d * 3 + 2]};
+  fill_points(P, ctrl, f, 0, false, om, sp, lane);
+  double mi = 0.0, mo = 0.0;
+  for (int t = lane; t < Nf * Nf; t += 32) {
+    const int i = t / Nf, j = t % Nf;
+    mi = fmax(mi, fabs(block_entry(sp, np, stride, 0, 2, 2, i, j)));
+    mo = fmax(mo, fabs(block_entry(sp, np, stride, 1, 2, 2, i, j)));
+  }
+  mi = warp_max(mi);
+  mo = warp_max(mo);
+  if (lane == 0 && mi > 0.0) atomicOr(&facecode[(int64_t)d * P.E + e], (mo > 0.0 ? MODE_MIXED : MODE_PURE) << (2 * f));
+}
+
+cudaError_t launch_bdr_modes(const DevProblem& P, const int32_t* bface, int64_t n_bface, uint32_t* facecode,
+                             cudaStream_t s) {
+  if (n_bface == 0) return cudaSuccess;
+  const int spw = weights_shm_per_warp(P);
+  int warps = 4;
+  while (warps > 1 && (size_t)warps * spw * sizeof(double) > 96 * 1024) warps >>= 1;
+  const size_t shmem = (size_t)warps * spw * sizeof(double);
+  cudaFuncSetAttribute(bdr_modes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+  const int64_t items = n_bface * P.M;
+  bdr_modes_kernel<<<(unsigned)((items + warps - 1) / warps), warps * 32, shmem, s>>>(P, bface, n_bface, facecode,
+                                                                                     spw);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ partial-inflow blocks
+// For every (face side, direction) with mode MIXED: B = sum_q a phi_i phi_j (receiving side's
+// own face-node basis on both indices), stored at slot mixed_off[d][e] + rank of the face
+// among e's mixed faces.
+__device__ inline int mixed_rank(uint32_t code, int f) {
+  int r = 0;
+  for (int g = 0; g < f; ++g) r += (face_mode(code, g) == MODE_MIXED);
+  return r;
+}
+
+__global__ void mixed_blocks_kernel(DevProblem P, const int32_t* __restrict__ iface, int64_t n_iface,
+                                    const int32_t* __restrict__ bface, int64_t n_bface,
+                                    const uint32_t* __restrict__ facecode, const int32_t* __restrict__ mixed_off,
+                                    double* __restrict__ mixedB, float* __restrict__ mixedB32, int shm_per_warp) {
+  extern __shared__ double sh[];
+  const int warp_in_block = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_in_block;
+  const int64_t n_faces = n_iface + n_bface;
+  if (item >= n_faces * P.M) return;
+  const int64_t fi = item / P.M;
+  const int d = (int)(item % P.M);
+  int64_t e0, e1 = -1;
+  int f0, f1 = -1, code = 0;
+  if (fi < n_iface) {
+    const int32_t* row = iface + fi * 5;
+    e0 = row[0];
+    f0 = row[1];
+    e1 = row[2];
+    f1 = row[3];
+    code = row[4];
+  } else {
+    e0 = bface[(fi - n_iface) * 2];
+    f0 = bface[(fi - n_iface) * 2 + 1];
+  }
+  const uint32_t c0 = facecode[(int64_t)d * P.E + e0];
+  const uint32_t c1 = (e1 >= 0) ? facecode[(int64_t)d * P.E + e1] : 0u;
+  const bool m0 = face_mode(c0, f0) == MODE_MIXED;
+  const bool m1 = (e1 >= 0) && face_mode(c1, f1) == MODE_MIXED;
+  if (!m0 && !m1) return;
+  double* wsh = sh + (size_t)warp_in_block * shm_per_warp;
+  double* ctrl = wsh;
+  double* sp = ctrl + P.Nv * P.dim;
+  const int np = face_npoints(P);
+  const int Nf = P.Nf;
+  const int stride = 2 + 2 * Nf;
+  copy_ctrl(P, e0, ctrl, lane);
+  double om[3] = {P.omega[d * 3 + 0], P.omega[d * 3 + 1], P.omega[d * 3 + 2]};
+  fill_points(P, ctrl, f0, code, e1 >= 0, om, sp, lane);
+  if (m0) {
+    const int64_t slot = mixed_off[(int64_t)d * P.E + e0] + mixed_rank(c0, f0);
+    for (int t = lane; t < Nf * Nf; t += 32) {
+      const double v = block_entry(sp, np, stride, 0, 2, 2, t / Nf, t % Nf);
+      mixedB[slot * Nf * Nf + t] = v;
+      mixedB32[slot * Nf * Nf + t] = (float)v;
+    }
+  }
+  if (m1) {
+    const int64_t slot = mixed_off[(int64_t)d * P.E + e1] + mixed_rank(c1, f1);
+    for (int t = lane; t < Nf * Nf; t += 32) {
+      const double v = block_entry(sp, np, stride, 1, 2 + Nf, 2 + Nf, t / Nf, t % Nf);
+      mixedB[slot * Nf * Nf + t] = v;
+      mixedB32[slot * Nf * Nf + t] = (float)v;
+    }
+  }
+}
+
+cudaError_t launch_mixed_blocks(const DevProblem& P, const int32_t* iface, int64_t n_iface, const int32_t* bface,
+                                int64_t n_bface, const uint32_t* facecode, const int32_t* mixed_off,
+                                double* mixedB, float* mixedB32, cudaStream_t s) {
+  const int64_t items = (n_iface + n_bface) * P.M;
+  if (items == 0) return cudaSuccess;
+  const int spw = weights_shm_per_warp(P);
+  int warps = 4;
+  while (warps > 1 && (size_t)warps * spw * sizeof(double) > 96 * 1024) warps >>= 1;
+  const size_t shmem = (size_t)warps * spw * sizeof(double);
+  cudaFuncSetAttribute(mixed_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+  mixed_blocks_kernel<<<(unsigned)((items + warps - 1) / warps), warps * 32, shmem, s>>>(
+      P, iface, n_iface, bface, n_bface, facecode, mixed_off, mixedB, mixedB32, spw);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ levels
+__global__ void levels_init_kernel(int32_t* levels, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    levels[i] = 0;
+}
+
+cudaError_t launch_levels_init(const DevProblem& P, int32_t* levels, cudaStream_t s) {
+  levels_init_kernel<<<1216, 256, 0, s>>>(levels, (int64_t)P.M * P.E);
+  return cudaGetLastError();
+}
+
+// level(d,e) = max over kept upwind neighbours of level + 1 (0 without kept in-arcs).  Values
+// only grow; repeated until nothing changes, this reaches the longest-path layering.
+__global__ void levels_relax_kernel(DevProblem P, const uint32_t* __restrict__ facecode, int32_t* levels,
+                                    int* changed) {
+  const int64_t n = (int64_t)P.M * P.E;
+  const int nfc = 2 * P.dim;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = i / P.E, e = i % P.E;
+    const uint32_t code = facecode[i];
+    int best = 0;
+    for (int f = 0; f < nfc; ++f) {
+      if (face_mode(code, f) == MODE_NONE || face_lagged(code, f)) continue;
+      const int64_t nb = P.nbr[e * nfc + f];
+      if (nb < 0) continue;
+      const int lv = ((volatile int32_t*)levels)[d * P.E + nb] + 1;
+      best = lv > best ? lv : best;
+    }
+    if (best > levels[i]) {
+      levels[i] = best;
+      *changed = 1;
+    }
+  }
+}
+
+cudaError_t launch_levels_relax(const DevProblem& P, const uint32_t* facecode, int32_t* levels, int* changed,
+                                cudaStream_t s) {
+  levels_relax_kernel<<<1216, 256, 0, s>>>(P, facecode, levels, changed);
+  return cudaGetLastError();
+}
+
+}  // namespace sn

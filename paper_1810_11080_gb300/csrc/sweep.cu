@@ -1,0 +1,304 @@
+// Lagged transport sweep (Sec. 3, eq. 21) and scalar-flux moment / scattering source
+// (eqs. 2 and 18) on the device.
+//
+// Sweep: one launch per wavefront level; every (element, direction) pair of the level is one
+// small dense system A psi_e = b solved by a W-lane segment of a warp (W = next power of two
+// >= N; 32/W systems per warp).  Lane i owns row i of the system in registers:
+//   A = sum_k Omega_k (S^k)^T + sigma_t M + sum_{inflow faces} B_f      (strong form of
+//       G + F_e + M_t: int (Omega.grad u_n) u_m + sigma_t int u_m u_n + oint max(-Omega.n,0) u_m u_n)
+//   b = src_e + sum_{inflow faces} B_f trace_f
+// with B_f = -Omega . FN_f on whole-inflow faces and the stored block on partially-inflow
+// faces; trace_f = the upwind neighbour's nodal values on the face (new iterate for kept
+// arcs, previous iterate for lagged ones) or the incident flux on the domain boundary.
+// Elimination: partial pivoting by a segment-wide argmax; rows are not moved, the pivot row is
+// broadcast by shuffles; back substitution in pivot order.
+#include <type_traits>
+#include "devmath.cuh"
+
+namespace sn {
+
+template <int I, int END, class F>
+__device__ __forceinline__ void static_for(F&& fn) {
+  if constexpr (I < END) {
+    fn(std::integral_constant<int, I>{});
+    static_for<I + 1, END>(fn);
+  }
+}
+
+// Volume node index of face node fj of face f (compile-time).
+template <int DIM, int P_>
+__host__ __device__ constexpr int fvi(int f, int fj) {
+  return face_vol_index(DIM, P_, f, fj % (P_ + 1), fj / (P_ + 1));
+}
+
+template <int DIM, int P_>
+struct Shape {
+  static constexpr int NP1 = P_ + 1;
+  static constexpr int N = ipow(NP1, DIM);
+  static constexpr int NF = ipow(NP1, DIM - 1);
+  static constexpr int W = N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32;
+  static constexpr int SPW = 32 / W;
+};
+
+// Face-node index of volume node i on local face f, or -1.
+template <int DIM, int P_>
+__device__ __forceinline__ int on_face(int f, int i) {
+  constexpr int n = P_ + 1;
+  const int t0 = i % n, t1 = (i / n) % n, t2 = (DIM == 3) ? i / (n * n) : 0;
+  const int axis = f >> 1, side = f & 1;
+  const int ta = axis == 0 ? t0 : (axis == 1 ? t1 : t2);
+  if (ta != side * P_) return -1;
+  const int o0 = axis == 0 ? t1 : t0;
+  const int o1 = axis == 2 ? t1 : t2;
+  return DIM == 2 ? o0 : o0 + n * o1;
+}
+
+template <int DIM, int P_>
+__global__ void __launch_bounds__(128) sweep64_kernel(DevProblem Pb, const int32_t* __restrict__ pairs,
+                                                      int64_t count, const uint32_t* __restrict__ facecode,
+                                                      const int32_t* __restrict__ mixed_off,
+                                                      const double* __restrict__ mixedB,
+                                                      const double* __restrict__ src,
+                                                      const double* psi_old, double* psi_new) {
+  using S = Shape<DIM, P_>;
+  constexpr int N = S::N, NF = S::NF, W = S::W, SPW = S::SPW, NP1 = S::NP1;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int seg = lane / W, i = lane % W;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t item = gwarp * SPW + seg;
+  const bool valid = item < count;
+  const int M = Pb.M;
+  const int64_t E = Pb.E;
+  const int32_t pr = valid ? pairs[item] : 0;
+  const int64_t e = pr / M;
+  const int d = pr % M;
+  const bool row = valid && (i < N);
+  const double om0 = Pb.omega[d * 3 + 0], om1 = Pb.omega[d * 3 + 1], om2 = Pb.omega[d * 3 + 2];
+  const double* blk = Pb.elem + e * Pb.blk;
+  double a[N];
+  double b = 0.0;
+  if (row) {
+    const double st = Pb.sig_t[e];
+    static_for<0, N>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      double v = om0 * __ldg(blk + j * N + i);
+      v = fma(om1, __ldg(blk + N * N + j * N + i), v);
+      if (DIM == 3) v = fma(om2, __ldg(blk + 2 * N * N + j * N + i), v);
+      a[j] = fma(st, __ldg(blk + DIM * N * N + j * N + i), v);
+    });
+    b = src[e * N + i];
+    if (Pb.q_dir != nullptr) {
+      const double* qd = Pb.q_dir + ((int64_t)d * E + e) * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) b = fma(__ldg(blk + DIM * N * N + i * N + j), qd[j], b);
+    }
+  } else {
+    static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = 0.0; });
+  }
+  const uint32_t code = valid ? facecode[(int64_t)d * E + e] : 0u;
+  const int mbase = (valid && (code & 0xAAAu)) ? mixed_off[(int64_t)d * E + e] : 0;
+  int mrank = 0;
+  static_for<0, 2 * DIM>([&](auto fconst) {
+    constexpr int f = decltype(fconst)::value;
+    const uint32_t mode = face_mode(code, f);
+    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+    if (mode != MODE_NONE && fi >= 0) {
+      double Brow[NF];
+      if (mode == MODE_PURE) {
+        const double* fnm = blk + (DIM + 1) * N * N + f * DIM * NF * NF + fi * NF;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) {
+          double v = om0 * __ldg(fnm + fj);
+          v = fma(om1, __ldg(fnm + NF * NF + fj), v);
+          if (DIM == 3) v = fma(om2, __ldg(fnm + 2 * NF * NF + fj), v);
+          Brow[fj] = -v;
+        }
+      } else {
+        const double* mb = mixedB + (int64_t)(mbase + mrank) * NF * NF + fi * NF;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) Brow[fj] = __ldg(mb + fj);
+      }
+      static_for<0, NF>([&](auto jconst) {
+        constexpr int fj = decltype(jconst)::value;
+        a[fvi<DIM, P_>(f, fj)] += Brow[fj];
+      });
+      const int64_t nb = Pb.nbr[e * 2 * DIM + f];
+      if (nb >= 0) {
+        const double* ps = face_lagged(code, f) ? psi_old : psi_new;
+        const int fn = Pb.nbr_face[e * 2 * DIM + f], oc = Pb.orient[e * 2 * DIM + f];
+        const double* pnb = ps + ((int64_t)d * E + nb) * N;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) {
+          int t0, t1;
+          orient_map_idx(DIM, oc, P_, fj % NP1, fj / NP1, t0, t1);
+          b = fma(Brow[fj], __ldg(pnb + face_vol_index(DIM, P_, fn, t0, t1)), b);
+        }
+      } else if (Pb.psi_inc != nullptr) {
+        const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * 2 * DIM + f]) * NF;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) b = fma(Brow[fj], __ldg(pin + fj), b);
+      }
+    }
+    if (mode == MODE_MIXED) ++mrank;
+  });
+  // ---- LU with partial pivoting within the segment
+  bool used = !row;
+  int myk = -1;
+  double myinv = 0.0;
+  int plk[N];
+  static_for<0, N>([&](auto kconst) {
+    constexpr int k = decltype(kconst)::value;
+    double v = used ? -1.0 : fabs(a[k]);
+    int idx = i;
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) {
+      const double v2 = __shfl_xor_sync(FULL, v, off, W);
+      const int i2 = __shfl_xor_sync(FULL, idx, off, W);
+      if (v2 > v || (v2 == v && i2 < idx)) {
+        v = v2;
+        idx = i2;
+      }
+    }
+    const int pl = idx;
+    plk[k] = pl;
+    const double piv = __shfl_sync(FULL, a[k], pl, W);
+    const double inv = 1.0 / piv;
+    if (i == pl && !used) {
+      used = true;
+      myk = k;
+      myinv = inv;
+    }
+    const bool elim = !used;
+    const double l = a[k] * inv;
+    static_for<k + 1, N>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      const double u = __shfl_sync(FULL, a[j], pl, W);
+      if (elim) a[j] = fma(-l, u, a[j]);
+    });
+    const double ub = __shfl_sync(FULL, b, pl, W);
+    if (elim) b = fma(-l, ub, b);
+  });
+  double x = 0.0;
+  static_for<0, N>([&](auto jconst) {
+    constexpr int j = N - 1 - decltype(jconst)::value;
+    const bool mine = (myk == j);
+    const double xl = mine ? b * myinv : 0.0;
+    const double xj = __shfl_sync(FULL, xl, plk[j], W);
+    if (mine) x = xj;
+    if (myk >= 0 && myk < j) b = fma(-a[j], xj, b);
+  });
+  if (row && myk >= 0) psi_new[((int64_t)d * E + e) * N + myk] = x;
+}
+
+template <int DIM, int P_>
+static cudaError_t launch_sweep64_t(const DevProblem& P, const int32_t* pairs, int64_t count,
+                                    const uint32_t* facecode, const int32_t* mixed_off, const double* mixedB,
+                                    const double* src, const double* psi_old, double* psi_new, cudaStream_t s) {
+  using S = Shape<DIM, P_>;
+  const int threads = 128;
+  const int64_t per_block = (threads / 32) * S::SPW;
+  const int64_t blocks = (count + per_block - 1) / per_block;
+  if (blocks == 0) return cudaSuccess;
+  sweep64_kernel<DIM, P_><<<(unsigned)blocks, threads, 0, s>>>(P, pairs, count, facecode, mixed_off, mixedB, src,
+                                                                psi_old, psi_new);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_level(const DevProblem& P, int precision, const int32_t* pairs, int64_t count,
+                               const uint32_t* facecode, const int32_t* mixed_off, const double* mixedB,
+                               const float* mixedB32, const double* src, const double* psi_old, double* psi_new,
+                               cudaStream_t s) {
+  (void)precision;
+  (void)mixedB32;
+#define SN_SWEEP_CASE(D, PP)                                                                                 \
+  if (P.dim == D && P.p == PP)                                                                               \
+    return launch_sweep64_t<D, PP>(P, pairs, count, facecode, mixed_off, mixedB, src, psi_old, psi_new, s);
+  SN_SWEEP_CASE(2, 1)
+  SN_SWEEP_CASE(2, 2)
+  SN_SWEEP_CASE(2, 3)
+  SN_SWEEP_CASE(3, 1)
+  SN_SWEEP_CASE(3, 2)
+#undef SN_SWEEP_CASE
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ moment and source
+__device__ inline void block_max2(double& a, double& b) {
+  __shared__ double ra[32], rb[32];
+  for (int off = 16; off > 0; off >>= 1) {
+    a = fmax(a, __shfl_xor_sync(0xffffffffu, a, off));
+    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, off));
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    ra[w] = a;
+    rb[w] = b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    a = l < nw ? ra[l] : 0.0;
+    b = l < nw ? rb[l] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) {
+      a = fmax(a, __shfl_xor_sync(0xffffffffu, a, off));
+      b = fmax(b, __shfl_xor_sync(0xffffffffu, b, off));
+    }
+  }
+}
+
+// phi = sum_d w_d psi_d (d ascending); residual maxima; src = M (q + sigma_s phi / (4 pi)).
+// Block = whole elements: threads (element slot, node).
+__global__ void moment_kernel(DevProblem P, const double* __restrict__ psi, const double* __restrict__ phi_prev,
+                              double* __restrict__ phi_out, double* __restrict__ src,
+                              unsigned long long* red) {
+  extern __shared__ double sphi[];
+  const int N = P.N;
+  const int epb = blockDim.x / N;
+  const int le = threadIdx.x / N, m = threadIdx.x % N;
+  const int64_t e = (int64_t)blockIdx.x * epb + le;
+  const bool ok = le < epb && e < P.E;
+  double phi = 0.0;
+  if (ok && psi != nullptr) {
+    for (int d = 0; d < P.M; ++d) phi = fma(P.w[d], __ldg(psi + ((int64_t)d * P.E + e) * N + m), phi);
+  } else if (ok) {
+    phi = phi_prev ? phi_prev[e * N + m] : 0.0;
+  }
+  if (red != nullptr) {
+    double diff = ok ? fabs(phi - (phi_prev ? phi_prev[e * N + m] : 0.0)) : 0.0;
+    double mag = ok ? fabs(phi) : 0.0;
+    block_max2(diff, mag);
+    if (threadIdx.x == 0) {
+      atomicMax(red + 0, (unsigned long long)__double_as_longlong(diff));
+      atomicMax(red + 1, (unsigned long long)__double_as_longlong(mag));
+    }
+  }
+  if (ok && phi_out != nullptr) phi_out[e * N + m] = phi;
+  sphi[threadIdx.x] = phi;
+  __syncthreads();
+  if (ok && src != nullptr) {
+    const double* Mm = P.elem + e * P.blk + (int64_t)P.dim * N * N + (int64_t)m * N;
+    const double c = P.sig_s[e] * (1.0 / (4.0 * 3.14159265358979323846));
+    const double* qe = P.q + e * N;
+    double s = 0.0;
+    for (int n = 0; n < N; ++n) s = fma(Mm[n], fma(c, sphi[le * N + n], qe[n]), s);
+    src[e * N + m] = s;
+  }
+}
+
+static unsigned moment_threads(int N) { return (unsigned)((256 / N) * N); }
+
+cudaError_t launch_moment(const DevProblem& P, const double* psi, const double* phi_prev, double* phi_out,
+                          double* src, unsigned long long* red, cudaStream_t s) {
+  const unsigned th = moment_threads(P.N);
+  const int64_t epb = th / P.N;
+  const int64_t blocks = (P.E + epb - 1) / epb;
+  moment_kernel<<<(unsigned)blocks, th, th * sizeof(double), s>>>(P, psi, phi_prev, phi_out, src, red);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_source(const DevProblem& P, const double* phi, double* src, cudaStream_t s) {
+  return launch_moment(P, nullptr, phi, nullptr, src, nullptr, s);
+}
+
+}  // namespace sn

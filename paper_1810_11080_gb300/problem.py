@@ -1,0 +1,19 @@
+"""Upload a problem description (mesh, quadrature, materials) into a Context."""
+import numpy as np
+
+from ._lib import Context
+
+
+def setup_problem(prob, device=0, stream=None, face_subdiv=2, ctx=None):
+    """Create (or reuse) a Context and pass it the arrays of an sn_inputs Problem."""
+    ctx = ctx or Context(device, stream)
+    m = prob.mesh
+    ctx.sn_set_mesh(m.dim, m.n_elem, m.r, np.ascontiguousarray(m.ctrl, dtype=np.float64),
+                    np.ascontiguousarray(m.face_nbr, dtype=np.int64), np.ascontiguousarray(m.nbr_face, dtype=np.int32),
+                    np.ascontiguousarray(m.orient, dtype=np.int32))
+    ctx.sn_set_discretization(prob.p, face_subdiv)
+    ctx.sn_set_quadrature(np.ascontiguousarray(prob.omega, dtype=np.float64),
+                          np.ascontiguousarray(prob.w, dtype=np.float64))
+    arr = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+    ctx.sn_set_materials(arr(prob.sigma_t), arr(prob.sigma_s), arr(prob.q), arr(prob.q_dir), arr(prob.psi_inc))
+    return ctx

@@ -1,0 +1,116 @@
+"""GPU parity against the CPU oracle, through the C ABI.
+
+Graph: removed arc sets and levels bit-exact.  Sweep (FP64): relative L2 <= 1e-11 on the
+angular flux of one lagged sweep from the same (phi, psi_old).  Source iteration: converged
+scalar flux to the oracle's within the iteration tolerance."""
+import numpy as np
+import pytest
+
+import sn_inputs as si
+from sn_inputs.mms import annulus_mms
+from gpu_util import oracle_graph, gpu_ctx, rel_l2, random_state
+from oracle.sweep import Sweeper
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+FP64_TOL = 1e-11
+
+CASES = {
+    "2d_sine_16": lambda: si.make_config("2d_sine_q2_p1_s4"),
+    "2d_sine_8_p2_strong": lambda: _strong_sine(8, 2),
+    "2d_smooth_10_p3_s8": lambda: si.make_config("2d_smooth_q3_p3_s8", n=10),
+    "2d_reoriented_6_p2": lambda: si.make_config("2d_sine_q2_p1_s4", n=6, p=2, reorient_seed=3),
+    "3d_twist_4_p2_s8": lambda: si.make_config("3d_twist_q2_p2_s8", n=4),
+    "3d_twist_3_p1_s4_reoriented": lambda: si.make_config("3d_twist_q2_p2_s8", n=3, p=1, sn=4, reorient_seed=9),
+    "3d_smooth_3_p2_s4": lambda: si.make_config("3d_smooth_q2_p2_s12", n=3, sn=4),
+}
+
+
+def _strong_sine(n, p):
+    prob = si.make_config("2d_sine_q2_p1_s4", n=n, p=p)
+    prob.mesh = si.structured_mesh((n, n), 2, si.disp_sine_2d(0.12 * 8 / n if n > 8 else 0.12))
+    return prob
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("weighting", ["unity", "face", "siginvface"])
+def test_graph_bit_exact(case, weighting):
+    prob = CASES[case]()
+    disc, G = oracle_graph(prob, weighting)
+    ctx, stats = gpu_ctx(prob, weighting)
+    removed, levels = ctx.sn_get_graph(len(prob.w), prob.mesh.n_elem)
+    assert np.array_equal(removed, G["removed"]), (len(removed), len(G["removed"]))
+    assert np.array_equal(levels, G["levels"])
+    assert stats["n_removed"] == len(G["removed"])
+    assert stats["max_level"] == int(G["levels"].max())
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_fp64_sweep_parity(case):
+    prob = CASES[case]()
+    disc, G = oracle_graph(prob, "face")
+    ctx, _ = gpu_ctx(prob, "face")
+    phi, psi_old = random_state(prob, seed=1)
+    ref = Sweeper(disc, G).sweep(phi, psi_old)
+    out = np.zeros_like(psi_old)
+    ctx.sn_sweep(phi, psi_old, out, 0)
+    assert rel_l2(out, ref) <= FP64_TOL, rel_l2(out, ref)
+
+
+def test_fp64_sweep_parity_with_direction_sources_and_inflow():
+    prob = si.make_config("2d_sine_q2_p1_s4", n=6, p=3)
+    prob, _f, _fac = annulus_mms(prob)
+    disc, G = oracle_graph(prob, "face")
+    ctx, _ = gpu_ctx(prob, "face")
+    phi, psi_old = random_state(prob, seed=2)
+    ref = Sweeper(disc, G).sweep(phi, psi_old)
+    out = np.zeros_like(psi_old)
+    ctx.sn_sweep(phi, psi_old, out, 0)
+    assert rel_l2(out, ref) <= FP64_TOL
+
+
+def test_fp64_sweep_device_pointers_match_host_pointers():
+    prob = si.make_config("2d_smooth_q3_p3_s8", n=8)
+    ctx, _ = gpu_ctx(prob, "face")
+    phi, psi_old = random_state(prob, seed=3)
+    out_h = np.zeros_like(psi_old)
+    ctx.sn_sweep(phi, psi_old, out_h, 0)
+    s = ctx._torch_stream
+    with torch.cuda.stream(s):
+        phi_d = torch.from_numpy(phi).cuda()
+        old_d = torch.from_numpy(psi_old).cuda()
+        new_d = torch.zeros_like(old_d)
+    s.synchronize()
+    ctx.sn_sweep(phi_d, old_d, new_d, 0)
+    s.synchronize()
+    assert np.array_equal(new_d.cpu().numpy(), out_h)
+
+
+@pytest.mark.parametrize("case", ["2d_sine_16", "3d_twist_4_p2_s8"])
+def test_source_iteration_converges_to_oracle(case):
+    prob = CASES[case]()
+    disc, G = oracle_graph(prob, "face")
+    ref = Sweeper(disc, G).source_iterate(tol=1e-11)
+    ctx, _ = gpu_ctx(prob, "face")
+    E, N = prob.mesh.n_elem, (prob.p + 1) ** prob.mesh.dim
+    phi = np.zeros((E, N))
+    res = ctx.sn_source_iterate(1e-11, 500, 0, phi_out=phi, history_cap=500)
+    assert res["converged"]
+    assert abs(res["iters"] - ref["iters"]) <= 1
+    assert rel_l2(phi, ref["phi"]) <= 1e-10
+    np.testing.assert_allclose(res["history"][:5], ref["history"][:5], rtol=1e-8)
+
+
+def test_moment_and_residual_match_numpy():
+    prob = si.make_config("2d_smooth_q3_p3_s8", n=6)
+    ctx, _ = gpu_ctx(prob, "face")
+    phi_prev, psi = random_state(prob, seed=4)
+    phi = np.zeros_like(phi_prev)
+    r = ctx.sn_moment(psi, phi_prev, phi)
+    ref = np.einsum("d,den->en", prob.w, psi)
+    assert rel_l2(phi, ref) <= 1e-14
+    assert abs(r - np.abs(ref - phi_prev).max() / np.abs(ref).max()) <= 1e-14
