@@ -115,6 +115,14 @@ def dist_env():
     return ws, rank, local
 
 
+def mixed_fp64_flops_per_update(dim, p, inflow_faces):
+    """Algorithmic FP64 flops of one update of the mixed form: FP64 row assembly (dim+1) N^2 FMA,
+    inflow-face blocks and traces, residual N^2 FMA, final sum N."""
+    N = (p + 1) ** dim
+    Nf = (p + 1) ** (dim - 1)
+    return 2 * (dim + 1) * N * N + inflow_faces * 2 * (dim + 2) * Nf * Nf + 2 * N * N + N
+
+
 def run_gpu(args):
     import torch
     import paper_1810_11080_gb300 as g
@@ -125,7 +133,7 @@ def run_gpu(args):
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
     prob = make_problem()
-    E, N, M = prob.mesh.n_elem, (prob.p + 1) ** prob.mesh.dim, len(prob.w)
+    dim, E, N, M = prob.mesh.dim, prob.mesh.n_elem, (prob.p + 1) ** prob.mesh.dim, len(prob.w)
     updates = E * M
     stream = torch.cuda.Stream(device=local)
     ctx = g.setup_problem(prob, device=local, stream=stream.cuda_stream)
@@ -137,33 +145,44 @@ def run_gpu(args):
         if ws > 1:
             torch.distributed.barrier()
 
-    # ---- resident FP64 steps (inputs in HBM)
-    ctx.sn_si_begin(None)
-    for _ in range(args.warmup):
-        ctx.sn_si_step(g.SN_PREC_FP64)
-    l0 = ctx.sn_kernel_launches()
-    clocks = ClockSampler()
-    clocks.start()
-    barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    sweep_ms = 0.0
-    for _ in range(args.steps):
-        _res, ms = ctx.sn_si_step(g.SN_PREC_FP64, time_sweep=True)
-        sweep_ms += ms
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop(local)
-    ms_total = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([ms_total], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    launches = ctx.sn_kernel_launches() - l0
-    value = ws * updates * args.steps / (ms_total / 1e3)
+    def timed_steps(prec):
+        ctx.sn_si_begin(None)
+        for _ in range(args.warmup):
+            ctx.sn_si_step(prec)
+        l0 = ctx.sn_kernel_launches()
+        clocks = ClockSampler()
+        clocks.start()
+        barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        sweep_ms = 0.0
+        for _ in range(args.steps):
+            _res, ms = ctx.sn_si_step(prec, time_sweep=True)
+            sweep_ms += ms
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop(local)
+        ms_total = ev0.elapsed_time(ev1)
+        if ws > 1:
+            t = torch.tensor([ms_total], dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms_total = float(t.item())
+        return dict(value=ws * updates * args.steps / (ms_total / 1e3), ms_per_step=ms_total / args.steps,
+                    sweep_ms_per_step=sweep_ms / args.steps, launches=int(ctx.sn_kernel_launches() - l0),
+                    clocks=clk)
+
+    forms = {"fp64": g.SN_PREC_FP64, "mixed": g.SN_PREC_MIXED}
+    meas = {k: timed_steps(v) for k, v in forms.items()}
+    head = "mixed"
+    hp = forms[head]
+    if args.quick:
+        if rank == 0:
+            return {"metric": METRIC, "quick": True,
+                    **{k: {kk: vv for kk, vv in m.items() if kk != "clocks"} for k, m in meas.items()}}
+        return None
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
     phi_h = torch.zeros((E, N), dtype=torch.float64, pin_memory=True).numpy()
@@ -171,13 +190,13 @@ def run_gpu(args):
     psa = torch.zeros((M, E, N), dtype=torch.float64, pin_memory=True).numpy()
     psb = torch.zeros((M, E, N), dtype=torch.float64, pin_memory=True).numpy()
     for _ in range(max(1, args.warmup)):
-        ctx.sn_sweep(phi_h, psa, psb, g.SN_PREC_FP64)
+        ctx.sn_sweep(phi_h, psa, psb, hp)
         ctx.sn_moment(psb, phi_h, phi2_h)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ctx.sn_sweep(phi_h, psa, psb, g.SN_PREC_FP64)
+        ctx.sn_sweep(phi_h, psa, psb, hp)
         ctx.sn_moment(psb, phi_h, phi2_h)
         phi_h, phi2_h = phi2_h, phi_h
         psa, psb = psb, psa
@@ -187,34 +206,52 @@ def run_gpu(args):
     h2d = phi_h.nbytes + psa.nbytes + psb.nbytes + phi_h.nbytes
     d2h = psb.nbytes + phi_h.nbytes
 
-    # ---- time to 1e-8 (FP64), full solve from phi = 0
-    t0 = time.perf_counter()
-    res = ctx.sn_source_iterate(1e-8, 2000, g.SN_PREC_FP64)
-    tts = time.perf_counter() - t0
+    # ---- time to a 1e-8 relative scalar-flux change, full solves from phi = 0
+    tts = {}
+    phis = {}
+    for k, prec in forms.items():
+        phis[k] = np.zeros((E, N))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ctx.sn_source_iterate(1e-8, 2000, prec, phi_out=phis[k])
+        tts[k] = dict(seconds=time.perf_counter() - t0, iters=res["iters"], converged=res["converged"])
+    diff = float(np.linalg.norm(phis["mixed"] - phis["fp64"]) / np.linalg.norm(phis["fp64"]))
 
     if rank != 0:
         return None
     pk, pk_kind = peaks()
-    inflow_faces = prob.mesh.dim          # on average dim of the 2 dim faces are inflow faces
-    fpu = flops_per_update(prob.mesh.dim, prob.p, inflow_faces)
-    achieved = fpu * updates * args.steps / (sweep_ms / 1e3) / 1e12
+    inflow_faces = dim            # on average dim of the 2 dim faces of an element are inflow faces
+
+    def roofline(kind, m):
+        fpu = flops_per_update(dim, prob.p, inflow_faces) if kind == "fp64" else \
+            mixed_fp64_flops_per_update(dim, prob.p, inflow_faces)
+        ach = fpu * updates / (m["sweep_ms_per_step"] / 1e3) / 1e12
+        kname = ("sweep64_kernel" if kind == "fp64" else "sweepmx_kernel") + f"<{dim},{prob.p}>"
+        return {"bound": "alu", "kernel": kname + " (all level launches of one sweep)", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64 pipe)", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": None, "peak_source": "FP64 DFMA microbenchmark (of measured)",
+                "fp64_flops_per_update": fpu, "sweep_ms_per_step": m["sweep_ms_per_step"]}
+
     out = {
-        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "precision": "fp64", "weighting": "face",
-                   "parallelism": "replicas" if ws > 1 else "single",
-                   "l2": "inputs larger than L2 (psi 2x84 MB + element factors 117 MB per sweep)"},
-        "roofline": {"bound": "alu", "kernel": "sweep64_kernel<2,3> (all level launches of one sweep)",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64 pipe)",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                     "peak_source": "FP64 DFMA microbenchmark (MEASURED_PEAKS.json has no FP64 entry)",
-                     "flops_per_update": fpu, "sweep_ms_per_step": sweep_ms / args.steps},
+        "metric": METRIC, "value": meas[head]["value"], "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": meas[head]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "precision": "mixed: FP32 assembly+LU, one FP64-residual refinement",
+                   "weighting": "face", "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (psi 2x84 MB + element factors 117 MB + FP32 copy 59 MB)"},
+        "roofline": roofline(head, meas[head]),
         "e2e": {"value": updates * args.steps / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches),
-        "clocks": clk,
-        "time_to_1e-8": {"fp64_s": tts, "iters": res["iters"], "converged": res["converged"]},
+        "gpu_launches": meas[head]["launches"],
+        "clocks": meas[head]["clocks"],
+        "fp64_form": {"value": meas["fp64"]["value"], "ms_per_step": meas["fp64"]["ms_per_step"], "dtype": "f64",
+                      "roofline": roofline("fp64", meas["fp64"]), "gpu_launches": meas["fp64"]["launches"],
+                      "clocks": meas["fp64"]["clocks"]},
+        "time_to_1e-8": {"fp64_s": tts["fp64"]["seconds"], "fp64_iters": tts["fp64"]["iters"],
+                         "mixed_s": tts["mixed"]["seconds"], "mixed_iters": tts["mixed"]["iters"],
+                         "speedup": tts["fp64"]["seconds"] / tts["mixed"]["seconds"],
+                         "phi_rel_l2_mixed_vs_fp64": diff,
+                         "converged": tts["fp64"]["converged"] and tts["mixed"]["converged"]},
         "graph": {"build_s": t_graph, "removed": gstats["n_removed"], "levels": gstats["max_level"] + 1,
                   "max_scc": gstats["max_scc"], "mixed_faces": gstats["n_mixed_faces"]},
         "peaks_file": pk_kind,
@@ -286,10 +323,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed steps only (no e2e, time-to-tolerance or CPU legs): for profiler launch lists")
     ap.add_argument("--cpu-sample-dirs", type=int, default=1)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -25,6 +25,18 @@ __device__ __forceinline__ void static_for(F&& fn) {
   }
 }
 
+// 1/x by Newton-Raphson (r <- r + r (1 - x r), two steps) from the hardware reciprocal
+// approximation: relative error below 2^-52 for normal x, at a third of the FP64 pipe slots of
+// an IEEE division.
+__device__ __forceinline__ double nr_rcp(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 // Volume node index of face node fj of face f (compile-time).
 template <int DIM, int P_>
 __host__ __device__ constexpr int fvi(int f, int fj) {
@@ -149,11 +161,12 @@ __global__ void __launch_bounds__(128) sweep64_kernel(DevProblem Pb, const int32
   int plk[N];
   static_for<0, N>([&](auto kconst) {
     constexpr int k = decltype(kconst)::value;
-    double v = used ? -1.0 : fabs(a[k]);
+    // argmax |a[k]| on the bit pattern (order-preserving for non-negative doubles): integer pipe
+    long long v = used ? -1LL : (__double_as_longlong(a[k]) & 0x7fffffffffffffffLL);
     int idx = i;
 #pragma unroll
     for (int off = W / 2; off > 0; off >>= 1) {
-      const double v2 = __shfl_xor_sync(FULL, v, off, W);
+      const long long v2 = __shfl_xor_sync(FULL, v, off, W);
       const int i2 = __shfl_xor_sync(FULL, idx, off, W);
       if (v2 > v || (v2 == v && i2 < idx)) {
         v = v2;
@@ -163,7 +176,7 @@ __global__ void __launch_bounds__(128) sweep64_kernel(DevProblem Pb, const int32
     const int pl = idx;
     plk[k] = pl;
     const double piv = __shfl_sync(FULL, a[k], pl, W);
-    const double inv = 1.0 / piv;
+    const double inv = nr_rcp(piv);
     if (i == pl && !used) {
       used = true;
       myk = k;
@@ -191,17 +204,199 @@ __global__ void __launch_bounds__(128) sweep64_kernel(DevProblem Pb, const int32
   if (row && myk >= 0) psi_new[((int64_t)d * E + e) * N + myk] = x;
 }
 
+// Mixed form (FP32 assembly and LU, one refinement with an FP64 residual):
+//   A32 = fl32 assembly of A from the FP32 factor copy; b in FP64;
+//   xhat = A32^{-1} fl32(b)            (partial pivoting, multipliers kept in the row)
+//   r    = b - A64 xhat                (FP64: the row of A assembled from the FP64 factors)
+//   psi  = xhat + A32^{-1} fl32(r)     (same factors, FP64 sum)
 template <int DIM, int P_>
-static cudaError_t launch_sweep64_t(const DevProblem& P, const int32_t* pairs, int64_t count,
-                                    const uint32_t* facecode, const int32_t* mixed_off, const double* mixedB,
-                                    const double* src, const double* psi_old, double* psi_new, cudaStream_t s) {
+__global__ void __launch_bounds__(128) sweepmx_kernel(DevProblem Pb, const int32_t* __restrict__ pairs,
+                                                      int64_t count, const uint32_t* __restrict__ facecode,
+                                                      const int32_t* __restrict__ mixed_off,
+                                                      const double* __restrict__ mixedB,
+                                                      const double* __restrict__ src,
+                                                      const double* psi_old, double* psi_new) {
+  using S = Shape<DIM, P_>;
+  constexpr int N = S::N, NF = S::NF, W = S::W, SPW = S::SPW, NP1 = S::NP1;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int seg = lane / W, i = lane % W;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t item = gwarp * SPW + seg;
+  const bool valid = item < count;
+  const int M = Pb.M;
+  const int64_t E = Pb.E;
+  const int32_t pr = valid ? pairs[item] : 0;
+  const int64_t e = pr / M;
+  const int d = pr % M;
+  const bool row = valid && (i < N);
+  const double om0 = Pb.omega[d * 3 + 0], om1 = Pb.omega[d * 3 + 1], om2 = Pb.omega[d * 3 + 2];
+  const float fo0 = (float)om0, fo1 = (float)om1, fo2 = (float)om2;
+  const double* blk = Pb.elem + e * Pb.blk;
+  const float* blk32 = Pb.elem32 + e * Pb.blk;
+  float a[N];
+  double a64[N];
+  double b = 0.0;
+  if (row) {
+    const double st = Pb.sig_t[e];
+    const float st32 = (float)st;
+    static_for<0, N>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      float v = fo0 * __ldg(blk32 + j * N + i);
+      v = fmaf(fo1, __ldg(blk32 + N * N + j * N + i), v);
+      if (DIM == 3) v = fmaf(fo2, __ldg(blk32 + 2 * N * N + j * N + i), v);
+      a[j] = fmaf(st32, __ldg(blk32 + DIM * N * N + j * N + i), v);
+      double w = om0 * __ldg(blk + j * N + i);
+      w = fma(om1, __ldg(blk + N * N + j * N + i), w);
+      if (DIM == 3) w = fma(om2, __ldg(blk + 2 * N * N + j * N + i), w);
+      a64[j] = fma(st, __ldg(blk + DIM * N * N + j * N + i), w);
+    });
+    b = src[e * N + i];
+    if (Pb.q_dir != nullptr) {
+      const double* qd = Pb.q_dir + ((int64_t)d * E + e) * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) b = fma(__ldg(blk + DIM * N * N + i * N + j), qd[j], b);
+    }
+  } else {
+    static_for<0, N>([&](auto jconst) {
+      a[decltype(jconst)::value] = 0.0f;
+      a64[decltype(jconst)::value] = 0.0;
+    });
+  }
+  const uint32_t code = valid ? facecode[(int64_t)d * E + e] : 0u;
+  const int mbase = (valid && (code & 0xAAAu)) ? mixed_off[(int64_t)d * E + e] : 0;
+  int mrank = 0;
+  static_for<0, 2 * DIM>([&](auto fconst) {
+    constexpr int f = decltype(fconst)::value;
+    const uint32_t mode = face_mode(code, f);
+    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+    if (mode != MODE_NONE && fi >= 0) {
+      double Brow[NF];
+      if (mode == MODE_PURE) {
+        const double* fnm = blk + (DIM + 1) * N * N + f * DIM * NF * NF + fi * NF;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) {
+          double v = om0 * __ldg(fnm + fj);
+          v = fma(om1, __ldg(fnm + NF * NF + fj), v);
+          if (DIM == 3) v = fma(om2, __ldg(fnm + 2 * NF * NF + fj), v);
+          Brow[fj] = -v;
+        }
+      } else {
+        const double* mb = mixedB + (int64_t)(mbase + mrank) * NF * NF + fi * NF;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) Brow[fj] = __ldg(mb + fj);
+      }
+      static_for<0, NF>([&](auto jconst) {
+        constexpr int fj = decltype(jconst)::value;
+        a64[fvi<DIM, P_>(f, fj)] += Brow[fj];
+        a[fvi<DIM, P_>(f, fj)] += (float)Brow[fj];
+      });
+      const int64_t nb = Pb.nbr[e * 2 * DIM + f];
+      if (nb >= 0) {
+        const double* ps = face_lagged(code, f) ? psi_old : psi_new;
+        const int fn = Pb.nbr_face[e * 2 * DIM + f], oc = Pb.orient[e * 2 * DIM + f];
+        const double* pnb = ps + ((int64_t)d * E + nb) * N;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) {
+          int t0, t1;
+          orient_map_idx(DIM, oc, P_, fj % NP1, fj / NP1, t0, t1);
+          b = fma(Brow[fj], __ldg(pnb + face_vol_index(DIM, P_, fn, t0, t1)), b);
+        }
+      } else if (Pb.psi_inc != nullptr) {
+        const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * 2 * DIM + f]) * NF;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) b = fma(Brow[fj], __ldg(pin + fj), b);
+      }
+    }
+    if (mode == MODE_MIXED) ++mrank;
+  });
+  // ---- FP32 LU with partial pivoting; the multiplier l_ik replaces a[k] of row i
+  bool used = !row;
+  int myk = -1;
+  float myinv = 0.0f;
+  int plk[N];
+  float bx = (float)b;
+  static_for<0, N>([&](auto kconst) {
+    constexpr int k = decltype(kconst)::value;
+    float v = used ? -1.0f : fabsf(a[k]);
+    int idx = i;
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) {
+      const float v2 = __shfl_xor_sync(FULL, v, off, W);
+      const int i2 = __shfl_xor_sync(FULL, idx, off, W);
+      if (v2 > v || (v2 == v && i2 < idx)) {
+        v = v2;
+        idx = i2;
+      }
+    }
+    const int pl = idx;
+    plk[k] = pl;
+    const float piv = __shfl_sync(FULL, a[k], pl, W);
+    const float inv = 1.0f / piv;
+    if (i == pl && !used) {
+      used = true;
+      myk = k;
+      myinv = inv;
+    }
+    const bool elim = !used;
+    const float l = a[k] * inv;
+    if (elim) a[k] = l;
+    static_for<k + 1, N>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      const float u = __shfl_sync(FULL, a[j], pl, W);
+      if (elim) a[j] = fmaf(-l, u, a[j]);
+    });
+    const float ub = __shfl_sync(FULL, bx, pl, W);
+    if (elim) bx = fmaf(-l, ub, bx);
+  });
+  // back substitution: unknown j is owned by lane plk[j]
+  auto back_sub = [&](float& rhs) -> float {
+    float xo = 0.0f;
+    static_for<0, N>([&](auto jconst) {
+      constexpr int j = N - 1 - decltype(jconst)::value;
+      const bool mine = (myk == j);
+      const float xl = mine ? rhs * myinv : 0.0f;
+      const float xj = __shfl_sync(FULL, xl, plk[j], W);
+      if (mine) xo = xj;
+      if (myk >= 0 && myk < j) rhs = fmaf(-a[j], xj, rhs);
+    });
+    return xo;
+  };
+  const float xhat = back_sub(bx);                 // lane plk[k] holds xhat_k
+  // ---- residual r_i = b_i - sum_j a64[i][j] xhat_j in FP64
+  const double xh64 = (double)xhat;
+  double r = b;
+  static_for<0, N>([&](auto jconst) {
+    constexpr int j = decltype(jconst)::value;
+    const double xj = __shfl_sync(FULL, xh64, plk[j], W);
+    r = fma(-a64[j], xj, r);
+  });
+  // ---- correction: forward replay of the multipliers on fl32(r), then back substitution
+  float rx = (float)r;
+  static_for<0, N>([&](auto kconst) {
+    constexpr int k = decltype(kconst)::value;
+    const float rb = __shfl_sync(FULL, rx, plk[k], W);
+    if (myk > k || (myk < 0 && row)) rx = fmaf(-a[k], rb, rx);
+  });
+  const float dx = back_sub(rx);
+  if (row && myk >= 0) psi_new[((int64_t)d * E + e) * N + myk] = xh64 + (double)dx;
+}
+
+template <int DIM, int P_>
+static cudaError_t launch_sweep_t(const DevProblem& P, int precision, const int32_t* pairs, int64_t count,
+                                  const uint32_t* facecode, const int32_t* mixed_off, const double* mixedB,
+                                  const double* src, const double* psi_old, double* psi_new, cudaStream_t s) {
   using S = Shape<DIM, P_>;
   const int threads = 128;
   const int64_t per_block = (threads / 32) * S::SPW;
   const int64_t blocks = (count + per_block - 1) / per_block;
   if (blocks == 0) return cudaSuccess;
-  sweep64_kernel<DIM, P_><<<(unsigned)blocks, threads, 0, s>>>(P, pairs, count, facecode, mixed_off, mixedB, src,
-                                                                psi_old, psi_new);
+  if (precision == SN_PREC_MIXED)
+    sweepmx_kernel<DIM, P_><<<(unsigned)blocks, threads, 0, s>>>(P, pairs, count, facecode, mixed_off, mixedB, src,
+                                                                  psi_old, psi_new);
+  else
+    sweep64_kernel<DIM, P_><<<(unsigned)blocks, threads, 0, s>>>(P, pairs, count, facecode, mixed_off, mixedB, src,
+                                                                  psi_old, psi_new);
   return cudaGetLastError();
 }
 
@@ -209,11 +404,10 @@ cudaError_t launch_sweep_level(const DevProblem& P, int precision, const int32_t
                                const uint32_t* facecode, const int32_t* mixed_off, const double* mixedB,
                                const float* mixedB32, const double* src, const double* psi_old, double* psi_new,
                                cudaStream_t s) {
-  (void)precision;
   (void)mixedB32;
 #define SN_SWEEP_CASE(D, PP)                                                                                 \
   if (P.dim == D && P.p == PP)                                                                               \
-    return launch_sweep64_t<D, PP>(P, pairs, count, facecode, mixed_off, mixedB, src, psi_old, psi_new, s);
+    return launch_sweep_t<D, PP>(P, precision, pairs, count, facecode, mixed_off, mixedB, src, psi_old, psi_new, s);
   SN_SWEEP_CASE(2, 1)
   SN_SWEEP_CASE(2, 2)
   SN_SWEEP_CASE(2, 3)
