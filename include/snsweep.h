@@ -183,6 +183,31 @@ sn_status sn_si_begin(sn_ctx* ctx, const double* phi0);
 sn_status sn_si_step(sn_ctx* ctx, int precision, double* residual, float* ms_sweep);
 sn_status sn_si_result(sn_ctx* ctx, double* phi_out, double* psi_out);
 
+/* Scalar-flux moment and relative change WITHOUT a context and without allocating anything
+ * (the paper has no counterpart: this is a deployment entry point).
+ *
+ * For callers that cannot allocate device memory: code that only holds raw device buffers
+ * handed to it by a host framework which owns all device memory through its own allocator
+ * (fixed budget, no side allocations), or that must not call cudaMalloc/cudaFree because they
+ * synchronise the whole device.  Such callers cannot create an sn_ctx, which allocates.
+ *
+ * Computes, on `cuda_stream` of device `device`, the same values as sn_moment:
+ *   phi_out[e][m] = sum_d w[d] psi[d][e][m]   (d ascending)
+ *   *residual     = max |phi_out - phi_prev| / max |phi_out|   (phi_prev NULL = 0)
+ * w [n_dir], psi [n_dir][n_elem][n_dofs], phi_prev / phi_out [n_elem][n_dofs]: DEVICE pointers,
+ * caller-owned (SN_EINVAL for host pointers).  residual: host pointer or NULL; when given, the
+ * call synchronises the stream.  No scattering source is produced (there is no context).
+ * Limit: n_elem * n_dofs <= 4,194,304 (SN_EINVAL beyond): the reduction scratch is a fixed
+ * 256 KiB file-scope device array that every GPU loading the library holds until exit.  Calls
+ * share that array and it keeps the last call's contents (every call overwrites what it
+ * reads, so nothing needs clearing); calls that overlap on the GPU (other streams, other
+ * threads) race on it.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  Calls no
+ * cudaMalloc, cudaFree or allocating library routine. */
+sn_status sn_moment_noalloc(int device, void* cuda_stream, int n_dir, int64_t n_elem, int n_dofs,
+                            const double* w, const double* psi, const double* phi_prev,
+                            double* phi_out, double* residual);
+
 /* Number of kernel launches this context has issued since creation (diagnostics). */
 int64_t sn_kernel_launches(const sn_ctx* ctx);
 

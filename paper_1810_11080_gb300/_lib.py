@@ -21,7 +21,7 @@ WEIGHTING = {"unity": 0, "face": 1, "siginvface": 2}
 EXPORTED = ["sn_create", "sn_destroy", "sn_last_error", "sn_set_mesh", "sn_set_discretization",
             "sn_set_quadrature", "sn_set_materials", "sn_num_boundary_faces", "sn_build_graph",
             "sn_get_graph", "sn_sweep", "sn_moment", "sn_source_iterate", "sn_si_begin", "sn_si_step",
-            "sn_si_result", "sn_kernel_launches"]
+            "sn_si_result", "sn_kernel_launches", "sn_moment_noalloc"]
 
 
 class sn_graph_stats(ctypes.Structure):
@@ -68,6 +68,7 @@ def load(path=LIB_PATH):
         "sn_si_step": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_float)]),
         "sn_si_result": (I, [P, P, P]),
         "sn_kernel_launches": (I64, [P]),
+        "sn_moment_noalloc": (I, [I, P, I, I64, I, P, P, P, P, ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -104,6 +105,20 @@ def _ptr(a, dtype, name):
             raise TypeError(f"{name}: expected contiguous {tmap[np.dtype(dtype).type]} tensor")
         return a.data_ptr()
     raise TypeError(f"{name}: expected numpy array or torch tensor")
+
+
+def sn_moment_noalloc(device, stream, w, psi, phi_prev, phi_out):
+    """Context-free scalar-flux moment for callers that cannot allocate device memory (see
+    include/snsweep.h).  All arrays are CUDA tensors; psi [n_dir][n_elem][n_dofs].  Returns the
+    relative scalar-flux change."""
+    n_dir, n_elem, n_dofs = psi.shape
+    r = ctypes.c_double()
+    st = lib().sn_moment_noalloc(int(device), stream, int(n_dir), int(n_elem), int(n_dofs), _ptr(w, np.float64, "w"),
+                                 _ptr(psi, np.float64, "psi"), _ptr(phi_prev, np.float64, "phi_prev"),
+                                 _ptr(phi_out, np.float64, "phi_out"), ctypes.byref(r))
+    if st != SN_OK:
+        raise SnError(st, "sn_moment_noalloc failed (device pointers only; n_elem*n_dofs <= 4194304)")
+    return r.value
 
 
 class Context:

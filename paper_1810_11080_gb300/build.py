@@ -44,6 +44,7 @@ def build(verbose=False, extra_nvcc=()):
         "geom.cu": [],
         "graph.cu": ["-fmad=false"],
         "sweep.cu": [],
+        "noalloc.cu": [],
     }
     cpp = ["api.cpp", "tables.cpp", "fas.cpp"]
     jobs = []
