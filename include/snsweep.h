@@ -58,7 +58,7 @@ typedef enum {
 } sn_status;
 
 enum { SN_WEIGHT_UNITY = 0, SN_WEIGHT_FACE = 1, SN_WEIGHT_SIGINVFACE = 2 };
-enum { SN_PREC_FP64 = 0, SN_PREC_MIXED = 1 };
+enum { SN_PREC_FP64 = 0, SN_PREC_MIXED = 1, SN_PREC_MIXED_DS = 2 };
 
 typedef struct {
   int64_t n_arcs;          /* arcs e' -> e over all directions                                 */
@@ -147,7 +147,10 @@ sn_status sn_get_graph(sn_ctx* ctx, int64_t* n_removed, int32_t* removed, int64_
  *   psi_old  [n_dir][n_elem][N]   previous angular flux (read for removed arcs only).
  *   psi_new  [n_dir][n_elem][N]   output; must not alias psi_old.
  *   precision SN_PREC_FP64: all local algebra in FP64.  SN_PREC_MIXED: FP32 assembly and LU,
- *   one refinement step whose residual is formed in FP64.
+ *   one refinement step whose residual is formed in FP64.  SN_PREC_MIXED_DS: as SN_PREC_MIXED
+ *   but the matrix row and the residual are formed in double-single arithmetic (pairs of FP32
+ *   values with error-free products and sums, ~2^-48 relative) on the FP32 pipe; only the
+ *   right-hand side and the final sum are FP64.
  * Synchronises the stream before returning when any pointer is a host pointer. */
 sn_status sn_sweep(sn_ctx* ctx, const double* phi_in, const double* psi_old, double* psi_new,
                    int precision);

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libsnsweep.so")
 
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENOTCONVERGED, SN_EMESH, SN_ESTATE = range(8)
 SN_WEIGHT_UNITY, SN_WEIGHT_FACE, SN_WEIGHT_SIGINVFACE = 0, 1, 2
-SN_PREC_FP64, SN_PREC_MIXED = 0, 1
+SN_PREC_FP64, SN_PREC_MIXED, SN_PREC_MIXED_DS = 0, 1, 2
 WEIGHTING = {"unity": 0, "face": 1, "siginvface": 2}
 
 EXPORTED = ["sn_create", "sn_destroy", "sn_last_error", "sn_set_mesh", "sn_set_discretization",

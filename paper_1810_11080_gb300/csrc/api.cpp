@@ -70,10 +70,12 @@ void free_graph_state(sn_ctx* c) {
   dfree(c->d_mixed_off);
   dfree(c->d_mixedB);
   dfree(c->d_mixedB32);
+  dfree(c->d_mixedB32lo);
   dfree(c->d_levels);
   dfree(c->d_pairs);
   dfree(c->d_elem);
   dfree(c->d_elem32);
+  dfree(c->d_elem32lo);
   c->graph_ready = false;
   c->si_ready = false;
   c->level_off.clear();
@@ -124,6 +126,7 @@ sn::DevProblem sn_ctx::dev() const {
   P.elem = d_elem;
   P.blk = blk;
   P.elem32 = d_elem32;
+  P.elem32lo = d_elem32lo;
   return P;
 }
 
@@ -429,8 +432,9 @@ sn_status sn_build_graph(sn_ctx* c, int weighting, int exact_max, sn_graph_stats
   SN_CUDA(c, launch_geometry(P, c->d_elem, c->d_flag, s));
   c->launches++;
   SN_CUDA(c, dalloc(c->d_elem32, (size_t)E * c->blk));
+  SN_CUDA(c, dalloc(c->d_elem32lo, (size_t)E * c->blk));
   P = c->dev();
-  SN_CUDA(c, launch_elem_to_fp32(P, c->d_elem32, s));
+  SN_CUDA(c, launch_elem_to_fp32(P, c->d_elem32, c->d_elem32lo, s));
   c->launches++;
   SN_CUDA(c, cudaEventRecord(ev[1], s));
   int bad = 0;
@@ -587,9 +591,10 @@ sn_status sn_build_graph(sn_ctx* c, int weighting, int exact_max, sn_graph_stats
   SN_CUDA(c, cudaMemcpyAsync(c->d_mixed_off, moff.data(), moff.size() * 4, cudaMemcpyHostToDevice, s));
   SN_CUDA(c, dalloc(c->d_mixedB, (size_t)std::max<int64_t>(1, nm) * c->Nf * c->Nf));
   SN_CUDA(c, dalloc(c->d_mixedB32, (size_t)std::max<int64_t>(1, nm) * c->Nf * c->Nf));
+  SN_CUDA(c, dalloc(c->d_mixedB32lo, (size_t)std::max<int64_t>(1, nm) * c->Nf * c->Nf));
   if (nm > 0) {
     SN_CUDA(c, launch_mixed_blocks(P, c->d_iface, nI, c->d_bface, nB, c->d_facecode, c->d_mixed_off, c->d_mixedB,
-                                   c->d_mixedB32, s));
+                                   c->d_mixedB32, c->d_mixedB32lo, s));
     c->launches++;
   }
   SN_CUDA(c, cudaEventRecord(ev[4], s));
@@ -638,7 +643,8 @@ sn_status run_levels(sn_ctx* c, int prec, const double* psi_old, double* psi_new
     for (int64_t l = 0; l < L; ++l) {
       const int64_t off = c->level_off[l], cnt = c->level_off[l + 1] - off;
       cudaError_t e = launch_sweep_level(P, prec, c->d_pairs + off, cnt, c->d_facecode, c->d_mixed_off,
-                                         c->d_mixedB, c->d_mixedB32, c->d_src, psi_old, psi_new, c->stream);
+                                         c->d_mixedB, c->d_mixedB32, c->d_mixedB32lo, c->d_src, psi_old, psi_new,
+                                         c->stream);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -691,7 +697,7 @@ sn_status sn_sweep(sn_ctx* c, const double* phi_in, const double* psi_old, doubl
   SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
   SN_REQ(c, phi_in && psi_old && psi_new, SN_EINVAL, "null array");
   SN_REQ(c, (const void*)psi_old != (const void*)psi_new, SN_EINVAL, "psi_new must not alias psi_old");
-  SN_REQ(c, precision == SN_PREC_FP64 || precision == SN_PREC_MIXED, SN_EINVAL, "unknown precision");
+  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_MIXED_DS, SN_EINVAL, "unknown precision");
   cudaSetDevice(c->device);
   const size_t npsi = (size_t)c->M * c->E * c->N, nphi = (size_t)c->E * c->N;
   sn_status st;
@@ -765,7 +771,7 @@ sn_status sn_si_begin(sn_ctx* c, const double* phi0) {
 sn_status sn_si_step(sn_ctx* c, int precision, double* residual, float* ms_sweep) {
   if (!c) return SN_EINVAL;
   SN_REQ(c, c->graph_ready && c->si_ready, SN_ESTATE, "sn_si_begin first");
-  SN_REQ(c, precision == SN_PREC_FP64 || precision == SN_PREC_MIXED, SN_EINVAL, "unknown precision");
+  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_MIXED_DS, SN_EINVAL, "unknown precision");
   cudaSetDevice(c->device);
   cudaStream_t s = c->stream;
   if (ms_sweep && !c->ev_a) {
@@ -810,7 +816,7 @@ sn_status sn_source_iterate(sn_ctx* c, double tol, int max_iter, int precision, 
   if (!c) return SN_EINVAL;
   SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
   SN_REQ(c, max_iter >= 1 && tol > 0.0, SN_EINVAL, "max_iter >= 1 and tol > 0 required");
-  SN_REQ(c, precision == SN_PREC_FP64 || precision == SN_PREC_MIXED, SN_EINVAL, "unknown precision");
+  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_MIXED_DS, SN_EINVAL, "unknown precision");
   auto t0 = std::chrono::steady_clock::now();
   sn_status st = sn_si_begin(c, phi0);
   if (st != SN_OK) return st;

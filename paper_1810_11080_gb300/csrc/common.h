@@ -68,7 +68,8 @@ struct DevProblem {
   int off_glv_t, off_glv_w, off_glf_t, off_glf_w, off_gll, off_geo, off_wq, off_B, off_dB, off_dV;
   const double* elem;        // [E][blk] element factors
   int64_t blk;               // doubles per element block
-  const float* elem32;       // [E][blk] FP32 copy (mixed form) or null
+  const float* elem32;       // [E][blk] FP32 rounding of elem (mixed forms) or null
+  const float* elem32lo;     // [E][blk] FP32 rounding of elem - elem32 (double-single form) or null
 };
 
 // Element factor block layout: S^0..S^{dim-1} (N x N, S^k[m][n] = int du_m/dx_k u_n),
@@ -80,7 +81,7 @@ inline int64_t elem_block_doubles(int dim, int N, int Nf) {
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_geometry(const DevProblem& P, double* elem, int* bad_flag, cudaStream_t s);
-cudaError_t launch_elem_to_fp32(const DevProblem& P, float* elem32, cudaStream_t s);
+cudaError_t launch_elem_to_fp32(const DevProblem& P, float* elem32, float* elem32lo, cudaStream_t s);
 cudaError_t launch_mass_lu(const DevProblem& P, double* lu, int32_t* perm, cudaStream_t s);
 cudaError_t launch_weights(const DevProblem& P, const int32_t* iface, int64_t n_iface, int weighting,
                            const double* mt_lu, const int32_t* mt_perm, double* z_o, double* z_n,
@@ -89,7 +90,8 @@ cudaError_t launch_bdr_modes(const DevProblem& P, const int32_t* bface, int64_t 
                              cudaStream_t s);
 cudaError_t launch_mixed_blocks(const DevProblem& P, const int32_t* iface, int64_t n_iface,
                                 const int32_t* bface, int64_t n_bface, const uint32_t* facecode,
-                                const int32_t* mixed_off, double* mixedB, float* mixedB32, cudaStream_t s);
+                                const int32_t* mixed_off, double* mixedB, float* mixedB32, float* mixedB32lo,
+                                cudaStream_t s);
 cudaError_t launch_levels_init(const DevProblem& P, int32_t* levels, cudaStream_t s);
 cudaError_t launch_levels_relax(const DevProblem& P, const uint32_t* facecode, int32_t* levels, int* changed,
                                 cudaStream_t s);
@@ -98,7 +100,8 @@ cudaError_t launch_moment(const DevProblem& P, const double* psi, const double* 
                           double* src, unsigned long long* red, cudaStream_t s);
 cudaError_t launch_sweep_level(const DevProblem& P, int precision, const int32_t* pairs, int64_t count,
                                const uint32_t* facecode, const int32_t* mixed_off, const double* mixedB,
-                               const float* mixedB32, const double* src, const double* psi_old, double* psi_new,
+                               const float* mixedB32, const float* mixedB32lo, const double* src,
+                               const double* psi_old, double* psi_new,
                                cudaStream_t s);
 
 }  // namespace sn
@@ -136,6 +139,7 @@ struct sn_ctx {
   double *d_sig_t = nullptr, *d_sig_s = nullptr, *d_q = nullptr, *d_qdir = nullptr, *d_psi_inc = nullptr;
   double* d_elem = nullptr;
   float* d_elem32 = nullptr;
+  float* d_elem32lo = nullptr;
   int64_t blk = 0;
   int tab_off[10] = {0};
   // graph
@@ -144,6 +148,7 @@ struct sn_ctx {
   int32_t* d_mixed_off = nullptr;
   double* d_mixedB = nullptr;
   float* d_mixedB32 = nullptr;
+  float* d_mixedB32lo = nullptr;
   int64_t n_mixed = 0;
   int32_t* d_levels = nullptr;
   int32_t* d_pairs = nullptr;

@@ -127,14 +127,19 @@ cudaError_t launch_geometry(const DevProblem& P, double* elem, int* bad, cudaStr
   return cudaGetLastError();
 }
 
-__global__ void to_fp32_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
+// FP32 split of the element factors: hi = fl32(x), lo = fl32(x - hi) (x = hi + lo to ~2^-48).
+__global__ void to_fp32_kernel(const double* __restrict__ a, float* __restrict__ hi, float* __restrict__ lo,
+                               int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float h = (float)a[i];
+    hi[i] = h;
+    lo[i] = (float)(a[i] - (double)h);
+  }
 }
 
-cudaError_t launch_elem_to_fp32(const DevProblem& P, float* elem32, cudaStream_t s) {
+cudaError_t launch_elem_to_fp32(const DevProblem& P, float* elem32, float* elem32lo, cudaStream_t s) {
   int64_t n = P.E * P.blk;
-  to_fp32_kernel<<<1216, 256, 0, s>>>(P.elem, elem32, n);
+  to_fp32_kernel<<<1216, 256, 0, s>>>(P.elem, elem32, elem32lo, n);
   return cudaGetLastError();
 }
 

@@ -380,7 +380,8 @@ __device__ inline int mixed_rank(uint32_t code, int f) {
 __global__ void mixed_blocks_kernel(DevProblem P, const int32_t* __restrict__ iface, int64_t n_iface,
                                     const int32_t* __restrict__ bface, int64_t n_bface,
                                     const uint32_t* __restrict__ facecode, const int32_t* __restrict__ mixed_off,
-                                    double* __restrict__ mixedB, float* __restrict__ mixedB32, int shm_per_warp) {
+                                    double* __restrict__ mixedB, float* __restrict__ mixedB32,
+                                    float* __restrict__ mixedB32lo, int shm_per_warp) {
   extern __shared__ double sh[];
   const int warp_in_block = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_in_block;
@@ -421,6 +422,7 @@ __global__ void mixed_blocks_kernel(DevProblem P, const int32_t* __restrict__ if
       const double v = block_entry(sp, np, stride, 0, 2, 2, t / Nf, t % Nf);
       mixedB[slot * Nf * Nf + t] = v;
       mixedB32[slot * Nf * Nf + t] = (float)v;
+      mixedB32lo[slot * Nf * Nf + t] = (float)(v - (double)(float)v);
     }
   }
   if (m1) {
@@ -429,13 +431,14 @@ __global__ void mixed_blocks_kernel(DevProblem P, const int32_t* __restrict__ if
       const double v = block_entry(sp, np, stride, 1, 2 + Nf, 2 + Nf, t / Nf, t % Nf);
       mixedB[slot * Nf * Nf + t] = v;
       mixedB32[slot * Nf * Nf + t] = (float)v;
+      mixedB32lo[slot * Nf * Nf + t] = (float)(v - (double)(float)v);
     }
   }
 }
 
 cudaError_t launch_mixed_blocks(const DevProblem& P, const int32_t* iface, int64_t n_iface, const int32_t* bface,
                                 int64_t n_bface, const uint32_t* facecode, const int32_t* mixed_off,
-                                double* mixedB, float* mixedB32, cudaStream_t s) {
+                                double* mixedB, float* mixedB32, float* mixedB32lo, cudaStream_t s) {
   const int64_t items = (n_iface + n_bface) * P.M;
   if (items == 0) return cudaSuccess;
   const int spw = weights_shm_per_warp(P);
@@ -444,7 +447,7 @@ cudaError_t launch_mixed_blocks(const DevProblem& P, const int32_t* iface, int64
   const size_t shmem = (size_t)warps * spw * sizeof(double);
   cudaFuncSetAttribute(mixed_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
   mixed_blocks_kernel<<<(unsigned)((items + warps - 1) / warps), warps * 32, shmem, s>>>(
-      P, iface, n_iface, bface, n_bface, facecode, mixed_off, mixedB, mixedB32, spw);
+      P, iface, n_iface, bface, n_bface, facecode, mixed_off, mixedB, mixedB32, mixedB32lo, spw);
   return cudaGetLastError();
 }
 

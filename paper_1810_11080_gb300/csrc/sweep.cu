@@ -382,16 +382,251 @@ __global__ void __launch_bounds__(128) sweepmx_kernel(DevProblem Pb, const int32
   if (row && myk >= 0) psi_new[((int64_t)d * E + e) * N + myk] = xh64 + (double)dx;
 }
 
+// ---- double-single (FP32 pair) arithmetic: error-free transformations (Knuth two-sum,
+// fma-based two-product), ~2^-48 relative precision on the FP32 pipe.
+__device__ __forceinline__ void ds_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// (ph, pl) = (xh + xl)(yh + yl) to first order in the low parts.
+__device__ __forceinline__ void ds_mul(float xh, float xl, float yh, float yl, float& ph, float& pl) {
+  ph = xh * yh;
+  pl = fmaf(xh, yh, -ph);
+  pl = fmaf(xh, yl, pl);
+  pl = fmaf(xl, yh, pl);
+}
+// (sh, sl) += (ph, pl), renormalised.
+__device__ __forceinline__ void ds_add(float& sh, float& sl, float ph, float pl) {
+  float t, e;
+  ds_two_sum(sh, ph, t, e);
+  e += sl + pl;
+  sh = t + e;
+  sl = e - (sh - t);
+}
+__device__ __forceinline__ void ds_split(double x, float& h, float& l) {
+  h = (float)x;
+  l = (float)(x - (double)h);
+}
+
+// Mixed form with a double-single residual: the row of A is assembled once in double-single
+// from the (hi, lo) FP32 split of the element factors; its hi part is the FP32 matrix that is
+// factored; the residual r = b - A xhat is accumulated in double-single; b stays FP64.
+template <int DIM, int P_>
+__global__ void __launch_bounds__(128) sweepds_kernel(DevProblem Pb, const int32_t* __restrict__ pairs,
+                                                      int64_t count, const uint32_t* __restrict__ facecode,
+                                                      const int32_t* __restrict__ mixed_off,
+                                                      const double* __restrict__ mixedB,
+                                                      const float* __restrict__ mixedBh,
+                                                      const float* __restrict__ mixedBl,
+                                                      const double* __restrict__ src,
+                                                      const double* psi_old, double* psi_new) {
+  using S = Shape<DIM, P_>;
+  constexpr int N = S::N, NF = S::NF, W = S::W, SPW = S::SPW, NP1 = S::NP1;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int seg = lane / W, i = lane % W;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t item = gwarp * SPW + seg;
+  const bool valid = item < count;
+  const int M = Pb.M;
+  const int64_t E = Pb.E;
+  const int32_t pr = valid ? pairs[item] : 0;
+  const int64_t e = pr / M;
+  const int d = pr % M;
+  const bool row = valid && (i < N);
+  const double om0 = Pb.omega[d * 3 + 0], om1 = Pb.omega[d * 3 + 1], om2 = Pb.omega[d * 3 + 2];
+  float oh[3], ol[3], sh, sl;
+  ds_split(om0, oh[0], ol[0]);
+  ds_split(om1, oh[1], ol[1]);
+  ds_split(om2, oh[2], ol[2]);
+  const double* blk = Pb.elem + e * Pb.blk;
+  const float* bh = Pb.elem32 + e * Pb.blk;
+  const float* bl = Pb.elem32lo + e * Pb.blk;
+  float ah[N], al[N];          // the row in double-single
+  float a[N];                  // FP32 row for the LU (starts as ah)
+  double b = 0.0;
+  if (row) {
+    ds_split(Pb.sig_t[e], sh, sl);
+    static_for<0, N>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      float h, l, ph, pl;
+      ds_mul(oh[0], ol[0], __ldg(bh + j * N + i), __ldg(bl + j * N + i), h, l);
+      ds_mul(oh[1], ol[1], __ldg(bh + N * N + j * N + i), __ldg(bl + N * N + j * N + i), ph, pl);
+      ds_add(h, l, ph, pl);
+      if (DIM == 3) {
+        ds_mul(oh[2], ol[2], __ldg(bh + 2 * N * N + j * N + i), __ldg(bl + 2 * N * N + j * N + i), ph, pl);
+        ds_add(h, l, ph, pl);
+      }
+      ds_mul(sh, sl, __ldg(bh + DIM * N * N + j * N + i), __ldg(bl + DIM * N * N + j * N + i), ph, pl);
+      ds_add(h, l, ph, pl);
+      ah[j] = h;
+      al[j] = l;
+    });
+    b = src[e * N + i];
+    if (Pb.q_dir != nullptr) {
+      const double* qd = Pb.q_dir + ((int64_t)d * E + e) * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) b = fma(__ldg(blk + DIM * N * N + i * N + j), qd[j], b);
+    }
+  } else {
+    static_for<0, N>([&](auto jconst) {
+      ah[decltype(jconst)::value] = 0.0f;
+      al[decltype(jconst)::value] = 0.0f;
+    });
+  }
+  const uint32_t code = valid ? facecode[(int64_t)d * E + e] : 0u;
+  const int mbase = (valid && (code & 0xAAAu)) ? mixed_off[(int64_t)d * E + e] : 0;
+  int mrank = 0;
+  static_for<0, 2 * DIM>([&](auto fconst) {
+    constexpr int f = decltype(fconst)::value;
+    const uint32_t mode = face_mode(code, f);
+    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+    if (mode != MODE_NONE && fi >= 0) {
+      double Brow[NF];
+      float Bh[NF], Bl[NF];
+      if (mode == MODE_PURE) {
+        const int o = (DIM + 1) * N * N + f * DIM * NF * NF + fi * NF;
+        const double* fnm = blk + o;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) {
+          double v = om0 * __ldg(fnm + fj);
+          v = fma(om1, __ldg(fnm + NF * NF + fj), v);
+          if (DIM == 3) v = fma(om2, __ldg(fnm + 2 * NF * NF + fj), v);
+          Brow[fj] = -v;
+          float h, l, ph, pl;
+          ds_mul(oh[0], ol[0], __ldg(bh + o + fj), __ldg(bl + o + fj), h, l);
+          ds_mul(oh[1], ol[1], __ldg(bh + o + NF * NF + fj), __ldg(bl + o + NF * NF + fj), ph, pl);
+          ds_add(h, l, ph, pl);
+          if (DIM == 3) {
+            ds_mul(oh[2], ol[2], __ldg(bh + o + 2 * NF * NF + fj), __ldg(bl + o + 2 * NF * NF + fj), ph, pl);
+            ds_add(h, l, ph, pl);
+          }
+          Bh[fj] = -h;
+          Bl[fj] = -l;
+        }
+      } else {
+        const int64_t o = (int64_t)(mbase + mrank) * NF * NF + fi * NF;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) {
+          Brow[fj] = __ldg(mixedB + o + fj);
+          Bh[fj] = __ldg(mixedBh + o + fj);
+          Bl[fj] = __ldg(mixedBl + o + fj);
+        }
+      }
+      static_for<0, NF>([&](auto jconst) {
+        constexpr int fj = decltype(jconst)::value;
+        constexpr int c = fvi<DIM, P_>(f, fj);
+        ds_add(ah[c], al[c], Bh[fj], Bl[fj]);
+      });
+      const int64_t nb = Pb.nbr[e * 2 * DIM + f];
+      if (nb >= 0) {
+        const double* ps = face_lagged(code, f) ? psi_old : psi_new;
+        const int fn = Pb.nbr_face[e * 2 * DIM + f], oc = Pb.orient[e * 2 * DIM + f];
+        const double* pnb = ps + ((int64_t)d * E + nb) * N;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) {
+          int t0, t1;
+          orient_map_idx(DIM, oc, P_, fj % NP1, fj / NP1, t0, t1);
+          b = fma(Brow[fj], __ldg(pnb + face_vol_index(DIM, P_, fn, t0, t1)), b);
+        }
+      } else if (Pb.psi_inc != nullptr) {
+        const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * 2 * DIM + f]) * NF;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) b = fma(Brow[fj], __ldg(pin + fj), b);
+      }
+    }
+    if (mode == MODE_MIXED) ++mrank;
+  });
+  static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = ah[decltype(jconst)::value]; });
+  // ---- FP32 LU with partial pivoting; multipliers kept in a[k]
+  bool used = !row;
+  int myk = -1;
+  float myinv = 0.0f;
+  int plk[N];
+  float bh32, bl32;
+  ds_split(b, bh32, bl32);
+  float bx = bh32;
+  static_for<0, N>([&](auto kconst) {
+    constexpr int k = decltype(kconst)::value;
+    float v = used ? -1.0f : fabsf(a[k]);
+    int idx = i;
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) {
+      const float v2 = __shfl_xor_sync(FULL, v, off, W);
+      const int i2 = __shfl_xor_sync(FULL, idx, off, W);
+      if (v2 > v || (v2 == v && i2 < idx)) {
+        v = v2;
+        idx = i2;
+      }
+    }
+    const int pl = idx;
+    plk[k] = pl;
+    const float piv = __shfl_sync(FULL, a[k], pl, W);
+    const float inv = 1.0f / piv;
+    if (i == pl && !used) {
+      used = true;
+      myk = k;
+      myinv = inv;
+    }
+    const bool elim = !used;
+    const float l = a[k] * inv;
+    if (elim) a[k] = l;
+    static_for<k + 1, N>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      const float u = __shfl_sync(FULL, a[j], pl, W);
+      if (elim) a[j] = fmaf(-l, u, a[j]);
+    });
+    const float ub = __shfl_sync(FULL, bx, pl, W);
+    if (elim) bx = fmaf(-l, ub, bx);
+  });
+  auto back_sub = [&](float& rhs) -> float {
+    float xo = 0.0f;
+    static_for<0, N>([&](auto jconst) {
+      constexpr int j = N - 1 - decltype(jconst)::value;
+      const bool mine = (myk == j);
+      const float xl = mine ? rhs * myinv : 0.0f;
+      const float xj = __shfl_sync(FULL, xl, plk[j], W);
+      if (mine) xo = xj;
+      if (myk >= 0 && myk < j) rhs = fmaf(-a[j], xj, rhs);
+    });
+    return xo;
+  };
+  const float xhat = back_sub(bx);
+  // ---- residual in double-single: r = b - sum_j (ah_j + al_j) xhat_j
+  float rh = bh32, rl = bl32;
+  static_for<0, N>([&](auto jconst) {
+    constexpr int j = decltype(jconst)::value;
+    const float xj = __shfl_sync(FULL, xhat, plk[j], W);
+    float ph = ah[j] * xj;
+    float pl = fmaf(ah[j], xj, -ph);
+    pl = fmaf(al[j], xj, pl);
+    ds_add(rh, rl, -ph, -pl);
+  });
+  float rx = rh + rl;
+  static_for<0, N>([&](auto kconst) {
+    constexpr int k = decltype(kconst)::value;
+    const float rb = __shfl_sync(FULL, rx, plk[k], W);
+    if (myk > k || (myk < 0 && row)) rx = fmaf(-a[k], rb, rx);
+  });
+  const float dx = back_sub(rx);
+  if (row && myk >= 0) psi_new[((int64_t)d * E + e) * N + myk] = (double)xhat + (double)dx;
+}
+
 template <int DIM, int P_>
 static cudaError_t launch_sweep_t(const DevProblem& P, int precision, const int32_t* pairs, int64_t count,
                                   const uint32_t* facecode, const int32_t* mixed_off, const double* mixedB,
-                                  const double* src, const double* psi_old, double* psi_new, cudaStream_t s) {
+                                  const float* mixedBh, const float* mixedBl, const double* src,
+                                  const double* psi_old, double* psi_new, cudaStream_t s) {
   using S = Shape<DIM, P_>;
   const int threads = 128;
   const int64_t per_block = (threads / 32) * S::SPW;
   const int64_t blocks = (count + per_block - 1) / per_block;
   if (blocks == 0) return cudaSuccess;
-  if (precision == SN_PREC_MIXED)
+  if (precision == SN_PREC_MIXED_DS)
+    sweepds_kernel<DIM, P_><<<(unsigned)blocks, threads, 0, s>>>(P, pairs, count, facecode, mixed_off, mixedB,
+                                                                  mixedBh, mixedBl, src, psi_old, psi_new);
+  else if (precision == SN_PREC_MIXED)
     sweepmx_kernel<DIM, P_><<<(unsigned)blocks, threads, 0, s>>>(P, pairs, count, facecode, mixed_off, mixedB, src,
                                                                   psi_old, psi_new);
   else
@@ -402,12 +637,12 @@ static cudaError_t launch_sweep_t(const DevProblem& P, int precision, const int3
 
 cudaError_t launch_sweep_level(const DevProblem& P, int precision, const int32_t* pairs, int64_t count,
                                const uint32_t* facecode, const int32_t* mixed_off, const double* mixedB,
-                               const float* mixedB32, const double* src, const double* psi_old, double* psi_new,
-                               cudaStream_t s) {
-  (void)mixedB32;
+                               const float* mixedB32, const float* mixedB32lo, const double* src,
+                               const double* psi_old, double* psi_new, cudaStream_t s) {
 #define SN_SWEEP_CASE(D, PP)                                                                                 \
   if (P.dim == D && P.p == PP)                                                                               \
-    return launch_sweep_t<D, PP>(P, precision, pairs, count, facecode, mixed_off, mixedB, src, psi_old, psi_new, s);
+    return launch_sweep_t<D, PP>(P, precision, pairs, count, facecode, mixed_off, mixedB, mixedB32, mixedB32lo, src, \
+                                 psi_old, psi_new, s);
   SN_SWEEP_CASE(2, 1)
   SN_SWEEP_CASE(2, 2)
   SN_SWEEP_CASE(2, 3)

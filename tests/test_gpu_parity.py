@@ -119,30 +119,33 @@ def test_moment_and_residual_match_numpy():
 MIXED_TOL = 1e-8     # single mixed sweep vs the FP64 oracle (FP32 LU + one FP64-residual refinement)
 
 
-@pytest.mark.parametrize("case", ["2d_sine_16", "2d_smooth_10_p3_s8", "3d_twist_4_p2_s8", "2d_reoriented_6_p2"])
-def test_mixed_sweep_accuracy(case):
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("case", ["2d_sine_16", "2d_smooth_10_p3_s8", "3d_twist_4_p2_s8", "2d_reoriented_6_p2",
+                                  "3d_twist_3_p1_s4_reoriented"])
+def test_mixed_sweep_accuracy(case, prec):
     prob = CASES[case]()
     disc, G = oracle_graph(prob, "face")
     ctx, _ = gpu_ctx(prob, "face")
     phi, psi_old = random_state(prob, seed=5)
     ref = Sweeper(disc, G).sweep(phi, psi_old)
     out = np.zeros_like(psi_old)
-    ctx.sn_sweep(phi, psi_old, out, 1)
+    ctx.sn_sweep(phi, psi_old, out, prec)
     err = rel_l2(out, ref)
-    print(f"mixed single-sweep rel L2 {case}: {err:.3e}")
+    print(f"mixed(prec={prec}) single-sweep rel L2 {case}: {err:.3e}")
     assert err <= MIXED_TOL, err
 
 
+@pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("case", ["2d_sine_16", "3d_twist_4_p2_s8"])
-def test_mixed_source_iteration_reaches_same_tolerance(case):
+def test_mixed_source_iteration_reaches_same_tolerance(case, prec):
     prob = CASES[case]()
     disc, G = oracle_graph(prob, "face")
     ref = Sweeper(disc, G).source_iterate(tol=1e-12)
     ctx, _ = gpu_ctx(prob, "face")
     E, N = prob.mesh.n_elem, (prob.p + 1) ** prob.mesh.dim
     phi = np.zeros((E, N))
-    res = ctx.sn_source_iterate(1e-8, 500, 1, phi_out=phi)
+    res = ctx.sn_source_iterate(1e-8, 500, prec, phi_out=phi)
     assert res["converged"]
     err = rel_l2(phi, ref["phi"])
-    print(f"mixed converged phi rel L2 {case}: {err:.3e} iters {res['iters']}")
+    print(f"mixed(prec={prec}) converged phi rel L2 {case}: {err:.3e} iters {res['iters']}")
     assert err <= 1e-7
