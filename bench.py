@@ -161,6 +161,7 @@ def run_gpu(args):
     t0 = time.time()
     gstats = ctx.sn_build_graph("face", 10)
     t_graph = time.time() - t0
+    ctx.sn_set_launch(g.SN_LAUNCH_DATAFLOW if args.launch == "dataflow" else g.SN_LAUNCH_LEVELS)
 
     def barrier():
         if ws > 1:
@@ -264,6 +265,7 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[head], "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "precision": PRECISION_DESC[head],
                    "weighting": "face", "parallelism": "replicas" if ws > 1 else "single",
+                   "launch": args.launch,
                    "l2": "inputs larger than L2 (psi 2x84 MB + element factors 117 MB + FP32 copy 59 MB)"},
         "roofline": roofline(head, meas[head]),
         "e2e": {"value": updates * args.steps / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": h2d,
@@ -354,6 +356,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch", default="levels", choices=["levels", "dataflow"],
+                    help="sweep schedule: one launch per level, or one persistent dataflow launch")
     ap.add_argument("--form", default="mixed_ds", choices=["fp64", "mixed", "mixed_ds"],
                     help="form reported as the headline value (all three are measured)")
     ap.add_argument("--quick", action="store_true",

@@ -59,6 +59,7 @@ typedef enum {
 
 enum { SN_WEIGHT_UNITY = 0, SN_WEIGHT_FACE = 1, SN_WEIGHT_SIGINVFACE = 2 };
 enum { SN_PREC_FP64 = 0, SN_PREC_MIXED = 1, SN_PREC_MIXED_DS = 2 };
+enum { SN_LAUNCH_LEVELS = 0, SN_LAUNCH_DATAFLOW = 1 };
 
 typedef struct {
   int64_t n_arcs;          /* arcs e' -> e over all directions                                 */
@@ -130,6 +131,17 @@ int64_t sn_num_boundary_faces(const sn_ctx* ctx);
  * weighting: SN_WEIGHT_UNITY / _FACE / _SIGINVFACE.  stats may be NULL.
  * Errors: SN_ESTATE (missing inputs), SN_EMESH (det J <= 0 somewhere). */
 sn_status sn_build_graph(sn_ctx* ctx, int weighting, int exact_max, sn_graph_stats* stats);
+
+/* Sweep schedule (no counterpart in the paper, which sweeps serially; both schedules compute
+ * the same result, since any topological order of the kept graph does [Sec. 3]).
+ *   SN_LAUNCH_LEVELS  : one kernel launch per wavefront level, replayed from a CUDA graph.
+ *   SN_LAUNCH_DATAFLOW: one persistent launch per sweep; warps take (element, direction) pairs
+ *                       from a queue in level order and wait only for the completion flags of
+ *                       their kept upwind neighbours (bounded polling: a wait that exceeds its
+ *                       limit makes the sweep return SN_ETIMEOUT instead of hanging).
+ *   blocks_per_sm: CTAs of 128 threads per SM for the dataflow grid (0 = occupancy limit).
+ * May be called at any time; applies to later sweeps. */
+sn_status sn_set_launch(sn_ctx* ctx, int mode, int blocks_per_sm);
 
 /* Copy the graph out (valid after sn_build_graph).
  *   *n_removed receives the number of removed arcs; if removed != NULL and cap >= that number,

@@ -16,12 +16,13 @@ LIB_PATH = os.path.join(_HERE, "libsnsweep.so")
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENOTCONVERGED, SN_EMESH, SN_ESTATE = range(8)
 SN_WEIGHT_UNITY, SN_WEIGHT_FACE, SN_WEIGHT_SIGINVFACE = 0, 1, 2
 SN_PREC_FP64, SN_PREC_MIXED, SN_PREC_MIXED_DS = 0, 1, 2
+SN_LAUNCH_LEVELS, SN_LAUNCH_DATAFLOW = 0, 1
 WEIGHTING = {"unity": 0, "face": 1, "siginvface": 2}
 
 EXPORTED = ["sn_create", "sn_destroy", "sn_last_error", "sn_set_mesh", "sn_set_discretization",
             "sn_set_quadrature", "sn_set_materials", "sn_num_boundary_faces", "sn_build_graph",
             "sn_get_graph", "sn_sweep", "sn_moment", "sn_source_iterate", "sn_si_begin", "sn_si_step",
-            "sn_si_result", "sn_kernel_launches", "sn_moment_noalloc"]
+            "sn_si_result", "sn_kernel_launches", "sn_moment_noalloc", "sn_set_launch"]
 
 
 class sn_graph_stats(ctypes.Structure):
@@ -68,6 +69,7 @@ def load(path=LIB_PATH):
         "sn_si_step": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_float)]),
         "sn_si_result": (I, [P, P, P]),
         "sn_kernel_launches": (I64, [P]),
+        "sn_set_launch": (I, [P, I, I]),
         "sn_moment_noalloc": (I, [I, P, I, I64, I, P, P, P, P, ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
@@ -207,6 +209,9 @@ class Context:
             self._check(s)
         return dict(status=s, iters=st.iters, converged=bool(st.converged), residual=st.residual,
                     ms_total=st.ms_total, history=hist[:min(st.iters, history_cap)].copy())
+
+    def sn_set_launch(self, mode, blocks_per_sm=0):
+        return self._check(self._lib.sn_set_launch(self._c, int(mode), int(blocks_per_sm)))
 
     def sn_si_begin(self, phi0=None):
         return self._check(self._lib.sn_si_begin(self._c, _ptr(phi0, np.float64, "phi0")))

@@ -78,6 +78,12 @@ void free_graph_state(sn_ctx* c) {
   dfree(c->d_elem32lo);
   c->graph_ready = false;
   c->si_ready = false;
+  for (auto& p : c->d_psi) dfree(p);
+  dfree(c->d_phi);
+  dfree(c->d_phi2);
+  dfree(c->d_src);
+  dfree(c->d_done);
+  for (auto& p : c->d_stage) dfree(p);
   c->level_off.clear();
   c->h_removed.clear();
   c->n_removed = 0;
@@ -179,6 +185,7 @@ void sn_destroy(sn_ctx* c) {
   dfree(c->d_phi);
   dfree(c->d_phi2);
   dfree(c->d_src);
+  dfree(c->d_done);
   for (auto& p : c->d_stage) dfree(p);
   dfree(c->d_red);
   dfree(c->d_flag);
@@ -401,6 +408,7 @@ sn_status ensure_buffers(sn_ctx* c) {
   if (!c->d_phi) SN_CUDA(c, dalloc(c->d_phi, nphi));
   if (!c->d_phi2) SN_CUDA(c, dalloc(c->d_phi2, nphi));
   if (!c->d_src) SN_CUDA(c, dalloc(c->d_src, nphi));
+  if (!c->d_done) SN_CUDA(c, dalloc(c->d_done, (size_t)c->M * c->E));
   return SN_OK;
 }
 
@@ -568,10 +576,16 @@ sn_status sn_build_graph(sn_ctx* c, int weighting, int exact_max, sn_graph_stats
   SN_CUDA(c, cudaStreamSynchronize(s));
   int32_t Lmax = 0;
   for (int32_t v : lv) Lmax = std::max(Lmax, v);
+  // Work list: pairs e*M+d sorted by (level, e, d); every level padded with -1 entries to a
+  // multiple of the systems per warp, so that no warp ever holds pairs of two levels (a pair
+  // may depend on the previous level; a warp must never wait on itself).
+  const int W = c->N <= 4 ? 4 : c->N <= 8 ? 8 : c->N <= 16 ? 16 : 32;
+  const int spw = 32 / W;
+  std::vector<int64_t> cnt(Lmax + 1, 0);
+  for (int32_t v : lv) cnt[v]++;
   c->level_off.assign(Lmax + 2, 0);
-  for (int32_t v : lv) c->level_off[v + 1]++;
-  for (int32_t L = 0; L <= Lmax; ++L) c->level_off[L + 1] += c->level_off[L];
-  std::vector<int32_t> pairs((size_t)M * E);
+  for (int32_t L = 0; L <= Lmax; ++L) c->level_off[L + 1] = c->level_off[L] + (cnt[L] + spw - 1) / spw * spw;
+  std::vector<int32_t> pairs((size_t)c->level_off.back(), -1);
   {
     std::vector<int64_t> pos(c->level_off.begin(), c->level_off.end() - 1);
     for (int64_t e = 0; e < E; ++e)
@@ -616,6 +630,17 @@ sn_status sn_build_graph(sn_ctx* c, int weighting, int exact_max, sn_graph_stats
   return SN_OK;
 }
 
+sn_status sn_set_launch(sn_ctx* c, int mode, int blocks_per_sm) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, mode == SN_LAUNCH_LEVELS || mode == SN_LAUNCH_DATAFLOW, SN_EINVAL, "unknown launch mode");
+  SN_REQ(c, blocks_per_sm >= 0 && blocks_per_sm <= 64, SN_EINVAL, "blocks_per_sm must be 0..64");
+  c->launch_mode = mode;
+  c->blocks_per_sm = blocks_per_sm;
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  return SN_OK;
+}
+
 sn_status sn_get_graph(sn_ctx* c, int64_t* n_removed, int32_t* removed, int64_t cap, int32_t* levels) {
   if (!c) return SN_EINVAL;
   SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
@@ -634,27 +659,39 @@ sn_status sn_get_graph(sn_ctx* c, int64_t* n_removed, int32_t* removed, int64_t 
 
 namespace {
 
-// All level launches of one sweep, replayed from a captured CUDA graph when the stream
-// allows capture (not the legacy default stream).
+// One sweep: either one launch per level, or one persistent dataflow launch (completion flags
+// and queue head cleared first).  Replayed from a captured CUDA graph when the stream allows
+// capture (not the legacy default stream).
 sn_status run_levels(sn_ctx* c, int prec, const double* psi_old, double* psi_new) {
   DevProblem P = c->dev();
   const int64_t L = (int64_t)c->level_off.size() - 1;
+  const int64_t total = c->level_off.back();
+  int* err = reinterpret_cast<int*>(c->d_red + 2);
+  unsigned long long* head = c->d_red + 3;
+  SweepArgs sa{c->d_facecode, c->d_mixed_off, c->d_mixedB, c->d_mixedB32, c->d_mixedB32lo, c->d_src,
+               psi_old, psi_new, c->d_done, err};
+  const int mode = c->launch_mode;
   auto launch_all = [&]() -> cudaError_t {
+    if (mode == SN_LAUNCH_DATAFLOW) {
+      cudaError_t e = cudaMemsetAsync(c->d_done, 0, (size_t)c->M * c->E * sizeof(int), c->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(c->d_red + 2, 0, 2 * sizeof(unsigned long long), c->stream);
+      if (e == cudaSuccess)
+        e = launch_sweep_flow(P, prec, c->d_pairs, total, sa, head, c->blocks_per_sm, c->stream);
+      return e;
+    }
     for (int64_t l = 0; l < L; ++l) {
       const int64_t off = c->level_off[l], cnt = c->level_off[l + 1] - off;
-      cudaError_t e = launch_sweep_level(P, prec, c->d_pairs + off, cnt, c->d_facecode, c->d_mixed_off,
-                                         c->d_mixedB, c->d_mixedB32, c->d_mixedB32lo, c->d_src, psi_old, psi_new,
-                                         c->stream);
+      cudaError_t e = launch_sweep_level(P, prec, c->d_pairs + off, cnt, sa, c->stream);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
   };
-  c->launches += L;
+  c->launches += (mode == SN_LAUNCH_DATAFLOW) ? 1 : L;
   if (c->stream == nullptr) {
     SN_CUDA(c, launch_all());
     return SN_OK;
   }
-  sn_ctx::GraphKey key{prec, psi_old, psi_new};
+  sn_ctx::GraphKey key{prec * 16 + mode, psi_old, psi_new};
   auto it = c->graphs.find(key);
   if (it == c->graphs.end()) {
     if (c->graphs.size() >= 8) {
@@ -674,6 +711,19 @@ sn_status run_levels(sn_ctx* c, int prec, const double* psi_old, double* psi_new
     it = c->graphs.emplace(key, ge).first;
   }
   SN_CUDA(c, cudaGraphLaunch(it->second, c->stream));
+  return SN_OK;
+}
+
+// After a synchronised sweep: SN_ETIMEOUT if a dataflow wait gave up.
+sn_status check_err(sn_ctx* c) {
+  if (c->launch_mode != SN_LAUNCH_DATAFLOW) return SN_OK;
+  unsigned long long w = 0;
+  SN_CUDA(c, cudaMemcpyAsync(&w, c->d_red + 2, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
+  SN_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (w & 0xffffffffull) {
+    set_err(c, "dataflow sweep: a dependency wait exceeded its spin limit");
+    return SN_ETIMEOUT;
+  }
   return SN_OK;
 }
 
@@ -719,7 +769,7 @@ sn_status sn_sweep(sn_ctx* c, const double* phi_in, const double* psi_old, doubl
     SN_CUDA(c, cudaMemcpyAsync(psi_new, dnew, npsi * 8, cudaMemcpyDeviceToHost, c->stream));
   }
   if (host_out || !is_device_ptr(phi_in) || !is_device_ptr(psi_old)) SN_CUDA(c, cudaStreamSynchronize(c->stream));
-  return SN_OK;
+  return check_err(c);
 }
 
 sn_status sn_moment(sn_ctx* c, const double* psi, const double* phi_prev, double* phi_out, double* residual) {
@@ -787,9 +837,13 @@ sn_status sn_si_step(sn_ctx* c, int precision, double* residual, float* ms_sweep
   DevProblem P = c->dev();
   SN_CUDA(c, launch_moment(P, c->d_psi[cur ^ 1], c->d_phi, c->d_phi2, c->d_src, c->d_red, s));
   c->launches++;
-  unsigned long long red[2];
+  unsigned long long red[3];
   SN_CUDA(c, cudaMemcpyAsync(red, c->d_red, sizeof(red), cudaMemcpyDeviceToHost, s));
   SN_CUDA(c, cudaStreamSynchronize(s));
+  if (c->launch_mode == SN_LAUNCH_DATAFLOW && (red[2] & 0xffffffffull)) {
+    set_err(c, "dataflow sweep: a dependency wait exceeded its spin limit");
+    return SN_ETIMEOUT;
+  }
   double diff, mag;
   std::memcpy(&diff, &red[0], 8);
   std::memcpy(&mag, &red[1], 8);

@@ -72,6 +72,20 @@ struct DevProblem {
   const float* elem32lo;     // [E][blk] FP32 rounding of elem - elem32 (double-single form) or null
 };
 
+// Per-sweep buffers seen by the sweep kernels.
+struct SweepArgs {
+  const uint32_t* facecode;   // [M][E]
+  const int32_t* mixed_off;   // [M][E]
+  const double* mixedB;       // partially-inflow blocks, FP64
+  const float* mixedBh;       // and their FP32 hi / lo split
+  const float* mixedBl;
+  const double* src;          // [E][N] M (q + sigma_s phi / 4 pi)
+  const double* psi_old;      // previous iterate (lagged arcs)
+  double* psi_new;            // this sweep's result
+  int* done;                  // [M][E] completion flags (dataflow schedule) or null
+  int* err;                   // device error word (dataflow wait gave up) or null
+};
+
 // Element factor block layout: S^0..S^{dim-1} (N x N, S^k[m][n] = int du_m/dx_k u_n),
 // mass M (N x N), then face matrices FN[f][k][i][j] = int_face w N_k phi_i phi_j with the
 // element's own outward scaled normal (2 dim faces x dim components x Nf x Nf).
@@ -99,10 +113,9 @@ cudaError_t launch_source(const DevProblem& P, const double* phi, double* src, c
 cudaError_t launch_moment(const DevProblem& P, const double* psi, const double* phi_prev, double* phi_out,
                           double* src, unsigned long long* red, cudaStream_t s);
 cudaError_t launch_sweep_level(const DevProblem& P, int precision, const int32_t* pairs, int64_t count,
-                               const uint32_t* facecode, const int32_t* mixed_off, const double* mixedB,
-                               const float* mixedB32, const float* mixedB32lo, const double* src,
-                               const double* psi_old, double* psi_new,
-                               cudaStream_t s);
+                               const SweepArgs& sa, cudaStream_t s);
+cudaError_t launch_sweep_flow(const DevProblem& P, int precision, const int32_t* pairs, int64_t count,
+                              const SweepArgs& sa, unsigned long long* head, int blocks_per_sm, cudaStream_t s);
 
 }  // namespace sn
 
@@ -159,8 +172,11 @@ struct sn_ctx {
   double* d_psi[2] = {nullptr, nullptr};
   double *d_phi = nullptr, *d_phi2 = nullptr, *d_src = nullptr;
   double* d_stage[3] = {nullptr, nullptr, nullptr};   // host-pointer staging
-  unsigned long long* d_red = nullptr;
+  unsigned long long* d_red = nullptr;   // [0..1] residual maxima, [2] error word, [3] queue head
   int* d_flag = nullptr;
+  int* d_done = nullptr;                 // [M][E] dataflow completion flags
+  int launch_mode = 0;                   // SN_LAUNCH_LEVELS / SN_LAUNCH_DATAFLOW
+  int blocks_per_sm = 0;                 // dataflow grid: 0 = occupancy limit
   int si_cur = 0;                 // which psi buffer holds the current iterate
   bool si_ready = false;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;

@@ -149,3 +149,36 @@ def test_mixed_source_iteration_reaches_same_tolerance(case, prec):
     err = rel_l2(phi, ref["phi"])
     print(f"mixed(prec={prec}) converged phi rel L2 {case}: {err:.3e} iters {res['iters']}")
     assert err <= 1e-7
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("case", ["2d_sine_16", "2d_smooth_10_p3_s8", "3d_twist_4_p2_s8", "2d_reoriented_6_p2",
+                                  "3d_twist_3_p1_s4_reoriented", "2d_sine_8_p2_strong"])
+def test_dataflow_schedule_matches_level_schedule(case, prec):
+    """The persistent dataflow sweep computes exactly what the per-level launches compute."""
+    import paper_1810_11080_gb300 as g
+    prob = CASES[case]()
+    ctx, _ = gpu_ctx(prob, "face")
+    phi, psi_old = random_state(prob, seed=6)
+    ref = np.zeros_like(psi_old)
+    ctx.sn_set_launch(g.SN_LAUNCH_LEVELS)
+    ctx.sn_sweep(phi, psi_old, ref, prec)
+    for bps in (0, 1):
+        out = np.full_like(psi_old, np.nan)
+        ctx.sn_set_launch(g.SN_LAUNCH_DATAFLOW, bps)
+        ctx.sn_sweep(phi, psi_old, out, prec)
+        assert np.array_equal(out, ref), (bps, rel_l2(out, ref))
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_dataflow_source_iteration(prec):
+    import paper_1810_11080_gb300 as g
+    prob = CASES["3d_twist_4_p2_s8"]()
+    disc, G = oracle_graph(prob, "face")
+    ref = Sweeper(disc, G).source_iterate(tol=1e-12)
+    ctx, _ = gpu_ctx(prob, "face")
+    ctx.sn_set_launch(g.SN_LAUNCH_DATAFLOW)
+    phi = np.zeros((prob.mesh.n_elem, (prob.p + 1) ** 3))
+    res = ctx.sn_source_iterate(1e-10, 500, prec, phi_out=phi)
+    assert res["converged"]
+    assert rel_l2(phi, ref["phi"]) <= 1e-9
