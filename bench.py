@@ -285,9 +285,50 @@ def run_gpu(args):
                   "max_scc": gstats["max_scc"], "mixed_faces": gstats["n_mixed_faces"]},
         "peaks_file": pk_kind,
     }
+    if not args.no_batch:
+        out["batched"] = run_batch(g, torch, args)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample_dirs)
     return out
+
+
+def run_batch(g, torch, args):
+    """256 independent 2D problems (n ~ U{8..64}, p ~ U{1,2,3}, r ~ U{2,3}, S4-S8, sigma_t ~ U[0.1,10],
+    c ~ U[0.5,0.95]) swept in one launch per step; schedule picked by the autotuner."""
+    import sn_inputs as si
+    probs = si.batch_problems(count=256, seed=31)
+    stream = torch.cuda.Stream()
+    ctxs = []
+    for p in probs:
+        c = g.setup_problem(p, device=0, stream=stream.cuda_stream)
+        c.sn_build_graph("face", 10)
+        ctxs.append(c)
+    b = g.Batch(ctxs, stream.cuda_stream)
+    ups = b.sn_batch_updates_per_sweep()
+    res = {"workload": "256 uneven 2D problems, n~U{8..64}, p~U{1,2,3}, r~U{2,3}, S4-S8, seed 31",
+           "updates_per_sweep": int(ups), "elements": int(sum(p.mesh.n_elem for p in probs))}
+    for name, prec in (("mixed_ds", g.SN_PREC_MIXED_DS), ("fp64", g.SN_PREC_FP64)):
+        mode, bps = b.sn_batch_tune(prec)
+        b.sn_batch_si_begin()
+        for _ in range(args.warmup):
+            b.sn_batch_si_step(prec)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        steps = max(5, args.steps // 4)
+        for _ in range(steps):
+            b.sn_batch_si_step(prec)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        t0 = time.perf_counter()
+        r = b.sn_batch_source_iterate(1e-8, 3000, prec)
+        res[name] = {"value": ups * steps / (ms / 1e3), "unit": "updates/s", "ms_per_step": ms / steps,
+                     "schedule": {"mode": "dataflow" if mode == 1 else "levels", "blocks_per_sm": bps},
+                     "time_to_1e-8_s": time.perf_counter() - t0, "max_iters": int(r["iters"].max()),
+                     "converged": r["status"] == 0}
+    b.close()
+    return res
 
 
 def cpu_baseline(n_dirs):
@@ -356,6 +397,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-problem batched measurement")
     ap.add_argument("--launch", default="levels", choices=["levels", "dataflow"],
                     help="sweep schedule: one launch per level, or one persistent dataflow launch")
     ap.add_argument("--form", default="mixed_ds", choices=["fp64", "mixed", "mixed_ds"],

@@ -143,6 +143,12 @@ sn_status sn_build_graph(sn_ctx* ctx, int weighting, int exact_max, sn_graph_sta
  * May be called at any time; applies to later sweeps. */
 sn_status sn_set_launch(sn_ctx* ctx, int mode, int blocks_per_sm);
 
+/* Autotuner (no counterpart in the paper): times three source iterations of every candidate
+ * schedule -- per-level launches, or the dataflow launch with 1, 2, 4 or the maximum resident
+ * CTAs per SM -- keeps the fastest via sn_set_launch and resets the iteration state
+ * (sn_si_begin(ctx, NULL)).  mode_out / blocks_per_sm_out may be NULL. */
+sn_status sn_autotune(sn_ctx* ctx, int precision, int* mode_out, int* blocks_per_sm_out);
+
 /* Copy the graph out (valid after sn_build_graph).
  *   *n_removed receives the number of removed arcs; if removed != NULL and cap >= that number,
  *   removed [k][3] receives (direction, e, e') rows sorted ascending: e depends on e' and the
@@ -197,6 +203,36 @@ sn_status sn_source_iterate(sn_ctx* ctx, double tol, int max_iter, int precision
 sn_status sn_si_begin(sn_ctx* ctx, const double* phi0);
 sn_status sn_si_step(sn_ctx* ctx, int precision, double* residual, float* ms_sweep);
 sn_status sn_si_result(sn_ctx* ctx, double* phi_out, double* psi_out);
+
+/* ---- Batches: many independent problems in one persistent launch (no counterpart in the
+ * paper; each problem is the method above).  The problems are contexts of the same dimension
+ * on the same device whose graphs are built; they may differ in mesh size, geometry order, DG
+ * order, direction set and materials.  A batch step sweeps every problem in one launch
+ * (dataflow schedule: warps take (problem, level, pairs) tasks from a queue ordered by level
+ * across problems; or one launch per level), then one launch forms every problem's scalar flux,
+ * scattering source and residual; the step is replayed from a CUDA graph.  The batch owns only
+ * its tables; flux buffers stay in the contexts (sn_si_result on a context reads its state after
+ * batch steps).  Do not interleave single-context steps of a member with batch steps. */
+typedef struct sn_batch sn_batch;
+sn_status sn_batch_create(sn_batch** out, int n_problems, sn_ctx* const* problems, void* cuda_stream);
+void sn_batch_destroy(sn_batch* batch);
+const char* sn_batch_last_error(const sn_batch* batch);
+/* Element-direction updates of one sweep over all problems. */
+int64_t sn_batch_updates_per_sweep(const sn_batch* batch);
+/* Schedule of later steps, as sn_set_launch (default: dataflow, maximum resident CTAs). */
+sn_status sn_batch_set_launch(sn_batch* batch, int mode, int blocks_per_sm);
+/* Autotuner over the same candidates as sn_autotune; resets the iteration state. */
+sn_status sn_batch_tune(sn_batch* batch, int precision, int* mode_out, int* blocks_per_sm_out);
+/* phi <- 0, psi <- 0 in every problem. */
+sn_status sn_batch_si_begin(sn_batch* batch);
+/* One source iteration of every problem; residuals [n_problems] (may be NULL) receive each
+ * problem's relative scalar-flux change; *ms_sweep (may be NULL) the device time of the step. */
+sn_status sn_batch_si_step(sn_batch* batch, int precision, double* residuals, float* ms_sweep);
+/* Steps until every problem's relative change is below tol; iters [n] receives the first
+ * iteration at which each problem reached it (-1 if never), residuals [n] the last change.
+ * SN_ENOTCONVERGED if some problem did not reach tol in max_iter steps. */
+sn_status sn_batch_source_iterate(sn_batch* batch, double tol, int max_iter, int precision, int32_t* iters,
+                                  double* residuals, double* ms_total);
 
 /* Scalar-flux moment and relative change WITHOUT a context and without allocating anything
  * (the paper has no counterpart: this is a deployment entry point).

@@ -22,7 +22,10 @@ WEIGHTING = {"unity": 0, "face": 1, "siginvface": 2}
 EXPORTED = ["sn_create", "sn_destroy", "sn_last_error", "sn_set_mesh", "sn_set_discretization",
             "sn_set_quadrature", "sn_set_materials", "sn_num_boundary_faces", "sn_build_graph",
             "sn_get_graph", "sn_sweep", "sn_moment", "sn_source_iterate", "sn_si_begin", "sn_si_step",
-            "sn_si_result", "sn_kernel_launches", "sn_moment_noalloc", "sn_set_launch"]
+            "sn_si_result", "sn_kernel_launches", "sn_moment_noalloc", "sn_set_launch", "sn_autotune",
+            "sn_batch_create", "sn_batch_destroy", "sn_batch_last_error", "sn_batch_updates_per_sweep",
+            "sn_batch_set_launch", "sn_batch_tune", "sn_batch_si_begin", "sn_batch_si_step",
+            "sn_batch_source_iterate"]
 
 
 class sn_graph_stats(ctypes.Structure):
@@ -70,6 +73,16 @@ def load(path=LIB_PATH):
         "sn_si_result": (I, [P, P, P]),
         "sn_kernel_launches": (I64, [P]),
         "sn_set_launch": (I, [P, I, I]),
+        "sn_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "sn_batch_create": (I, [ctypes.POINTER(P), I, P, P]),
+        "sn_batch_destroy": (None, [P]),
+        "sn_batch_last_error": (ctypes.c_char_p, [P]),
+        "sn_batch_updates_per_sweep": (I64, [P]),
+        "sn_batch_set_launch": (I, [P, I, I]),
+        "sn_batch_tune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "sn_batch_si_begin": (I, [P]),
+        "sn_batch_si_step": (I, [P, I, P, ctypes.POINTER(ctypes.c_float)]),
+        "sn_batch_source_iterate": (I, [P, D, I, I, P, P, ctypes.POINTER(D)]),
         "sn_moment_noalloc": (I, [I, P, I, I64, I, P, P, P, P, ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
@@ -213,6 +226,11 @@ class Context:
     def sn_set_launch(self, mode, blocks_per_sm=0):
         return self._check(self._lib.sn_set_launch(self._c, int(mode), int(blocks_per_sm)))
 
+    def sn_autotune(self, precision=SN_PREC_MIXED_DS):
+        m, b = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.sn_autotune(self._c, int(precision), ctypes.byref(m), ctypes.byref(b)))
+        return m.value, b.value
+
     def sn_si_begin(self, phi0=None):
         return self._check(self._lib.sn_si_begin(self._c, _ptr(phi0, np.float64, "phi0")))
 
@@ -229,3 +247,63 @@ class Context:
 
     def sn_kernel_launches(self):
         return self._lib.sn_kernel_launches(self._c)
+
+
+class Batch:
+    """Owns one sn_batch over a list of Contexts (which must outlive it)."""
+
+    def __init__(self, contexts, stream=None):
+        self._lib = lib()
+        self._ctxs = list(contexts)
+        arr = (ctypes.c_void_p * len(self._ctxs))(*[c._c.value for c in self._ctxs])
+        self._b = ctypes.c_void_p()
+        st = self._lib.sn_batch_create(ctypes.byref(self._b), len(self._ctxs), arr, stream)
+        if st != SN_OK:
+            raise SnError(st, "sn_batch_create failed (contexts must share device and dimension and have graphs)")
+
+    def _check(self, st):
+        if st != SN_OK:
+            raise SnError(st, self._lib.sn_batch_last_error(self._b).decode())
+        return st
+
+    def close(self):
+        if self._b:
+            self._lib.sn_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sn_batch_updates_per_sweep(self):
+        return self._lib.sn_batch_updates_per_sweep(self._b)
+
+    def sn_batch_set_launch(self, mode, blocks_per_sm=0):
+        return self._check(self._lib.sn_batch_set_launch(self._b, int(mode), int(blocks_per_sm)))
+
+    def sn_batch_tune(self, precision=SN_PREC_MIXED_DS):
+        m, b = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.sn_batch_tune(self._b, int(precision), ctypes.byref(m), ctypes.byref(b)))
+        return m.value, b.value
+
+    def sn_batch_si_begin(self):
+        return self._check(self._lib.sn_batch_si_begin(self._b))
+
+    def sn_batch_si_step(self, precision=SN_PREC_MIXED_DS, time_sweep=False):
+        res = np.zeros(len(self._ctxs))
+        ms = ctypes.c_float()
+        self._check(self._lib.sn_batch_si_step(self._b, int(precision), res.ctypes.data,
+                                               ctypes.byref(ms) if time_sweep else None))
+        return res, (ms.value if time_sweep else None)
+
+    def sn_batch_source_iterate(self, tol, max_iter, precision=SN_PREC_MIXED_DS):
+        its = np.zeros(len(self._ctxs), dtype=np.int32)
+        res = np.zeros(len(self._ctxs))
+        ms = ctypes.c_double()
+        st = self._lib.sn_batch_source_iterate(self._b, float(tol), int(max_iter), int(precision), its.ctypes.data,
+                                               res.ctypes.data, ctypes.byref(ms))
+        if st not in (SN_OK, SN_ENOTCONVERGED):
+            self._check(st)
+        return dict(status=st, iters=its, residuals=res, ms_total=ms.value)

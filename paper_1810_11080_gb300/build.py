@@ -45,8 +45,9 @@ def build(verbose=False, extra_nvcc=()):
         "graph.cu": ["-fmad=false"],
         "sweep.cu": [],
         "noalloc.cu": [],
+        "batch.cu": [],
     }
-    cpp = ["api.cpp", "tables.cpp", "fas.cpp"]
+    cpp = ["api.cpp", "batch_api.cpp", "tables.cpp", "fas.cpp"]
     jobs = []
     for src, flags in cu.items():
         obj = os.path.join(BUILD, src + ".o")

@@ -593,6 +593,7 @@ sn_status sn_build_graph(sn_ctx* c, int weighting, int exact_max, sn_graph_stats
   }
   SN_CUDA(c, dalloc(c->d_pairs, pairs.size()));
   SN_CUDA(c, cudaMemcpyAsync(c->d_pairs, pairs.data(), pairs.size() * 4, cudaMemcpyHostToDevice, s));
+  c->h_pairs = pairs;
   // partially-inflow blocks
   std::vector<int32_t> moff((size_t)M * E);
   int64_t nm = 0;
@@ -641,6 +642,38 @@ sn_status sn_set_launch(sn_ctx* c, int mode, int blocks_per_sm) {
   return SN_OK;
 }
 
+sn_status sn_autotune(sn_ctx* c, int precision, int* mode_out, int* blocks_per_sm_out) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
+  const int cand[5][2] = {{SN_LAUNCH_LEVELS, 0}, {SN_LAUNCH_DATAFLOW, 1}, {SN_LAUNCH_DATAFLOW, 2},
+                          {SN_LAUNCH_DATAFLOW, 4}, {SN_LAUNCH_DATAFLOW, 0}};
+  float best = 1e30f;
+  int bm = SN_LAUNCH_LEVELS, bb = 0;
+  for (auto& cd : cand) {
+    sn_status st = sn_set_launch(c, cd[0], cd[1]);
+    if (st != SN_OK) return st;
+    if ((st = sn_si_begin(c, nullptr)) != SN_OK) return st;
+    if ((st = sn_si_step(c, precision, nullptr, nullptr)) != SN_OK) return st;   // capture + warm
+    float tot = 0.0f;
+    for (int r = 0; r < 3; ++r) {
+      float ms = 0.0f;
+      if ((st = sn_si_step(c, precision, nullptr, &ms)) != SN_OK) return st;
+      tot += ms;
+    }
+    if (tot < best) {
+      best = tot;
+      bm = cd[0];
+      bb = cd[1];
+    }
+  }
+  sn_status st = sn_set_launch(c, bm, bb);
+  if (st != SN_OK) return st;
+  if ((st = sn_si_begin(c, nullptr)) != SN_OK) return st;
+  if (mode_out) *mode_out = bm;
+  if (blocks_per_sm_out) *blocks_per_sm_out = bb;
+  return SN_OK;
+}
+
 sn_status sn_get_graph(sn_ctx* c, int64_t* n_removed, int32_t* removed, int64_t cap, int32_t* levels) {
   if (!c) return SN_EINVAL;
   SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
@@ -669,7 +702,7 @@ sn_status run_levels(sn_ctx* c, int prec, const double* psi_old, double* psi_new
   int* err = reinterpret_cast<int*>(c->d_red + 2);
   unsigned long long* head = c->d_red + 3;
   SweepArgs sa{c->d_facecode, c->d_mixed_off, c->d_mixedB, c->d_mixedB32, c->d_mixedB32lo, c->d_src,
-               psi_old, psi_new, c->d_done, err};
+               psi_old, psi_new, c->d_done, err, c->d_pairs};
   const int mode = c->launch_mode;
   auto launch_all = [&]() -> cudaError_t {
     if (mode == SN_LAUNCH_DATAFLOW) {

@@ -84,7 +84,24 @@ struct SweepArgs {
   double* psi_new;            // this sweep's result
   int* done;                  // [M][E] completion flags (dataflow schedule) or null
   int* err;                   // device error word (dataflow wait gave up) or null
+  const int32_t* pairs;       // level-ordered (e*M + d) work list (-1 = padding); batched kernels
 };
+
+// Per-problem pointers of the fused moment / source kernel in a batch.
+struct MomentArgs {
+  const double* psi;          // [M][E][N] this sweep's angular flux
+  const double* phi_prev;     // [E][N]
+  double* phi_out;            // [E][N]
+  double* src;                // [E][N] scattering + isotropic source for the next sweep
+};
+
+// Batched sweep over problems of one dimension (batch.cu).  A task = up to 32/W consecutive
+// entries of one problem's level-ordered pair list; int4 = (problem, p, offset, 0).
+cudaError_t launch_batch_sweep(int dim, int precision, bool dataflow, const DevProblem* probs, const SweepArgs* args,
+                               const int4* tasks, int64_t ntasks, unsigned long long* head, int* err,
+                               int blocks_per_sm, cudaStream_t s);
+cudaError_t launch_batch_moment(const DevProblem* probs, const MomentArgs* margs, const int64_t* block_off,
+                                int nprob, int64_t nblocks, unsigned long long* red, cudaStream_t s);
 
 // Element factor block layout: S^0..S^{dim-1} (N x N, S^k[m][n] = int du_m/dx_k u_n),
 // mass M (N x N), then face matrices FN[f][k][i][j] = int_face w N_k phi_i phi_j with the
@@ -165,6 +182,7 @@ struct sn_ctx {
   int64_t n_mixed = 0;
   int32_t* d_levels = nullptr;
   int32_t* d_pairs = nullptr;
+  std::vector<int32_t> h_pairs;     // host copy of the padded, level-ordered work list
   std::vector<int64_t> level_off;
   std::vector<int32_t> h_removed;   // (d, e, e') triples
   int64_t n_removed = 0;
@@ -192,3 +210,4 @@ struct sn_ctx {
   std::map<GraphKey, cudaGraphExec_t> graphs;
   sn::DevProblem dev() const;
 };
+

@@ -18,642 +18,9 @@
 // Two schedules: one launch per wavefront level (pairs of a level are independent), or one
 // persistent "dataflow" launch per sweep in which warps take pairs from a queue in level order
 // and wait only for the completion flags of their kept upwind neighbours.
-#include <type_traits>
-#include "devmath.cuh"
+#include "sweep_body.cuh"
 
 namespace sn {
-
-template <int I, int END, class F>
-__device__ __forceinline__ void static_for(F&& fn) {
-  if constexpr (I < END) {
-    fn(std::integral_constant<int, I>{});
-    static_for<I + 1, END>(fn);
-  }
-}
-
-// 1/x by Newton-Raphson (r <- r + r (1 - x r), two steps) from the hardware reciprocal
-// approximation: relative error below 2^-52 for normal x, at a third of the FP64 pipe slots of
-// an IEEE division.
-__device__ __forceinline__ double nr_rcp(double x) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
-
-// Volume node index of face node fj of face f (compile-time).
-template <int DIM, int P_>
-__host__ __device__ constexpr int fvi(int f, int fj) {
-  return face_vol_index(DIM, P_, f, fj % (P_ + 1), fj / (P_ + 1));
-}
-
-template <int DIM, int P_>
-struct Shape {
-  static constexpr int NP1 = P_ + 1;
-  static constexpr int N = ipow(NP1, DIM);
-  static constexpr int NF = ipow(NP1, DIM - 1);
-  static constexpr int W = N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32;
-  static constexpr int SPW = 32 / W;
-};
-
-// Face-node index of volume node i on local face f, or -1.
-template <int DIM, int P_>
-__device__ __forceinline__ int on_face(int f, int i) {
-  constexpr int n = P_ + 1;
-  const int t0 = i % n, t1 = (i / n) % n, t2 = (DIM == 3) ? i / (n * n) : 0;
-  const int axis = f >> 1, side = f & 1;
-  const int ta = axis == 0 ? t0 : (axis == 1 ? t1 : t2);
-  if (ta != side * P_) return -1;
-  const int o0 = axis == 0 ? t1 : t0;
-  const int o1 = axis == 2 ? t1 : t2;
-  return DIM == 2 ? o0 : o0 + n * o1;
-}
-
-// ---- double-single (FP32 pair) arithmetic: error-free transformations (Knuth two-sum,
-// fma-based two-product), ~2^-48 relative precision on the FP32 pipe.
-__device__ __forceinline__ void ds_two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-// (ph, pl) = (xh + xl)(yh + yl) to first order in the low parts.
-__device__ __forceinline__ void ds_mul(float xh, float xl, float yh, float yl, float& ph, float& pl) {
-  ph = xh * yh;
-  pl = fmaf(xh, yh, -ph);
-  pl = fmaf(xh, yl, pl);
-  pl = fmaf(xl, yh, pl);
-}
-// (sh, sl) += (ph, pl), renormalised.
-__device__ __forceinline__ void ds_add(float& sh, float& sl, float ph, float pl) {
-  float t, e;
-  ds_two_sum(sh, ph, t, e);
-  e += sl + pl;
-  sh = t + e;
-  sl = e - (sh - t);
-}
-__device__ __forceinline__ void ds_split(double x, float& h, float& l) {
-  h = (float)x;
-  l = (float)(x - (double)h);
-}
-
-// ---- dataflow synchronisation
-constexpr long long SPIN_LIMIT = 1LL << 20;     // ~0.1-1 s of polling before giving up
-
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(int* p, int v) {
-  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-template <bool DF>
-__device__ __forceinline__ double trace_load(const double* p) {
-  if constexpr (DF) return __ldcg(p);      // written during this launch: bypass the incoherent L1
-  else return __ldg(p);
-}
-
-// Wait until every kept upwind neighbour of (e, d) has published its angular flux.  A wait that
-// exceeds SPIN_LIMIT polls sets *err and gives up (the result is then wrong and the host
-// reports SN_ETIMEOUT); it never traps.
-template <int DIM>
-__device__ void wait_upwind(const DevProblem& Pb, const SweepArgs& sa, uint32_t code, int64_t e, int d, bool valid) {
-  if (!valid) return;
-#pragma unroll
-  for (int f = 0; f < 2 * DIM; ++f) {
-    if (face_mode(code, f) == MODE_NONE || face_lagged(code, f)) continue;
-    const int64_t nb = Pb.nbr[e * 2 * DIM + f];
-    if (nb < 0) continue;
-    const int* flag = sa.done + (int64_t)d * Pb.E + nb;
-    long long spins = 0;
-    while (ld_acquire(flag) == 0) {
-      if (++spins > SPIN_LIMIT) {
-        atomicExch(sa.err, 1);
-        break;
-      }
-      if ((spins & 255) == 0 && *(volatile int*)sa.err) break;   // another wait gave up: stop
-      __nanosleep(64);
-    }
-  }
-}
-
-// Publish (e, d): every lane's flux store is made visible device-wide before the flag.
-template <bool DF, int W>
-__device__ __forceinline__ void publish(const DevProblem& Pb, const SweepArgs& sa, int64_t e, int d, bool valid,
-                                        int i) {
-  if constexpr (DF) {
-    __threadfence();
-    __syncwarp();
-    if (valid && i == 0) st_release(sa.done + (int64_t)d * Pb.E + e, 1);
-  }
-}
-
-// b += B_f trace_f for one inflow face row (FP64): neighbour trace or incident flux.
-template <int DIM, int P_, bool DF>
-__device__ __forceinline__ void face_rhs(const DevProblem& Pb, const SweepArgs& sa, uint32_t code, int f, int64_t e,
-                                         int d, const double* Brow, double& b) {
-  constexpr int NF = Shape<DIM, P_>::NF, NP1 = P_ + 1, N = Shape<DIM, P_>::N;
-  const int64_t nb = Pb.nbr[e * 2 * DIM + f];
-  if (nb >= 0) {
-    const bool lag = face_lagged(code, f);
-    const double* ps = lag ? sa.psi_old : sa.psi_new;
-    const int fn = Pb.nbr_face[e * 2 * DIM + f], oc = Pb.orient[e * 2 * DIM + f];
-    const double* pnb = ps + ((int64_t)d * Pb.E + nb) * N;
-#pragma unroll
-    for (int fj = 0; fj < NF; ++fj) {
-      int t0, t1;
-      orient_map_idx(DIM, oc, P_, fj % NP1, fj / NP1, t0, t1);
-      const double* pt = pnb + face_vol_index(DIM, P_, fn, t0, t1);
-      b = fma(Brow[fj], lag ? __ldg(pt) : trace_load<DF>(pt), b);
-    }
-  } else if (Pb.psi_inc != nullptr) {
-    const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * 2 * DIM + f]) * NF;
-#pragma unroll
-    for (int fj = 0; fj < NF; ++fj) b = fma(Brow[fj], __ldg(pin + fj), b);
-  }
-}
-
-// FP64 inflow block row fi of face f: -Omega . FN_f (whole-inflow) or the stored block.
-template <int DIM, int P_>
-__device__ __forceinline__ void brow64(const double* blk, const SweepArgs& sa, uint32_t mode, int f, int fi,
-                                       int slot, double om0, double om1, double om2, double* Brow) {
-  constexpr int NF = Shape<DIM, P_>::NF, N = Shape<DIM, P_>::N;
-  if (mode == MODE_PURE) {
-    const double* fnm = blk + (DIM + 1) * N * N + f * DIM * NF * NF + fi * NF;
-#pragma unroll
-    for (int fj = 0; fj < NF; ++fj) {
-      double v = om0 * __ldg(fnm + fj);
-      v = fma(om1, __ldg(fnm + NF * NF + fj), v);
-      if (DIM == 3) v = fma(om2, __ldg(fnm + 2 * NF * NF + fj), v);
-      Brow[fj] = -v;
-    }
-  } else {
-    const double* mb = sa.mixedB + (int64_t)slot * NF * NF + fi * NF;
-#pragma unroll
-    for (int fj = 0; fj < NF; ++fj) Brow[fj] = __ldg(mb + fj);
-  }
-}
-
-// ---- FP32 pivoted LU of the segment's rows with multipliers kept in a[k]; returns plk, myk, myinv.
-template <int N, int W>
-__device__ __forceinline__ void lu32(float (&a)[N], float& bx, int i, bool row, int (&plk)[N], int& myk,
-                                     float& myinv) {
-  constexpr unsigned FULL = 0xffffffffu;
-  bool used = !row;
-  myk = -1;
-  myinv = 0.0f;
-  static_for<0, N>([&](auto kconst) {
-    constexpr int k = decltype(kconst)::value;
-    float v = used ? -1.0f : fabsf(a[k]);
-    int idx = i;
-#pragma unroll
-    for (int off = W / 2; off > 0; off >>= 1) {
-      const float v2 = __shfl_xor_sync(FULL, v, off, W);
-      const int i2 = __shfl_xor_sync(FULL, idx, off, W);
-      if (v2 > v || (v2 == v && i2 < idx)) {
-        v = v2;
-        idx = i2;
-      }
-    }
-    const int pl = idx;
-    plk[k] = pl;
-    const float piv = __shfl_sync(FULL, a[k], pl, W);
-    const float inv = 1.0f / piv;
-    if (i == pl && !used) {
-      used = true;
-      myk = k;
-      myinv = inv;
-    }
-    const bool elim = !used;
-    const float l = a[k] * inv;
-    if (elim) a[k] = l;
-    static_for<k + 1, N>([&](auto jconst) {
-      constexpr int j = decltype(jconst)::value;
-      const float u = __shfl_sync(FULL, a[j], pl, W);
-      if (elim) a[j] = fmaf(-l, u, a[j]);
-    });
-    const float ub = __shfl_sync(FULL, bx, pl, W);
-    if (elim) bx = fmaf(-l, ub, bx);
-  });
-}
-
-template <int N, int W>
-__device__ __forceinline__ float back_sub32(const float (&a)[N], float rhs, const int (&plk)[N], int myk,
-                                            float myinv) {
-  constexpr unsigned FULL = 0xffffffffu;
-  float xo = 0.0f;
-  static_for<0, N>([&](auto jconst) {
-    constexpr int j = N - 1 - decltype(jconst)::value;
-    const bool mine = (myk == j);
-    const float xl = mine ? rhs * myinv : 0.0f;
-    const float xj = __shfl_sync(FULL, xl, plk[j], W);
-    if (mine) xo = xj;
-    if (myk >= 0 && myk < j) rhs = fmaf(-a[j], xj, rhs);
-  });
-  return xo;
-}
-
-// Forward replay of the kept multipliers on a new right-hand side.
-template <int N, int W>
-__device__ __forceinline__ float forward32(const float (&a)[N], float r, const int (&plk)[N], int myk, bool row) {
-  constexpr unsigned FULL = 0xffffffffu;
-  static_for<0, N>([&](auto kconst) {
-    constexpr int k = decltype(kconst)::value;
-    const float rb = __shfl_sync(FULL, r, plk[k], W);
-    if (myk > k || (myk < 0 && row)) r = fmaf(-a[k], rb, r);
-  });
-  return r;
-}
-
-// ---- latency-oriented FP32 solve: Gauss-Jordan inverse with partial pivoting.
-// Pivot search: one integer max per segment over key = (bits(|a|) with the 5 low mantissa bits
-// cleared) | (31 - lane): the largest |a| (to 2^-18 relative) wins, ties go to the lowest lane.
-template <int W>
-__device__ __forceinline__ int seg_argmax_key(unsigned key, int lane) {
-  constexpr unsigned FULL = 0xffffffffu;
-  if constexpr (W == 32) {
-    return 31 - (int)(__reduce_max_sync(FULL, key) & 31u);
-  } else if constexpr (W == 16) {
-    const unsigned m0 = __reduce_max_sync(FULL, lane < 16 ? key : 0u);
-    const unsigned m1 = __reduce_max_sync(FULL, lane < 16 ? 0u : key);
-    return 31 - (int)((lane < 16 ? m0 : m1) & 31u);
-  } else {
-#pragma unroll
-    for (int off = W / 2; off > 0; off >>= 1) key = max(key, __shfl_xor_sync(FULL, key, off, W));
-    return 31 - (int)(key & 31u);
-  }
-}
-
-__device__ __forceinline__ float rcp_approx(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
-// Row-per-lane Gauss-Jordan on the segment: on return the lane that was chosen as pivot of
-// step k (plk[k], myk == k) holds in v[] row k of A^{-1}, with columns indexed by the original
-// row (= lane) index: x_k = sum_j v[j] b_j.  All rows are updated at every step, so there are
-// N dependent steps and no triangular solves.
-template <int N, int W>
-__device__ __forceinline__ void gj32(float (&a)[N], float (&v)[N], int i, int lane, bool row, int (&plk)[N],
-                                     int& myk) {
-  constexpr unsigned FULL = 0xffffffffu;
-  bool used = !row;
-  myk = -1;
-  static_for<0, N>([&](auto jconst) { v[decltype(jconst)::value] = (row && decltype(jconst)::value == i) ? 1.0f : 0.0f; });
-  static_for<0, N>([&](auto kconst) {
-    constexpr int k = decltype(kconst)::value;
-    const unsigned key = used ? 0u : ((__float_as_uint(a[k]) & 0x7fffffe0u) | (unsigned)(31 - lane));
-    const int pl = seg_argmax_key<W>(key, lane);
-    plk[k] = pl;
-    const float piv = __shfl_sync(FULL, a[k], pl, W);
-    const float inv = rcp_approx(piv);
-    const bool me = (lane == pl);
-    if (me) {
-      used = true;
-      myk = k;
-    }
-    const float l = me ? 0.0f : a[k] * inv;
-    static_for<k + 1, N>([&](auto jconst) {
-      constexpr int j = decltype(jconst)::value;
-      const float u = __shfl_sync(FULL, a[j], pl, W);
-      a[j] = me ? a[j] * inv : fmaf(-l, u, a[j]);
-    });
-    static_for<0, N>([&](auto jconst) {
-      constexpr int j = decltype(jconst)::value;
-      const float u = __shfl_sync(FULL, v[j], pl, W);
-      v[j] = me ? v[j] * inv : fmaf(-l, u, v[j]);
-    });
-  });
-}
-
-// y_k = sum_j v[j] r_j on the pivot lane of step k; r_j lives on lane j of the segment.
-template <int N, int W>
-__device__ __forceinline__ float gj_apply(const float (&v)[N], float r) {
-  constexpr unsigned FULL = 0xffffffffu;
-  float s0 = 0.0f, s1 = 0.0f;
-  static_for<0, N>([&](auto jconst) {
-    constexpr int j = decltype(jconst)::value;
-    const float rj = __shfl_sync(FULL, r, j, W);
-    if (j & 1) s1 = fmaf(v[j], rj, s1);
-    else s0 = fmaf(v[j], rj, s0);
-  });
-  return s0 + s1;
-}
-
-// ------------------------------------------------------------------ FP64 form
-template <int DIM, int P_, bool DF>
-__device__ __forceinline__ void body64(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid, int lane) {
-  using S = Shape<DIM, P_>;
-  constexpr int N = S::N, NF = S::NF, W = S::W;
-  constexpr unsigned FULL = 0xffffffffu;
-  const int i = lane % W;
-  const int M = Pb.M;
-  const int64_t E = Pb.E;
-  const int64_t e = pr / M;
-  const int d = pr % M;
-  const bool row = valid && (i < N);
-  const double om0 = Pb.omega[d * 3 + 0], om1 = Pb.omega[d * 3 + 1], om2 = Pb.omega[d * 3 + 2];
-  const double* blk = Pb.elem + e * Pb.blk;
-  double a[N];
-  double b = 0.0;
-  if (row) {
-    const double st = Pb.sig_t[e];
-    static_for<0, N>([&](auto jconst) {
-      constexpr int j = decltype(jconst)::value;
-      double v = om0 * __ldg(blk + j * N + i);
-      v = fma(om1, __ldg(blk + N * N + j * N + i), v);
-      if (DIM == 3) v = fma(om2, __ldg(blk + 2 * N * N + j * N + i), v);
-      a[j] = fma(st, __ldg(blk + DIM * N * N + j * N + i), v);
-    });
-    b = sa.src[e * N + i];
-    if (Pb.q_dir != nullptr) {
-      const double* qd = Pb.q_dir + ((int64_t)d * E + e) * N;
-#pragma unroll
-      for (int j = 0; j < N; ++j) b = fma(__ldg(blk + DIM * N * N + i * N + j), qd[j], b);
-    }
-  } else {
-    static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = 0.0; });
-  }
-  const uint32_t code = valid ? sa.facecode[(int64_t)d * E + e] : 0u;
-  const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[(int64_t)d * E + e] : 0;
-  if constexpr (DF) wait_upwind<DIM>(Pb, sa, code, e, d, valid);
-  int mrank = 0;
-  static_for<0, 2 * DIM>([&](auto fconst) {
-    constexpr int f = decltype(fconst)::value;
-    const uint32_t mode = face_mode(code, f);
-    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
-    if (mode != MODE_NONE && fi >= 0) {
-      double Brow[NF];
-      brow64<DIM, P_>(blk, sa, mode, f, fi, mbase + mrank, om0, om1, om2, Brow);
-      static_for<0, NF>([&](auto jconst) {
-        constexpr int fj = decltype(jconst)::value;
-        a[fvi<DIM, P_>(f, fj)] += Brow[fj];
-      });
-      face_rhs<DIM, P_, DF>(Pb, sa, code, f, e, d, Brow, b);
-    }
-    if (mode == MODE_MIXED) ++mrank;
-  });
-  // LU with partial pivoting; argmax |a[k]| on the bit pattern (integer pipe)
-  bool used = !row;
-  int myk = -1;
-  double myinv = 0.0;
-  int plk[N];
-  static_for<0, N>([&](auto kconst) {
-    constexpr int k = decltype(kconst)::value;
-    // key: high word of |a[k]| (sign cleared, 5 low bits replaced by the lane): integer max
-    const unsigned hw = (unsigned)((unsigned long long)__double_as_longlong(a[k]) >> 32);
-    const unsigned key = used ? 0u : ((hw & 0x7fffffe0u) | (unsigned)(31 - lane));
-    const int pl = seg_argmax_key<W>(key, lane);
-    plk[k] = pl;
-    const double piv = __shfl_sync(FULL, a[k], pl, W);
-    const double inv = nr_rcp(piv);
-    if (lane == pl && !used) {
-      used = true;
-      myk = k;
-      myinv = inv;
-    }
-    const bool elim = !used;
-    const double l = a[k] * inv;
-    static_for<k + 1, N>([&](auto jconst) {
-      constexpr int j = decltype(jconst)::value;
-      const double u = __shfl_sync(FULL, a[j], pl, W);
-      if (elim) a[j] = fma(-l, u, a[j]);
-    });
-    const double ub = __shfl_sync(FULL, b, pl, W);
-    if (elim) b = fma(-l, ub, b);
-  });
-  double x = 0.0;
-  static_for<0, N>([&](auto jconst) {
-    constexpr int j = N - 1 - decltype(jconst)::value;
-    const bool mine = (myk == j);
-    const double xl = mine ? b * myinv : 0.0;
-    const double xj = __shfl_sync(FULL, xl, plk[j], W);
-    if (mine) x = xj;
-    if (myk >= 0 && myk < j) b = fma(-a[j], xj, b);
-  });
-  if (row && myk >= 0) sa.psi_new[((int64_t)d * E + e) * N + myk] = x;
-  publish<DF, W>(Pb, sa, e, d, valid, i);
-}
-
-// ------------------------------------------------------------------ mixed form, FP64 residual
-//   A32 = fl32 assembly of A from the FP32 factor copy; b in FP64;
-//   xhat = A32^{-1} fl32(b); r = b - A64 xhat (FP64 row); psi = xhat + A32^{-1} fl32(r).
-template <int DIM, int P_, bool DF>
-__device__ __forceinline__ void bodymx(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid, int lane) {
-  using S = Shape<DIM, P_>;
-  constexpr int N = S::N, NF = S::NF, W = S::W;
-  constexpr unsigned FULL = 0xffffffffu;
-  const int i = lane % W;
-  const int M = Pb.M;
-  const int64_t E = Pb.E;
-  const int64_t e = pr / M;
-  const int d = pr % M;
-  const bool row = valid && (i < N);
-  const double om0 = Pb.omega[d * 3 + 0], om1 = Pb.omega[d * 3 + 1], om2 = Pb.omega[d * 3 + 2];
-  const float fo0 = (float)om0, fo1 = (float)om1, fo2 = (float)om2;
-  const double* blk = Pb.elem + e * Pb.blk;
-  const float* blk32 = Pb.elem32 + e * Pb.blk;
-  float a[N];
-  double a64[N];
-  double b = 0.0;
-  if (row) {
-    const double st = Pb.sig_t[e];
-    const float st32 = (float)st;
-    static_for<0, N>([&](auto jconst) {
-      constexpr int j = decltype(jconst)::value;
-      float v = fo0 * __ldg(blk32 + j * N + i);
-      v = fmaf(fo1, __ldg(blk32 + N * N + j * N + i), v);
-      if (DIM == 3) v = fmaf(fo2, __ldg(blk32 + 2 * N * N + j * N + i), v);
-      a[j] = fmaf(st32, __ldg(blk32 + DIM * N * N + j * N + i), v);
-      double w = om0 * __ldg(blk + j * N + i);
-      w = fma(om1, __ldg(blk + N * N + j * N + i), w);
-      if (DIM == 3) w = fma(om2, __ldg(blk + 2 * N * N + j * N + i), w);
-      a64[j] = fma(st, __ldg(blk + DIM * N * N + j * N + i), w);
-    });
-    b = sa.src[e * N + i];
-    if (Pb.q_dir != nullptr) {
-      const double* qd = Pb.q_dir + ((int64_t)d * E + e) * N;
-#pragma unroll
-      for (int j = 0; j < N; ++j) b = fma(__ldg(blk + DIM * N * N + i * N + j), qd[j], b);
-    }
-  } else {
-    static_for<0, N>([&](auto jconst) {
-      a[decltype(jconst)::value] = 0.0f;
-      a64[decltype(jconst)::value] = 0.0;
-    });
-  }
-  const uint32_t code = valid ? sa.facecode[(int64_t)d * E + e] : 0u;
-  const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[(int64_t)d * E + e] : 0;
-  if constexpr (DF) wait_upwind<DIM>(Pb, sa, code, e, d, valid);
-  int mrank = 0;
-  static_for<0, 2 * DIM>([&](auto fconst) {
-    constexpr int f = decltype(fconst)::value;
-    const uint32_t mode = face_mode(code, f);
-    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
-    if (mode != MODE_NONE && fi >= 0) {
-      double Brow[NF];
-      brow64<DIM, P_>(blk, sa, mode, f, fi, mbase + mrank, om0, om1, om2, Brow);
-      static_for<0, NF>([&](auto jconst) {
-        constexpr int fj = decltype(jconst)::value;
-        a64[fvi<DIM, P_>(f, fj)] += Brow[fj];
-        a[fvi<DIM, P_>(f, fj)] += (float)Brow[fj];
-      });
-      face_rhs<DIM, P_, DF>(Pb, sa, code, f, e, d, Brow, b);
-    }
-    if (mode == MODE_MIXED) ++mrank;
-  });
-  int plk[N], myk;
-  float v[N];
-  gj32<N, W>(a, v, i, lane, row, plk, myk);
-  const float xhat = gj_apply<N, W>(v, (float)b);     // on the pivot lane of step myk
-  const double xh64 = (double)xhat;
-  double r = b;
-  static_for<0, N>([&](auto jconst) {
-    constexpr int j = decltype(jconst)::value;
-    const double xj = __shfl_sync(FULL, xh64, plk[j], W);
-    r = fma(-a64[j], xj, r);
-  });
-  const float dx = gj_apply<N, W>(v, (float)r);
-  if (row && myk >= 0) sa.psi_new[((int64_t)d * E + e) * N + myk] = xh64 + (double)dx;
-  publish<DF, W>(Pb, sa, e, d, valid, i);
-}
-
-// ------------------------------------------------------------------ mixed form, double-single residual
-// The row of A is assembled once in double-single from the (hi, lo) FP32 split of the element
-// factors; its hi part is the FP32 matrix that is factored; r = b - A xhat is accumulated in
-// double-single; b stays FP64.
-template <int DIM, int P_, bool DF>
-__device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid, int lane) {
-  using S = Shape<DIM, P_>;
-  constexpr int N = S::N, NF = S::NF, W = S::W;
-  constexpr unsigned FULL = 0xffffffffu;
-  const int i = lane % W;
-  const int M = Pb.M;
-  const int64_t E = Pb.E;
-  const int64_t e = pr / M;
-  const int d = pr % M;
-  const bool row = valid && (i < N);
-  const double om0 = Pb.omega[d * 3 + 0], om1 = Pb.omega[d * 3 + 1], om2 = Pb.omega[d * 3 + 2];
-  float oh[3], ol[3], sh, sl;
-  ds_split(om0, oh[0], ol[0]);
-  ds_split(om1, oh[1], ol[1]);
-  ds_split(om2, oh[2], ol[2]);
-  const double* blk = Pb.elem + e * Pb.blk;
-  const float* bh = Pb.elem32 + e * Pb.blk;
-  const float* bl = Pb.elem32lo + e * Pb.blk;
-  float ah[N], al[N];
-  float a[N];
-  double b = 0.0;
-  if (row) {
-    ds_split(Pb.sig_t[e], sh, sl);
-    static_for<0, N>([&](auto jconst) {
-      constexpr int j = decltype(jconst)::value;
-      float h, l, ph, pl;
-      ds_mul(oh[0], ol[0], __ldg(bh + j * N + i), __ldg(bl + j * N + i), h, l);
-      ds_mul(oh[1], ol[1], __ldg(bh + N * N + j * N + i), __ldg(bl + N * N + j * N + i), ph, pl);
-      ds_add(h, l, ph, pl);
-      if (DIM == 3) {
-        ds_mul(oh[2], ol[2], __ldg(bh + 2 * N * N + j * N + i), __ldg(bl + 2 * N * N + j * N + i), ph, pl);
-        ds_add(h, l, ph, pl);
-      }
-      ds_mul(sh, sl, __ldg(bh + DIM * N * N + j * N + i), __ldg(bl + DIM * N * N + j * N + i), ph, pl);
-      ds_add(h, l, ph, pl);
-      ah[j] = h;
-      al[j] = l;
-    });
-    b = sa.src[e * N + i];
-    if (Pb.q_dir != nullptr) {
-      const double* qd = Pb.q_dir + ((int64_t)d * E + e) * N;
-#pragma unroll
-      for (int j = 0; j < N; ++j) b = fma(__ldg(blk + DIM * N * N + i * N + j), qd[j], b);
-    }
-  } else {
-    static_for<0, N>([&](auto jconst) {
-      ah[decltype(jconst)::value] = 0.0f;
-      al[decltype(jconst)::value] = 0.0f;
-    });
-  }
-  const uint32_t code = valid ? sa.facecode[(int64_t)d * E + e] : 0u;
-  const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[(int64_t)d * E + e] : 0;
-  if constexpr (DF) wait_upwind<DIM>(Pb, sa, code, e, d, valid);
-  int mrank = 0;
-  static_for<0, 2 * DIM>([&](auto fconst) {
-    constexpr int f = decltype(fconst)::value;
-    const uint32_t mode = face_mode(code, f);
-    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
-    if (mode != MODE_NONE && fi >= 0) {
-      double Brow[NF];
-      float Bh[NF], Bl[NF];
-      if (mode == MODE_PURE) {
-        const int o = (DIM + 1) * N * N + f * DIM * NF * NF + fi * NF;
-        const double* fnm = blk + o;
-#pragma unroll
-        for (int fj = 0; fj < NF; ++fj) {
-          double v = om0 * __ldg(fnm + fj);
-          v = fma(om1, __ldg(fnm + NF * NF + fj), v);
-          if (DIM == 3) v = fma(om2, __ldg(fnm + 2 * NF * NF + fj), v);
-          Brow[fj] = -v;
-          float h, l, ph, pl;
-          ds_mul(oh[0], ol[0], __ldg(bh + o + fj), __ldg(bl + o + fj), h, l);
-          ds_mul(oh[1], ol[1], __ldg(bh + o + NF * NF + fj), __ldg(bl + o + NF * NF + fj), ph, pl);
-          ds_add(h, l, ph, pl);
-          if (DIM == 3) {
-            ds_mul(oh[2], ol[2], __ldg(bh + o + 2 * NF * NF + fj), __ldg(bl + o + 2 * NF * NF + fj), ph, pl);
-            ds_add(h, l, ph, pl);
-          }
-          Bh[fj] = -h;
-          Bl[fj] = -l;
-        }
-      } else {
-        const int64_t o = (int64_t)(mbase + mrank) * NF * NF + fi * NF;
-#pragma unroll
-        for (int fj = 0; fj < NF; ++fj) {
-          Brow[fj] = __ldg(sa.mixedB + o + fj);
-          Bh[fj] = __ldg(sa.mixedBh + o + fj);
-          Bl[fj] = __ldg(sa.mixedBl + o + fj);
-        }
-      }
-      static_for<0, NF>([&](auto jconst) {
-        constexpr int fj = decltype(jconst)::value;
-        constexpr int c = fvi<DIM, P_>(f, fj);
-        ds_add(ah[c], al[c], Bh[fj], Bl[fj]);
-      });
-      face_rhs<DIM, P_, DF>(Pb, sa, code, f, e, d, Brow, b);
-    }
-    if (mode == MODE_MIXED) ++mrank;
-  });
-  static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = ah[decltype(jconst)::value]; });
-  int plk[N], myk;
-  float v[N];
-  float bh32, bl32;
-  ds_split(b, bh32, bl32);
-  gj32<N, W>(a, v, i, lane, row, plk, myk);
-  const float xhat = gj_apply<N, W>(v, bh32);        // on the pivot lane of step myk
-  float rh = bh32, rl = bl32;
-  static_for<0, N>([&](auto jconst) {
-    constexpr int j = decltype(jconst)::value;
-    const float xj = __shfl_sync(FULL, xhat, plk[j], W);
-    float ph = ah[j] * xj;
-    float pl = fmaf(ah[j], xj, -ph);
-    pl = fmaf(al[j], xj, pl);
-    ds_add(rh, rl, -ph, -pl);
-  });
-  const float dx = gj_apply<N, W>(v, rh + rl);
-  if (row && myk >= 0) sa.psi_new[((int64_t)d * E + e) * N + myk] = (double)xhat + (double)dx;
-  publish<DF, W>(Pb, sa, e, d, valid, i);
-}
-
-template <int DIM, int P_, int PREC, bool DF>
-__device__ __forceinline__ void solve_item(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid,
-                                           int lane) {
-  if constexpr (PREC == SN_PREC_FP64) body64<DIM, P_, DF>(Pb, sa, pr, valid, lane);
-  else if constexpr (PREC == SN_PREC_MIXED) bodymx<DIM, P_, DF>(Pb, sa, pr, valid, lane);
-  else bodyds<DIM, P_, DF>(Pb, sa, pr, valid, lane);
-}
 
 // One wavefront level: pairs[0, count) are mutually independent.
 template <int DIM, int P_, int PREC>
