@@ -287,9 +287,45 @@ def run_gpu(args):
     }
     if not args.no_batch:
         out["batched"] = run_batch(g, torch, args)
+    if not args.no_3d:
+        out["twisted_3d"] = run_3d(g, torch, args)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample_dirs)
     return out
+
+
+def run_3d(g, torch, args):
+    """3D cyclic workload: 32^3 hexahedra, Q2 geometry twisted by 60 degrees about z, p = 2 (27 dofs),
+    S8 (80 directions), sigma_t = 1, sigma_s = 0.8, q = 1: 2,621,440 updates per sweep."""
+    import sn_inputs as si
+    prob = si.make_config("3d_twist_q2_p2_s8")
+    stream = torch.cuda.Stream()
+    ctx = g.setup_problem(prob, device=0, stream=stream.cuda_stream)
+    t0 = time.time()
+    gs = ctx.sn_build_graph("face", 10)
+    res = {"workload": "32^3 Q2 hexes twisted 60 deg about z, p=2, S8 (80 dirs), sigma_t=1, sigma_s=0.8, q=1",
+           "updates_per_sweep": int(prob.mesh.n_elem * len(prob.w)), "graph_build_s": time.time() - t0,
+           "removed_arcs": int(gs["n_removed"]), "max_scc": int(gs["max_scc"]), "levels": int(gs["max_level"] + 1),
+           "mixed_faces": int(gs["n_mixed_faces"])}
+    ups = prob.mesh.n_elem * len(prob.w)
+    E, N = prob.mesh.n_elem, 27
+    for name, prec in (("mixed_ds", g.SN_PREC_MIXED_DS), ("fp64", g.SN_PREC_FP64)):
+        mode, bps = ctx.sn_autotune(prec)
+        for _ in range(args.warmup):
+            ctx.sn_si_step(prec)
+        tot = 0.0
+        steps = max(5, args.steps // 4)
+        for _ in range(steps):
+            _, ms = ctx.sn_si_step(prec, time_sweep=True)
+            tot += ms
+        phi = np.zeros((E, N))
+        t1 = time.perf_counter()
+        r = ctx.sn_source_iterate(1e-8, 3000, prec, phi_out=phi)
+        res[name] = {"sweep_updates_per_s": ups * steps / (tot / 1e3), "sweep_ms": tot / steps,
+                     "schedule": {"mode": "dataflow" if mode == 1 else "levels", "blocks_per_sm": bps},
+                     "time_to_1e-8_s": time.perf_counter() - t1, "iters": r["iters"], "converged": r["converged"]}
+    ctx.close()
+    return res
 
 
 def run_batch(g, torch, args):
@@ -398,6 +434,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-problem batched measurement")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3D twisted-mesh measurement")
     ap.add_argument("--launch", default="levels", choices=["levels", "dataflow"],
                     help="sweep schedule: one launch per level, or one persistent dataflow launch")
     ap.add_argument("--form", default="mixed_ds", choices=["fp64", "mixed", "mixed_ds"],

@@ -234,6 +234,62 @@ sn_status sn_batch_si_step(sn_batch* batch, int precision, double* residuals, fl
 sn_status sn_batch_source_iterate(sn_batch* batch, double tol, int max_iter, int precision, int32_t* iters,
                                   double* residuals, double* ms_total);
 
+/* ---- Learned flux predictor (this project's addition; the paper has none).  A per-element
+ * MLP -- x -> tanh(x W1 + b1) -> tanh(. W2 + b2) -> . W3 + b3, width 64, BF16 weights, FP32
+ * accumulation, trained by Adam on the device -- supplies the initial scalar flux of source
+ * iteration and a post-sweep correction; plain source iteration is the fallback and the judge
+ * of convergence.  Packed parameters: W1 [n_in][64], b1 [64], W2 [64][64], b2 [64],
+ * W3 [64][n_out], b3 [n_out] (FP32 masters). */
+#define SN_FEATURES 16
+typedef struct sn_mlp sn_mlp;
+/* n_in, n_out in 1..64; Glorot-uniform weights from a seeded mt19937_64, zero biases. */
+sn_status sn_mlp_create(sn_mlp** out, int device, void* cuda_stream, int n_in, int n_out, uint64_t seed);
+void sn_mlp_destroy(sn_mlp* mlp);
+int64_t sn_mlp_num_params(const sn_mlp* mlp);
+/* get (may be NULL) receives the FP32 parameters; set (may be NULL) replaces them (and resets
+ * the Adam state).  Host or device pointers. */
+sn_status sn_mlp_params(sn_mlp* mlp, float* get, const float* set);
+/* y [rows][n_out] = MLP(x [rows][n_in]). */
+sn_status sn_mlp_forward(sn_mlp* mlp, int64_t rows, const float* x, float* y);
+/* loss = sum (y - t)^2 / (2 rows n_out) and its gradient grad [n_params] (may be NULL). */
+sn_status sn_mlp_grad(sn_mlp* mlp, int64_t rows, const float* x, const float* target, float* loss, float* grad);
+/* Adam (lr, 0.9, 0.999, 1e-8) over epochs x minibatches of batch_rows consecutive rows (the rows
+ * are expected pre-shuffled; minibatch order is shuffled by seed).  *loss_out = mean loss of the
+ * last epoch. */
+sn_status sn_mlp_train(sn_mlp* mlp, int64_t rows, const float* x, const float* target, int epochs, int batch_rows,
+                       float lr, uint64_t seed, float* loss_out);
+
+/* Per-element predictor data of a context (graph built):
+ *   sn_predictor_features: feat [n_elem][16] = sigma_t, sigma_s, sigma_a, c, mean q, mean control
+ *     point (3), volume, size h, distance to the mesh bounding box, boundary faces, mean face-
+ *     neighbour sigma_t, sigma_t h, log sigma_t, mean face-neighbour c; phi_ref [n_elem] (may be
+ *     NULL) = 4 pi max(mean q, 1e-12) / max(sigma_a, 1e-3 sigma_t).
+ *   sn_predictor_init_targets: target [n_elem][N] = phi / phi_ref (initial-guess model output).
+ *   sn_predictor_corr_data: from iterates phi_a, phi_b, phi_c (l-1, l, l+1): inputs [n_elem][18] =
+ *     features, |c-b|/|b-a| (clipped at 10), log10(|c-b|/|c|); with phi_inf, target [n_elem] =
+ *     log1p(clip(<phi_inf - c, c - b> / |c - b|^2, 0, 500)) (correction model output). */
+sn_status sn_predictor_features(sn_ctx* ctx, float* feat, double* phi_ref);
+sn_status sn_predictor_init_targets(sn_ctx* ctx, const double* phi, float* target);
+sn_status sn_predictor_corr_data(sn_ctx* ctx, const double* phi_a, const double* phi_b, const double* phi_c,
+                                 const double* phi_inf, float* inputs, float* target);
+
+typedef struct {
+  float init_mean[SN_FEATURES], init_istd[SN_FEATURES];          /* feature normalisation */
+  float corr_mean[SN_FEATURES + 2], corr_istd[SN_FEATURES + 2];  /* correction-input normalisation */
+  int32_t corr_start, corr_every;                                /* correction schedule */
+} sn_predictor_cfg;
+
+/* Source iteration with the predictor: phi_0 = init_model(normalised features) * phi_ref (or 0
+ * without init_model); from iteration corr_start, every corr_every plain steps, the correction
+ * model's g per element gives phi <- phi + expm1(clip(g, 0, 6)) (phi - phi_prev) and the
+ * scattering source is refreshed.  A correction is accepted if the next plain residual is below
+ * the one before it; otherwise corrections stop (plain source iteration continues).
+ * Convergence is declared only on a step whose input was not corrected.  n_accepted /
+ * n_rejected may be NULL. */
+sn_status sn_source_iterate_learned(sn_ctx* ctx, double tol, int max_iter, int precision, sn_mlp* init_model,
+                                    sn_mlp* corr_model, const sn_predictor_cfg* cfg, double* phi_out,
+                                    sn_si_stats* stats, int32_t* n_accepted, int32_t* n_rejected);
+
 /* Scalar-flux moment and relative change WITHOUT a context and without allocating anything
  * (the paper has no counterpart: this is a deployment entry point).
  *

@@ -25,7 +25,9 @@ EXPORTED = ["sn_create", "sn_destroy", "sn_last_error", "sn_set_mesh", "sn_set_d
             "sn_si_result", "sn_kernel_launches", "sn_moment_noalloc", "sn_set_launch", "sn_autotune",
             "sn_batch_create", "sn_batch_destroy", "sn_batch_last_error", "sn_batch_updates_per_sweep",
             "sn_batch_set_launch", "sn_batch_tune", "sn_batch_si_begin", "sn_batch_si_step",
-            "sn_batch_source_iterate"]
+            "sn_batch_source_iterate", "sn_mlp_create", "sn_mlp_destroy", "sn_mlp_num_params", "sn_mlp_params",
+            "sn_mlp_forward", "sn_mlp_grad", "sn_mlp_train", "sn_predictor_features", "sn_predictor_init_targets",
+            "sn_predictor_corr_data", "sn_source_iterate_learned"]
 
 
 class sn_graph_stats(ctypes.Structure):
@@ -41,6 +43,15 @@ class sn_graph_stats(ctypes.Structure):
 class sn_si_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("residual", ctypes.c_double),
                 ("ms_total", ctypes.c_double)]
+
+
+SN_FEATURES = 16
+
+
+class sn_predictor_cfg(ctypes.Structure):
+    _fields_ = [("init_mean", ctypes.c_float * SN_FEATURES), ("init_istd", ctypes.c_float * SN_FEATURES),
+                ("corr_mean", ctypes.c_float * (SN_FEATURES + 2)), ("corr_istd", ctypes.c_float * (SN_FEATURES + 2)),
+                ("corr_start", ctypes.c_int32), ("corr_every", ctypes.c_int32)]
 
 
 class SnError(RuntimeError):
@@ -83,6 +94,19 @@ def load(path=LIB_PATH):
         "sn_batch_si_begin": (I, [P]),
         "sn_batch_si_step": (I, [P, I, P, ctypes.POINTER(ctypes.c_float)]),
         "sn_batch_source_iterate": (I, [P, D, I, I, P, P, ctypes.POINTER(D)]),
+        "sn_mlp_create": (I, [ctypes.POINTER(P), I, P, I, I, ctypes.c_uint64]),
+        "sn_mlp_destroy": (None, [P]),
+        "sn_mlp_num_params": (I64, [P]),
+        "sn_mlp_params": (I, [P, P, P]),
+        "sn_mlp_forward": (I, [P, I64, P, P]),
+        "sn_mlp_grad": (I, [P, I64, P, P, ctypes.POINTER(ctypes.c_float), P]),
+        "sn_mlp_train": (I, [P, I64, P, P, I, I, ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)]),
+        "sn_predictor_features": (I, [P, P, P]),
+        "sn_predictor_init_targets": (I, [P, P, P]),
+        "sn_predictor_corr_data": (I, [P, P, P, P, P, P, P]),
+        "sn_source_iterate_learned": (I, [P, D, I, I, P, P, ctypes.POINTER(sn_predictor_cfg), P,
+                                          ctypes.POINTER(sn_si_stats), ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32)]),
         "sn_moment_noalloc": (I, [I, P, I, I64, I, P, P, P, P, ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
@@ -163,12 +187,14 @@ class Context:
             pass
 
     def sn_set_mesh(self, dim, n_elem, r, ctrl, face_nbr, nbr_face, orient):
+        self._n_elem = int(n_elem)
         return self._check(self._lib.sn_set_mesh(self._c, dim, n_elem, r, _ptr(ctrl, np.float64, "ctrl"),
                                                  _ptr(face_nbr, np.int64, "face_nbr"),
                                                  _ptr(nbr_face, np.int32, "nbr_face"),
                                                  _ptr(orient, np.int32, "orient")))
 
     def sn_set_discretization(self, p, face_subdiv=2):
+        self._p = int(p)
         return self._check(self._lib.sn_set_discretization(self._c, p, face_subdiv))
 
     def sn_set_quadrature(self, omega, w):
@@ -245,6 +271,41 @@ class Context:
         return self._check(self._lib.sn_si_result(self._c, _ptr(phi_out, np.float64, "phi_out"),
                                                   _ptr(psi_out, np.float64, "psi_out")))
 
+    def sn_predictor_features(self):
+        E = self._n_elem
+        feat = np.zeros((E, SN_FEATURES), dtype=np.float32)
+        ref = np.zeros(E)
+        self._check(self._lib.sn_predictor_features(self._c, feat.ctypes.data, ref.ctypes.data))
+        return feat, ref
+
+    def sn_predictor_init_targets(self, phi):
+        t = np.zeros(phi.shape, dtype=np.float32)
+        self._check(self._lib.sn_predictor_init_targets(self._c, _ptr(phi, np.float64, "phi"), t.ctypes.data))
+        return t
+
+    def sn_predictor_corr_data(self, phi_a, phi_b, phi_c, phi_inf=None):
+        E = phi_a.shape[0]
+        x = np.zeros((E, SN_FEATURES + 2), dtype=np.float32)
+        t = np.zeros(E, dtype=np.float32) if phi_inf is not None else None
+        self._check(self._lib.sn_predictor_corr_data(self._c, _ptr(phi_a, np.float64, "phi_a"),
+                                                     _ptr(phi_b, np.float64, "phi_b"), _ptr(phi_c, np.float64, "phi_c"),
+                                                     _ptr(phi_inf, np.float64, "phi_inf"), x.ctypes.data,
+                                                     None if t is None else t.ctypes.data))
+        return x, t
+
+    def sn_source_iterate_learned(self, tol, max_iter, precision, init_model, corr_model, cfg, phi_out=None):
+        st = sn_si_stats()
+        acc, rej = ctypes.c_int32(), ctypes.c_int32()
+        s = self._lib.sn_source_iterate_learned(self._c, float(tol), int(max_iter), int(precision),
+                                                None if init_model is None else init_model._m,
+                                                None if corr_model is None else corr_model._m, ctypes.byref(cfg),
+                                                _ptr(phi_out, np.float64, "phi_out"), ctypes.byref(st),
+                                                ctypes.byref(acc), ctypes.byref(rej))
+        if s not in (SN_OK, SN_ENOTCONVERGED):
+            self._check(s)
+        return dict(status=s, iters=st.iters, converged=bool(st.converged), residual=st.residual,
+                    ms_total=st.ms_total, accepted=acc.value, rejected=rej.value)
+
     def sn_kernel_launches(self):
         return self._lib.sn_kernel_launches(self._c)
 
@@ -307,3 +368,66 @@ class Batch:
         if st not in (SN_OK, SN_ENOTCONVERGED):
             self._check(st)
         return dict(status=st, iters=its, residuals=res, ms_total=ms.value)
+
+
+class MLP:
+    """Owns one sn_mlp (3 layers, width 64, BF16 weights)."""
+
+    def __init__(self, n_in, n_out, seed=0, device=0, stream=None):
+        self._lib = lib()
+        self._m = ctypes.c_void_p()
+        self.n_in, self.n_out = n_in, n_out
+        st = self._lib.sn_mlp_create(ctypes.byref(self._m), int(device), stream, int(n_in), int(n_out), int(seed))
+        if st != SN_OK:
+            raise SnError(st, "sn_mlp_create failed")
+
+    def _check(self, st, what="sn_mlp"):
+        if st != SN_OK:
+            raise SnError(st, f"{what} failed")
+        return st
+
+    def close(self):
+        if self._m:
+            self._lib.sn_mlp_destroy(self._m)
+            self._m = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sn_mlp_num_params(self):
+        return self._lib.sn_mlp_num_params(self._m)
+
+    def get_params(self):
+        p = np.zeros(self.sn_mlp_num_params(), dtype=np.float32)
+        self._check(self._lib.sn_mlp_params(self._m, p.ctypes.data, None))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self._lib.sn_mlp_params(self._m, None, p.ctypes.data))
+
+    def sn_mlp_forward(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.zeros((x.shape[0], self.n_out), dtype=np.float32)
+        self._check(self._lib.sn_mlp_forward(self._m, x.shape[0], x.ctypes.data, y.ctypes.data))
+        return y
+
+    def sn_mlp_grad(self, x, t):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        g = np.zeros(self.sn_mlp_num_params(), dtype=np.float32)
+        L = ctypes.c_float()
+        self._check(self._lib.sn_mlp_grad(self._m, x.shape[0], x.ctypes.data, t.ctypes.data, ctypes.byref(L),
+                                          g.ctypes.data))
+        return L.value, g
+
+    def sn_mlp_train(self, x, t, epochs, batch_rows=4096, lr=1e-3, seed=0):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        L = ctypes.c_float()
+        self._check(self._lib.sn_mlp_train(self._m, x.shape[0], x.ctypes.data, t.ctypes.data, int(epochs),
+                                           int(batch_rows), float(lr), int(seed), ctypes.byref(L)))
+        return L.value

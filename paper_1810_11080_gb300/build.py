@@ -46,8 +46,9 @@ def build(verbose=False, extra_nvcc=()):
         "sweep.cu": [],
         "noalloc.cu": [],
         "batch.cu": [],
+        "mlp.cu": [],
     }
-    cpp = ["api.cpp", "batch_api.cpp", "tables.cpp", "fas.cpp"]
+    cpp = ["api.cpp", "batch_api.cpp", "predictor.cpp", "tables.cpp", "fas.cpp"]
     jobs = []
     for src, flags in cu.items():
         obj = os.path.join(BUILD, src + ".o")

@@ -1,0 +1,43 @@
+"""Train the learned flux predictor for the 3D Q2 p=2 S12 workload family (random smooth
+perturbation 0.1 h, log-normal sigma_t, scattering ratio 0.99, q = 1, vacuum) on solves the
+method itself generates, and save the model.
+
+    python -m paper_1810_11080_gb300.train_predictor --solves 2000 --n 8 --out <path.npz>
+
+Training problems use seeds 1000, 1002, ... (mesh seed s, material seed s + 1); evaluation
+problems elsewhere use seeds >= 5000.
+"""
+import argparse
+import json
+import time
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--solves", type=int, default=2000)
+    ap.add_argument("--n", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--out", required=True)
+    args = ap.parse_args()
+    import torch
+    import sn_inputs as si
+    from . import learned
+    stream = torch.cuda.Stream()
+    t0 = time.time()
+    probs = [si.make_config("3d_smooth_q2_p2_s12", n=args.n, seed=1000 + 2 * k) for k in range(args.solves)]
+    data = learned.generate(probs, stream=stream.cuda_stream)
+    t1 = time.time()
+    model = learned.train(data, epochs=args.epochs, stream=stream.cuda_stream)
+    t2 = time.time()
+    model["train_solves"] = args.solves
+    model["train_n"] = args.n
+    learned.save(model, args.out)
+    print(json.dumps({"solves": args.solves, "n": args.n, "rows_init": int(model["rows_init"]),
+                      "rows_corr": int(model["rows_corr"]), "init_loss": float(model["init_loss"]),
+                      "corr_loss": float(model["corr_loss"]), "gen_s": t1 - t0, "train_s": t2 - t1}))
+
+
+if __name__ == "__main__":
+    main()

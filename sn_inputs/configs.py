@@ -42,8 +42,9 @@ CONFIGS = {
 }
 
 
-def make_config(name, n=None, sn=None, p=None, reorient_seed=None):
-    """Build one workload (optionally at a reduced grid size n)."""
+def make_config(name, n=None, sn=None, p=None, reorient_seed=None, seed=None):
+    """Build one workload (optionally at a reduced grid size n).  seed replaces the mesh and
+    material seeds of the random workloads by (seed, seed + 1)."""
     c = dict(CONFIGS[name])
     if n is not None:
         c["n"] = n
@@ -59,9 +60,9 @@ def make_config(name, n=None, sn=None, p=None, reorient_seed=None):
         st = np.ones(ne)
         ss = 0.5 * np.ones(ne)
     elif name == "2d_smooth_q3_p3_s8":
-        mesh = structured_mesh((n, n), r, disp_random_smooth(h, seed=11))
+        mesh = structured_mesh((n, n), r, disp_random_smooth(h, seed=11 if seed is None else seed))
         ne = mesh.n_elem
-        rng = np.random.default_rng(12)
+        rng = np.random.default_rng(12 if seed is None else seed + 1)
         st = rng.uniform(0.5, 5.0, size=ne)
         ss = 0.9 * st
     elif name == "3d_twist_q2_p2_s8":
@@ -70,9 +71,9 @@ def make_config(name, n=None, sn=None, p=None, reorient_seed=None):
         st = np.ones(ne)
         ss = 0.8 * np.ones(ne)
     elif name == "3d_smooth_q2_p2_s12":
-        mesh = structured_mesh((n, n, n), r, disp_random_smooth_3d(h, seed=41))
+        mesh = structured_mesh((n, n, n), r, disp_random_smooth_3d(h, seed=41 if seed is None else seed))
         ne = mesh.n_elem
-        rng = np.random.default_rng(42)
+        rng = np.random.default_rng(42 if seed is None else seed + 1)
         st = np.exp(rng.normal(0.0, 1.0, size=ne))
         ss = 0.99 * st
     else:
