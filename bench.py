@@ -115,6 +115,22 @@ def make_problem(n=None):
     return si.make_config(WORKLOAD, n=n)
 
 
+def max_over_ranks(value):
+    """Largest value over all ranks (the job is as slow as its slowest replica)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world_size, units_per_rank, steps, ms_max):
+    """Whole-job units per second: every replica processes units_per_rank per step."""
+    return world_size * units_per_rank * steps / (ms_max / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -187,12 +203,8 @@ def run_gpu(args):
         torch.cuda.synchronize()
         barrier()
         clk = clocks.stop(local)
-        ms_total = ev0.elapsed_time(ev1)
-        if ws > 1:
-            t = torch.tensor([ms_total], dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms_total = float(t.item())
-        return dict(value=ws * updates * args.steps / (ms_total / 1e3), ms_per_step=ms_total / args.steps,
+        ms_total = max_over_ranks(ev0.elapsed_time(ev1))
+        return dict(value=job_throughput(ws, updates, args.steps, ms_total), ms_per_step=ms_total / args.steps,
                     sweep_ms_per_step=sweep_ms / args.steps, launches=int(ctx.sn_kernel_launches() - l0),
                     clocks=clk)
 
@@ -289,6 +301,8 @@ def run_gpu(args):
         out["batched"] = run_batch(g, torch, args)
     if not args.no_3d:
         out["twisted_3d"] = run_3d(g, torch, args)
+    if not args.no_learned:
+        out["learned"] = run_learned(g, torch, args)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample_dirs)
     return out
@@ -326,6 +340,54 @@ def run_3d(g, torch, args):
                      "time_to_1e-8_s": time.perf_counter() - t1, "iters": r["iters"], "converged": r["converged"]}
     ctx.close()
     return res
+
+
+def run_learned(g, torch, args):
+    """3D learned-predictor workload family: n^3 Q2 hexes with seeded smooth perturbation 0.1h,
+    p = 2, S12 (168 directions), sigma_t = exp(N(0,1)), c = 0.99, q = 1, the workload's own seeds
+    (41, 42; the predictor was trained on seeds >= 1000).  Time to a 1e-8 relative scalar-flux
+    change: plain FP64 source iteration vs the predictor (FP64 and double-single sweeps)."""
+    import sn_inputs as si
+    from paper_1810_11080_gb300 import learned
+    path = os.path.join(ROOT, "paper_1810_11080_gb300", "models", "predictor_3d_q2_p2_s12.npz")
+    if not os.path.exists(path):
+        return {"unavailable": "trained predictor file not present"}
+    stream = torch.cuda.Stream()
+    model = learned.load(path)
+    init, corr, cfg = learned.build(model, stream=stream.cuda_stream)
+    prob = si.make_config("3d_smooth_q2_p2_s12", n=args.learned_n)
+    ctx = g.setup_problem(prob, device=0, stream=stream.cuda_stream)
+    ctx.sn_build_graph("face", 10)
+    E, N = prob.mesh.n_elem, 27
+    out = {"workload": f"{args.learned_n}^3 Q2 hexes, smooth perturbation 0.1h (seed 41), p=2, S12 (168 dirs), "
+                       f"sigma_t=exp(N(0,1)) (seed 42), c=0.99, q=1",
+           "updates_per_sweep": int(E * len(prob.w)), "train_solves": int(model.get("train_solves", 0)),
+           "train_n": int(model.get("train_n", 0))}
+    ref = np.zeros((E, N))
+    runs = {}
+    for name, prec, use in (("plain_fp64", g.SN_PREC_FP64, False), ("learned_fp64", g.SN_PREC_FP64, True),
+                            ("plain_mixed_ds", g.SN_PREC_MIXED_DS, False),
+                            ("learned_mixed_ds", g.SN_PREC_MIXED_DS, True)):
+        phi = np.zeros((E, N))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if use:
+            r = ctx.sn_source_iterate_learned(1e-8, 5000, prec, init, corr, cfg, phi_out=phi)
+        else:
+            r = ctx.sn_source_iterate(1e-8, 5000, prec, phi_out=phi)
+        dt = time.perf_counter() - t0
+        if name == "plain_fp64":
+            ref = phi.copy()
+        runs[name] = {"seconds": dt, "iters": r["iters"], "converged": r["converged"],
+                      "phi_rel_l2_vs_plain_fp64": float(np.linalg.norm(phi - ref) / np.linalg.norm(ref))}
+        if use:
+            runs[name]["corrections_accepted"] = r["accepted"]
+            runs[name]["corrections_rejected"] = r["rejected"]
+    out.update(runs)
+    out["speedup_learned_mixed_ds_vs_plain_fp64"] = runs["plain_fp64"]["seconds"] / runs["learned_mixed_ds"]["seconds"]
+    out["speedup_learned_fp64_vs_plain_fp64"] = runs["plain_fp64"]["seconds"] / runs["learned_fp64"]["seconds"]
+    ctx.close()
+    return out
 
 
 def run_batch(g, torch, args):
@@ -435,6 +497,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-problem batched measurement")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D twisted-mesh measurement")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-predictor measurement")
+    ap.add_argument("--learned-n", type=int, default=24, help="mesh size n^3 of the learned-predictor measurement")
     ap.add_argument("--launch", default="levels", choices=["levels", "dataflow"],
                     help="sweep schedule: one launch per level, or one persistent dataflow launch")
     ap.add_argument("--form", default="mixed_ds", choices=["fp64", "mixed", "mixed_ds"],

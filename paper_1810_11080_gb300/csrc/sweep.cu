@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(128) sweep_level_kernel(DevProblem Pb, SweepAr
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t item = gwarp * S::SPW + lane / S::W;
+  pdl_launch_dependents();
   const int32_t pr = item < count ? pairs[item] : -1;
   solve_item<DIM, P_, PREC, false>(Pb, sa, pr < 0 ? 0 : pr, pr >= 0, lane);
 }
@@ -62,8 +63,16 @@ static cudaError_t launch_level_t(const DevProblem& P, const SweepArgs& sa, cons
   const int64_t per_block = (threads / 32) * S::SPW;
   const int64_t blocks = (count + per_block - 1) / per_block;
   if (blocks == 0) return cudaSuccess;
-  sweep_level_kernel<DIM, P_, PREC><<<(unsigned)blocks, threads, 0, s>>>(P, sa, pairs, count);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, sweep_level_kernel<DIM, P_, PREC>, P, sa, pairs, count);
 }
 
 template <int DIM, int P_, int PREC>

@@ -81,6 +81,12 @@ __device__ __forceinline__ void ds_split(double x, float& h, float& l) {
   l = (float)(x - (double)h);
 }
 
+// ---- programmatic dependent launch (per-level schedule): the next level's grid may start as
+// soon as every CTA of this one has begun; it waits for this grid's completion (and memory
+// flush) only where it first reads data produced by earlier launches.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---- dataflow synchronisation
 constexpr long long SPIN_LIMIT = 1LL << 20;     // ~0.1-1 s of polling before giving up
 
@@ -352,7 +358,6 @@ __device__ __forceinline__ void body64(const DevProblem& Pb, const SweepArgs& sa
       if (DIM == 3) v = fma(om2, __ldg(blk + 2 * N * N + j * N + i), v);
       a[j] = fma(st, __ldg(blk + DIM * N * N + j * N + i), v);
     });
-    b = sa.src[e * N + i];
     if (Pb.q_dir != nullptr) {
       const double* qd = Pb.q_dir + ((int64_t)d * E + e) * N;
 #pragma unroll
@@ -364,6 +369,8 @@ __device__ __forceinline__ void body64(const DevProblem& Pb, const SweepArgs& sa
   const uint32_t code = valid ? sa.facecode[(int64_t)d * E + e] : 0u;
   const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[(int64_t)d * E + e] : 0;
   if constexpr (DF) wait_upwind<DIM>(Pb, sa, code, e, d, valid);
+  else pdl_wait();                       // sources and upwind traces come from earlier launches
+  if (row) b += sa.src[e * N + i];
   int mrank = 0;
   static_for<0, 2 * DIM>([&](auto fconst) {
     constexpr int f = decltype(fconst)::value;
@@ -457,7 +464,6 @@ __device__ __forceinline__ void bodymx(const DevProblem& Pb, const SweepArgs& sa
       if (DIM == 3) w = fma(om2, __ldg(blk + 2 * N * N + j * N + i), w);
       a64[j] = fma(st, __ldg(blk + DIM * N * N + j * N + i), w);
     });
-    b = sa.src[e * N + i];
     if (Pb.q_dir != nullptr) {
       const double* qd = Pb.q_dir + ((int64_t)d * E + e) * N;
 #pragma unroll
@@ -472,6 +478,8 @@ __device__ __forceinline__ void bodymx(const DevProblem& Pb, const SweepArgs& sa
   const uint32_t code = valid ? sa.facecode[(int64_t)d * E + e] : 0u;
   const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[(int64_t)d * E + e] : 0;
   if constexpr (DF) wait_upwind<DIM>(Pb, sa, code, e, d, valid);
+  else pdl_wait();                       // sources and upwind traces come from earlier launches
+  if (row) b += sa.src[e * N + i];
   int mrank = 0;
   static_for<0, 2 * DIM>([&](auto fconst) {
     constexpr int f = decltype(fconst)::value;
@@ -548,7 +556,6 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
       ah[j] = h;
       al[j] = l;
     });
-    b = sa.src[e * N + i];
     if (Pb.q_dir != nullptr) {
       const double* qd = Pb.q_dir + ((int64_t)d * E + e) * N;
 #pragma unroll
@@ -563,6 +570,8 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
   const uint32_t code = valid ? sa.facecode[(int64_t)d * E + e] : 0u;
   const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[(int64_t)d * E + e] : 0;
   if constexpr (DF) wait_upwind<DIM>(Pb, sa, code, e, d, valid);
+  else pdl_wait();                       // sources and upwind traces come from earlier launches
+  if (row) b += sa.src[e * N + i];
   int mrank = 0;
   static_for<0, 2 * DIM>([&](auto fconst) {
     constexpr int f = decltype(fconst)::value;
