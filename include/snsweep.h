@@ -223,8 +223,9 @@ int64_t sn_batch_updates_per_sweep(const sn_batch* batch);
 sn_status sn_batch_set_launch(sn_batch* batch, int mode, int blocks_per_sm);
 /* Autotuner over the same candidates as sn_autotune; resets the iteration state. */
 sn_status sn_batch_tune(sn_batch* batch, int precision, int* mode_out, int* blocks_per_sm_out);
-/* phi <- 0, psi <- 0 in every problem. */
-sn_status sn_batch_si_begin(sn_batch* batch);
+/* psi <- 0 and phi <- phi0[k] (host or device [E_k][N_k]; phi0 or phi0[k] NULL = 0) in every
+ * problem. */
+sn_status sn_batch_si_begin(sn_batch* batch, const double* const* phi0);
 /* One source iteration of every problem; residuals [n_problems] (may be NULL) receive each
  * problem's relative scalar-flux change; *ms_sweep (may be NULL) the device time of the step. */
 sn_status sn_batch_si_step(sn_batch* batch, int precision, double* residuals, float* ms_sweep);
@@ -286,6 +287,9 @@ typedef struct {
  * the one before it; otherwise corrections stop (plain source iteration continues).
  * Convergence is declared only on a step whose input was not corrected.  n_accepted /
  * n_rejected may be NULL. */
+/* phi0 [n_elem][N] = init_model(normalised features) * phi_ref: the predicted initial flux. */
+sn_status sn_predictor_initial_phi(sn_ctx* ctx, sn_mlp* init_model, const sn_predictor_cfg* cfg, double* phi0);
+
 sn_status sn_source_iterate_learned(sn_ctx* ctx, double tol, int max_iter, int precision, sn_mlp* init_model,
                                     sn_mlp* corr_model, const sn_predictor_cfg* cfg, double* phi_out,
                                     sn_si_stats* stats, int32_t* n_accepted, int32_t* n_rejected);

@@ -27,7 +27,7 @@ EXPORTED = ["sn_create", "sn_destroy", "sn_last_error", "sn_set_mesh", "sn_set_d
             "sn_batch_set_launch", "sn_batch_tune", "sn_batch_si_begin", "sn_batch_si_step",
             "sn_batch_source_iterate", "sn_mlp_create", "sn_mlp_destroy", "sn_mlp_num_params", "sn_mlp_params",
             "sn_mlp_forward", "sn_mlp_grad", "sn_mlp_train", "sn_predictor_features", "sn_predictor_init_targets",
-            "sn_predictor_corr_data", "sn_source_iterate_learned"]
+            "sn_predictor_corr_data", "sn_source_iterate_learned", "sn_predictor_initial_phi"]
 
 
 class sn_graph_stats(ctypes.Structure):
@@ -91,7 +91,8 @@ def load(path=LIB_PATH):
         "sn_batch_updates_per_sweep": (I64, [P]),
         "sn_batch_set_launch": (I, [P, I, I]),
         "sn_batch_tune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
-        "sn_batch_si_begin": (I, [P]),
+        "sn_batch_si_begin": (I, [P, P]),
+        "sn_predictor_initial_phi": (I, [P, P, ctypes.POINTER(sn_predictor_cfg), P]),
         "sn_batch_si_step": (I, [P, I, P, ctypes.POINTER(ctypes.c_float)]),
         "sn_batch_source_iterate": (I, [P, D, I, I, P, P, ctypes.POINTER(D)]),
         "sn_mlp_create": (I, [ctypes.POINTER(P), I, P, I, I, ctypes.c_uint64]),
@@ -293,6 +294,11 @@ class Context:
                                                      None if t is None else t.ctypes.data))
         return x, t
 
+    def sn_predictor_initial_phi(self, init_model, cfg):
+        phi = np.zeros((self._n_elem, self._N))
+        self._check(self._lib.sn_predictor_initial_phi(self._c, init_model._m, ctypes.byref(cfg), phi.ctypes.data))
+        return phi
+
     def sn_source_iterate_learned(self, tol, max_iter, precision, init_model, corr_model, cfg, phi_out=None):
         st = sn_si_stats()
         acc, rej = ctypes.c_int32(), ctypes.c_int32()
@@ -349,8 +355,13 @@ class Batch:
         self._check(self._lib.sn_batch_tune(self._b, int(precision), ctypes.byref(m), ctypes.byref(b)))
         return m.value, b.value
 
-    def sn_batch_si_begin(self):
-        return self._check(self._lib.sn_batch_si_begin(self._b))
+    def sn_batch_si_begin(self, phi0=None):
+        """phi0: None or a list of per-problem arrays (or None entries)."""
+        if phi0 is None:
+            return self._check(self._lib.sn_batch_si_begin(self._b, None))
+        keep = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in phi0]
+        arr = (ctypes.c_void_p * len(keep))(*[None if a is None else a.ctypes.data for a in keep])
+        return self._check(self._lib.sn_batch_si_begin(self._b, arr))
 
     def sn_batch_si_step(self, precision=SN_PREC_MIXED_DS, time_sweep=False):
         res = np.zeros(len(self._ctxs))

@@ -84,6 +84,16 @@ void free_graph_state(sn_ctx* c) {
   dfree(c->d_src);
   dfree(c->d_done);
   for (auto& p : c->d_stage) dfree(p);
+  for (int k = 0; k < 2; ++k) {
+    dfree(c->d_psih[k]);
+    dfree(c->d_psil[k]);
+    dfree(c->d_scr_h[k]);
+    dfree(c->d_scr_l[k]);
+  }
+  dfree(c->d_srch);
+  dfree(c->d_srcl);
+  dfree(c->d_om32);
+  dfree(c->d_st32);
   c->level_off.clear();
   c->h_removed.clear();
   c->n_removed = 0;
@@ -133,6 +143,8 @@ sn::DevProblem sn_ctx::dev() const {
   P.blk = blk;
   P.elem32 = d_elem32;
   P.elem32lo = d_elem32lo;
+  P.om32 = d_om32;
+  P.st32 = d_st32;
   return P;
 }
 
@@ -409,6 +421,12 @@ sn_status ensure_buffers(sn_ctx* c) {
   if (!c->d_phi2) SN_CUDA(c, dalloc(c->d_phi2, nphi));
   if (!c->d_src) SN_CUDA(c, dalloc(c->d_src, nphi));
   if (!c->d_done) SN_CUDA(c, dalloc(c->d_done, (size_t)c->M * c->E));
+  for (int k = 0; k < 2; ++k) {
+    if (!c->d_psih[k]) SN_CUDA(c, dalloc(c->d_psih[k], npsi));
+    if (!c->d_psil[k]) SN_CUDA(c, dalloc(c->d_psil[k], npsi));
+  }
+  if (!c->d_srch) SN_CUDA(c, dalloc(c->d_srch, nphi));
+  if (!c->d_srcl) SN_CUDA(c, dalloc(c->d_srcl, nphi));
   return SN_OK;
 }
 
@@ -624,6 +642,28 @@ sn_status sn_build_graph(sn_ctx* c, int weighting, int exact_max, sn_graph_stats
   for (auto& x : ev) cudaEventDestroy(x);
   gs.max_level = Lmax;
   gs.n_mixed_faces = nm;
+  {
+    // FP32 (hi, lo) splits of the directions and of sigma_t for the double-single form
+    std::vector<float> om(6 * (size_t)M), stt(2 * (size_t)E), sig(E);
+    std::vector<double> sigd(E);
+    SN_CUDA(c, cudaMemcpy(sigd.data(), c->d_sig_t, E * 8, cudaMemcpyDeviceToHost));
+    for (int64_t d = 0; d < M; ++d)
+      for (int k = 0; k < 3; ++k) {
+        const double x = c->h_omega[d * 3 + k];
+        const float h = (float)x;
+        om[d * 6 + 2 * k] = h;
+        om[d * 6 + 2 * k + 1] = (float)(x - (double)h);
+      }
+    for (int64_t e = 0; e < E; ++e) {
+      const float h = (float)sigd[e];
+      stt[2 * e] = h;
+      stt[2 * e + 1] = (float)(sigd[e] - (double)h);
+    }
+    SN_CUDA(c, dalloc(c->d_om32, om.size()));
+    SN_CUDA(c, dalloc(c->d_st32, stt.size()));
+    SN_CUDA(c, cudaMemcpy(c->d_om32, om.data(), om.size() * 4, cudaMemcpyHostToDevice));
+    SN_CUDA(c, cudaMemcpy(c->d_st32, stt.data(), stt.size() * 4, cudaMemcpyHostToDevice));
+  }
   sn_status st = ensure_buffers(c);
   if (st != SN_OK) return st;
   c->graph_ready = true;
@@ -702,9 +742,43 @@ sn_status run_levels(sn_ctx* c, int prec, const double* psi_old, double* psi_new
   int* err = reinterpret_cast<int*>(c->d_red + 2);
   unsigned long long* head = c->d_red + 3;
   SweepArgs sa{c->d_facecode, c->d_mixed_off, c->d_mixedB, c->d_mixedB32, c->d_mixedB32lo, c->d_src,
-               psi_old, psi_new, c->d_done, err, c->d_pairs};
+               psi_old, psi_new, c->d_done, err, c->d_pairs,
+               c->d_srch, c->d_srcl, nullptr, nullptr, nullptr, nullptr};
+  // (hi, lo) splits of the two iterates: the context's own buffers, or scratch for caller buffers
+  bool convert_old = false;
+  const size_t npsi = (size_t)c->M * c->E * c->N;
+  for (int k = 0; k < 2; ++k) {
+    if (psi_old == c->d_psi[k]) {
+      sa.psi_old_h = c->d_psih[k];
+      sa.psi_old_l = c->d_psil[k];
+    }
+    if (psi_new == c->d_psi[k]) {
+      sa.psi_new_h = c->d_psih[k];
+      sa.psi_new_l = c->d_psil[k];
+    }
+  }
+  if (prec == SN_PREC_MIXED_DS) {
+    for (int k = 0; k < 2; ++k)
+      if (!c->d_scr_h[k] && (k == 0 ? !sa.psi_old_h : !sa.psi_new_h)) {
+        SN_CUDA(c, dalloc(c->d_scr_h[k], npsi));
+        SN_CUDA(c, dalloc(c->d_scr_l[k], npsi));
+      }
+    if (!sa.psi_old_h) {
+      sa.psi_old_h = c->d_scr_h[0];
+      sa.psi_old_l = c->d_scr_l[0];
+      convert_old = true;
+    }
+    if (!sa.psi_new_h) {
+      sa.psi_new_h = c->d_scr_h[1];
+      sa.psi_new_l = c->d_scr_l[1];
+    }
+  }
   const int mode = c->launch_mode;
   auto launch_all = [&]() -> cudaError_t {
+    if (convert_old) {
+      cudaError_t e = launch_split(psi_old, c->d_scr_h[0], c->d_scr_l[0], (int64_t)npsi, c->stream);
+      if (e != cudaSuccess) return e;
+    }
     if (mode == SN_LAUNCH_DATAFLOW) {
       cudaError_t e = cudaMemsetAsync(c->d_done, 0, (size_t)c->M * c->E * sizeof(int), c->stream);
       if (e == cudaSuccess) e = cudaMemsetAsync(c->d_red + 2, 0, 2 * sizeof(unsigned long long), c->stream);
@@ -795,7 +869,7 @@ sn_status sn_sweep(sn_ctx* c, const double* phi_in, const double* psi_old, doubl
     dnew = c->d_stage[2];
   }
   DevProblem P = c->dev();
-  SN_CUDA(c, launch_source(P, dphi, c->d_src, c->stream));
+  SN_CUDA(c, launch_source(P, dphi, c->d_src, c->d_srch, c->d_srcl, c->stream));
   c->launches++;
   if ((st = run_levels(c, precision, dold, dnew)) != SN_OK) return st;
   if (host_out) {
@@ -820,7 +894,7 @@ sn_status sn_moment(sn_ctx* c, const double* psi, const double* phi_prev, double
   double* dout = host_out ? c->d_phi2 : phi_out;
   SN_CUDA(c, cudaMemsetAsync(c->d_red, 0, 2 * sizeof(unsigned long long), c->stream));
   DevProblem P = c->dev();
-  SN_CUDA(c, launch_moment(P, dpsi, dprev, dout, c->d_src, c->d_red, c->stream));
+  SN_CUDA(c, launch_moment(P, dpsi, dprev, dout, c->d_src, c->d_srch, c->d_srcl, c->d_red, c->stream));
   c->launches++;
   unsigned long long red[2];
   SN_CUDA(c, cudaMemcpyAsync(red, c->d_red, sizeof(red), cudaMemcpyDeviceToHost, c->stream));
@@ -842,8 +916,10 @@ sn_status sn_si_begin(sn_ctx* c, const double* phi0) {
   if (phi0) SN_CUDA(c, cudaMemcpyAsync(c->d_phi, phi0, nphi * 8, cudaMemcpyDefault, s));
   else SN_CUDA(c, cudaMemsetAsync(c->d_phi, 0, nphi * 8, s));
   SN_CUDA(c, cudaMemsetAsync(c->d_psi[0], 0, npsi * 8, s));
+  SN_CUDA(c, cudaMemsetAsync(c->d_psih[0], 0, npsi * 4, s));
+  SN_CUDA(c, cudaMemsetAsync(c->d_psil[0], 0, npsi * 4, s));
   DevProblem P = c->dev();
-  SN_CUDA(c, launch_source(P, c->d_phi, c->d_src, s));
+  SN_CUDA(c, launch_source(P, c->d_phi, c->d_src, c->d_srch, c->d_srcl, s));
   c->launches++;
   SN_CUDA(c, cudaStreamSynchronize(s));
   c->si_cur = 0;
@@ -868,7 +944,8 @@ sn_status sn_si_step(sn_ctx* c, int precision, double* residual, float* ms_sweep
   if (ms_sweep) SN_CUDA(c, cudaEventRecord(c->ev_b, s));
   SN_CUDA(c, cudaMemsetAsync(c->d_red, 0, 2 * sizeof(unsigned long long), s));
   DevProblem P = c->dev();
-  SN_CUDA(c, launch_moment(P, c->d_psi[cur ^ 1], c->d_phi, c->d_phi2, c->d_src, c->d_red, s));
+  SN_CUDA(c, launch_moment(P, c->d_psi[cur ^ 1], c->d_phi, c->d_phi2, c->d_src, c->d_srch, c->d_srcl, c->d_red,
+                           s));
   c->launches++;
   unsigned long long red[3];
   SN_CUDA(c, cudaMemcpyAsync(red, c->d_red, sizeof(red), cudaMemcpyDeviceToHost, s));

@@ -141,6 +141,11 @@ __global__ void moment_batch_kernel(const DevProblem* __restrict__ probs, const 
     double s = 0.0;
     for (int n = 0; n < N; ++n) s = fma(Mm[n], fma(cs, sphi[le * N + n], qe[n]), s);
     ma.src[e * N + m] = s;
+    if (ma.src_h != nullptr) {
+      const float h = (float)s;
+      ma.src_h[e * N + m] = h;
+      ma.src_l[e * N + m] = (float)(s - (double)h);
+    }
   }
 }
 

@@ -141,15 +141,24 @@ sn_status sn_batch_create(sn_batch** out, int n_problems, sn_ctx* const* problem
   for (int k = 0; k < n; ++k) {
     sn_ctx* c = b->ctx[k];
     SweepArgs base{c->d_facecode, c->d_mixed_off, c->d_mixedB, c->d_mixedB32, c->d_mixedB32lo, c->d_src,
-                   nullptr, nullptr, b->d_done + done_off[k], errw, c->d_pairs};
+                   nullptr, nullptr, b->d_done + done_off[k], errw, c->d_pairs,
+                   c->d_srch, c->d_srcl, nullptr, nullptr, nullptr, nullptr};
     args0[k] = base;
     args0[k].psi_old = c->d_psi[0];
     args0[k].psi_new = c->d_psi[1];
+    args0[k].psi_old_h = c->d_psih[0];
+    args0[k].psi_old_l = c->d_psil[0];
+    args0[k].psi_new_h = c->d_psih[1];
+    args0[k].psi_new_l = c->d_psil[1];
     args1[k] = base;
     args1[k].psi_old = c->d_psi[1];
     args1[k].psi_new = c->d_psi[0];
-    m0[k] = MomentArgs{c->d_psi[1], b->phiA[k], b->phiB[k], c->d_src};
-    m1[k] = MomentArgs{c->d_psi[0], b->phiB[k], b->phiA[k], c->d_src};
+    args1[k].psi_old_h = c->d_psih[1];
+    args1[k].psi_old_l = c->d_psil[1];
+    args1[k].psi_new_h = c->d_psih[0];
+    args1[k].psi_new_l = c->d_psil[0];
+    m0[k] = MomentArgs{c->d_psi[1], b->phiA[k], b->phiB[k], c->d_src, c->d_srch, c->d_srcl};
+    m1[k] = MomentArgs{c->d_psi[0], b->phiB[k], b->phiA[k], c->d_src, c->d_srch, c->d_srcl};
   }
   // tasks ordered by level across problems; each problem's levels are padded to its 32/W
   int Lmax = 0;
@@ -214,16 +223,21 @@ sn_status sn_batch_set_launch(sn_batch* b, int mode, int blocks_per_sm) {
   return SN_OK;
 }
 
-sn_status sn_batch_si_begin(sn_batch* b) {
+sn_status sn_batch_si_begin(sn_batch* b, const double* const* phi0) {
   if (!b) return SN_EINVAL;
   SB_CUDA(b, cudaSetDevice(b->device));
   for (int k = 0; k < b->n; ++k) {
     sn_ctx* c = b->ctx[k];
     const size_t npsi = (size_t)c->M * c->E * c->N, nphi = (size_t)c->E * c->N;
     SB_CUDA(b, cudaMemsetAsync(c->d_psi[0], 0, npsi * 8, b->stream));
-    SB_CUDA(b, cudaMemsetAsync(b->phiA[k], 0, nphi * 8, b->stream));
+    SB_CUDA(b, cudaMemsetAsync(c->d_psih[0], 0, npsi * 4, b->stream));
+    SB_CUDA(b, cudaMemsetAsync(c->d_psil[0], 0, npsi * 4, b->stream));
+    if (phi0 && phi0[k])
+      SB_CUDA(b, cudaMemcpyAsync(b->phiA[k], phi0[k], nphi * 8, cudaMemcpyDefault, b->stream));
+    else
+      SB_CUDA(b, cudaMemsetAsync(b->phiA[k], 0, nphi * 8, b->stream));
     DevProblem P = c->dev();
-    SB_CUDA(b, launch_source(P, b->phiA[k], c->d_src, b->stream));
+    SB_CUDA(b, launch_source(P, b->phiA[k], c->d_src, c->d_srch, c->d_srcl, b->stream));
     c->d_phi = b->phiA[k];
     c->d_phi2 = b->phiB[k];
     c->si_cur = 0;
@@ -292,7 +306,7 @@ sn_status sn_batch_source_iterate(sn_batch* b, double tol, int max_iter, int pre
   if (!b) return SN_EINVAL;
   SB_REQ(b, tol > 0.0 && max_iter >= 1, SN_EINVAL, "tol > 0 and max_iter >= 1 required");
   auto t0 = std::chrono::steady_clock::now();
-  sn_status st = sn_batch_si_begin(b);
+  sn_status st = sn_batch_si_begin(b, nullptr);
   if (st != SN_OK) return st;
   std::vector<double> res(b->n, INFINITY);
   std::vector<int32_t> it_conv(b->n, -1);
@@ -326,7 +340,7 @@ sn_status sn_batch_tune(sn_batch* b, int precision, int* mode_out, int* blocks_p
   for (auto& cd : cand) {
     sn_status st = sn_batch_set_launch(b, cd[0], cd[1]);
     if (st != SN_OK) return st;
-    if ((st = sn_batch_si_begin(b)) != SN_OK) return st;
+    if ((st = sn_batch_si_begin(b, nullptr)) != SN_OK) return st;
     if ((st = sn_batch_si_step(b, precision, nullptr, nullptr)) != SN_OK) return st;
     if ((st = sn_batch_si_step(b, precision, nullptr, nullptr)) != SN_OK) return st;
     float tot = 0.0f;
@@ -343,7 +357,7 @@ sn_status sn_batch_tune(sn_batch* b, int precision, int* mode_out, int* blocks_p
   }
   sn_status st = sn_batch_set_launch(b, bm, bb);
   if (st != SN_OK) return st;
-  if ((st = sn_batch_si_begin(b)) != SN_OK) return st;
+  if ((st = sn_batch_si_begin(b, nullptr)) != SN_OK) return st;
   if (mode_out) *mode_out = bm;
   if (blocks_per_sm_out) *blocks_per_sm_out = bb;
   return SN_OK;

@@ -70,6 +70,8 @@ struct DevProblem {
   int64_t blk;               // doubles per element block
   const float* elem32;       // [E][blk] FP32 rounding of elem (mixed forms) or null
   const float* elem32lo;     // [E][blk] FP32 rounding of elem - elem32 (double-single form) or null
+  const float* om32;         // [M][6] (hi, lo) FP32 split of each direction's three components
+  const float* st32;         // [E][2] (hi, lo) FP32 split of sigma_t
 };
 
 // Per-sweep buffers seen by the sweep kernels.
@@ -85,6 +87,13 @@ struct SweepArgs {
   int* done;                  // [M][E] completion flags (dataflow schedule) or null
   int* err;                   // device error word (dataflow wait gave up) or null
   const int32_t* pairs;       // level-ordered (e*M + d) work list (-1 = padding); batched kernels
+  // double-single form: FP32 (hi, lo) splits of the source and of both angular-flux iterates
+  const float* src_h;
+  const float* src_l;
+  const float* psi_old_h;
+  const float* psi_old_l;
+  float* psi_new_h;
+  float* psi_new_l;
 };
 
 // Per-problem pointers of the fused moment / source kernel in a batch.
@@ -93,6 +102,8 @@ struct MomentArgs {
   const double* phi_prev;     // [E][N]
   double* phi_out;            // [E][N]
   double* src;                // [E][N] scattering + isotropic source for the next sweep
+  float* src_h;               // its FP32 (hi, lo) split (double-single form)
+  float* src_l;
 };
 
 // Batched sweep over problems of one dimension (batch.cu).  A task = up to 32/W consecutive
@@ -126,9 +137,11 @@ cudaError_t launch_mixed_blocks(const DevProblem& P, const int32_t* iface, int64
 cudaError_t launch_levels_init(const DevProblem& P, int32_t* levels, cudaStream_t s);
 cudaError_t launch_levels_relax(const DevProblem& P, const uint32_t* facecode, int32_t* levels, int* changed,
                                 cudaStream_t s);
-cudaError_t launch_source(const DevProblem& P, const double* phi, double* src, cudaStream_t s);
+cudaError_t launch_source(const DevProblem& P, const double* phi, double* src, float* src_h, float* src_l,
+                          cudaStream_t s);
 cudaError_t launch_moment(const DevProblem& P, const double* psi, const double* phi_prev, double* phi_out,
-                          double* src, unsigned long long* red, cudaStream_t s);
+                          double* src, float* src_h, float* src_l, unsigned long long* red, cudaStream_t s);
+cudaError_t launch_split(const double* x, float* h, float* l, int64_t n, cudaStream_t s);
 cudaError_t launch_sweep_level(const DevProblem& P, int precision, const int32_t* pairs, int64_t count,
                                const SweepArgs& sa, cudaStream_t s);
 cudaError_t launch_sweep_flow(const DevProblem& P, int precision, const int32_t* pairs, int64_t count,
@@ -189,6 +202,11 @@ struct sn_ctx {
   // iteration state
   double* d_psi[2] = {nullptr, nullptr};
   double *d_phi = nullptr, *d_phi2 = nullptr, *d_src = nullptr;
+  float* d_psih[2] = {nullptr, nullptr};   // FP32 (hi, lo) splits of d_psi (double-single form)
+  float* d_psil[2] = {nullptr, nullptr};
+  float *d_srch = nullptr, *d_srcl = nullptr;
+  float *d_scr_h[2] = {nullptr, nullptr}, *d_scr_l[2] = {nullptr, nullptr};   // for caller psi buffers
+  float *d_om32 = nullptr, *d_st32 = nullptr;
   double* d_stage[3] = {nullptr, nullptr, nullptr};   // host-pointer staging
   unsigned long long* d_red = nullptr;   // [0..1] residual maxima, [2] error word, [3] queue head
   int* d_flag = nullptr;

@@ -392,6 +392,43 @@ sn_status sn_predictor_corr_data(sn_ctx* c, const double* phi_a, const double* p
   return SN_OK;
 }
 
+sn_status sn_predictor_initial_phi(sn_ctx* c, sn_mlp* init_model, const sn_predictor_cfg* cfg, double* phi0) {
+  if (!c || !init_model || !cfg || !phi0) return SN_EINVAL;
+  if (!c->graph_ready) return SN_ESTATE;
+  if (init_model->n_in != SN_FEATURES || init_model->n_out != c->N) return SN_EINVAL;
+  cudaSetDevice(c->device);
+  const int64_t E = c->E;
+  const size_t EN = (size_t)E * c->N;
+  cudaStream_t s = c->stream;
+  Staged S;
+  float *feat = nullptr, *featn = nullptr, *y = nullptr, *norm = nullptr;
+  double* ref = nullptr;
+  auto al = [&](auto*& p, size_t n) {
+    if (cudaMalloc((void**)&p, n * sizeof(*p)) != cudaSuccess) return false;
+    S.own.push_back(p);
+    return true;
+  };
+  if (!al(feat, E * SN_FEATURES) || !al(featn, E * SN_FEATURES) || !al(y, EN) || !al(norm, 2 * SN_FEATURES) ||
+      !al(ref, E))
+    return SN_ENOMEM;
+  float hn[2 * SN_FEATURES];
+  std::memcpy(hn, cfg->init_mean, sizeof(cfg->init_mean));
+  std::memcpy(hn + SN_FEATURES, cfg->init_istd, sizeof(cfg->init_istd));
+  if (cudaMemcpyAsync(norm, hn, sizeof(hn), cudaMemcpyHostToDevice, s) != cudaSuccess) return SN_ECUDA;
+  sn_status st = sn_predictor_features(c, feat, ref);
+  if (st != SN_OK) return st;
+  if (launch_predictor_normalise(E, SN_FEATURES, feat, norm, norm + SN_FEATURES, featn, s) != cudaSuccess)
+    return SN_ECUDA;
+  init_model->stream = s;
+  if ((st = sn_mlp_forward(init_model, E, featn, y)) != SN_OK) return st;
+  double* dout = S.out(phi0, EN);
+  if (!dout) return SN_ENOMEM;
+  if (launch_predictor_scale(E, c->N, ref, nullptr, nullptr, y, dout, s) != cudaSuccess) return SN_ECUDA;
+  if (dout != phi0) cudaMemcpyAsync(phi0, dout, EN * 8, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SN_ECUDA;
+  return SN_OK;
+}
+
 sn_status sn_source_iterate_learned(sn_ctx* c, double tol, int max_iter, int precision, sn_mlp* init_model,
                                     sn_mlp* corr_model, const sn_predictor_cfg* cfg, double* phi_out,
                                     sn_si_stats* stats, int32_t* n_accepted, int32_t* n_rejected) {
@@ -465,7 +502,7 @@ sn_status sn_source_iterate_learned(sn_ctx* c, double tol, int max_iter, int pre
         return SN_ECUDA;
       if ((st = sn_mlp_forward(corr_model, E, cinn, y)) != SN_OK) return st;
       if (launch_predictor_apply_corr(E, c->N, y, hin, c->d_phi, s) != cudaSuccess) return SN_ECUDA;
-      if (launch_source(c->dev(), c->d_phi, c->d_src, s) != cudaSuccess) return SN_ECUDA;
+      if (launch_source(c->dev(), c->d_phi, c->d_src, c->d_srch, c->d_srcl, s) != cudaSuccess) return SN_ECUDA;
       c->launches += 4;
       res_before = res;
       corrected_last = true;

@@ -30,7 +30,6 @@ __global__ void __launch_bounds__(128) sweep_level_kernel(DevProblem Pb, SweepAr
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t item = gwarp * S::SPW + lane / S::W;
-  pdl_launch_dependents();
   const int32_t pr = item < count ? pairs[item] : -1;
   solve_item<DIM, P_, PREC, false>(Pb, sa, pr < 0 ? 0 : pr, pr >= 0, lane);
 }
@@ -70,8 +69,9 @@ static cudaError_t launch_level_t(const DevProblem& P, const SweepArgs& sa, cons
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
+  // The FP64 form is bound by the FP64 pipe: an overlapped next level would only compete for it.
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = (PREC == SN_PREC_FP64) ? 0 : 1;
   return cudaLaunchKernelEx(&cfg, sweep_level_kernel<DIM, P_, PREC>, P, sa, pairs, count);
 }
 
@@ -135,8 +135,8 @@ __device__ inline void block_max2(double& a, double& b) {
 // phi = sum_d w_d psi_d (d ascending); residual maxima; src = M (q + sigma_s phi / (4 pi)).
 // Block = whole elements: threads (element slot, node).
 __global__ void moment_kernel(DevProblem P, const double* __restrict__ psi, const double* __restrict__ phi_prev,
-                              double* __restrict__ phi_out, double* __restrict__ src,
-                              unsigned long long* red) {
+                              double* __restrict__ phi_out, double* __restrict__ src, float* __restrict__ src_h,
+                              float* __restrict__ src_l, unsigned long long* red) {
   extern __shared__ double sphi[];
   const int N = P.N;
   const int epb = blockDim.x / N;
@@ -168,22 +168,43 @@ __global__ void moment_kernel(DevProblem P, const double* __restrict__ psi, cons
     double s = 0.0;
     for (int n = 0; n < N; ++n) s = fma(Mm[n], fma(c, sphi[le * N + n], qe[n]), s);
     src[e * N + m] = s;
+    if (src_h != nullptr) {
+      const float h = (float)s;
+      src_h[e * N + m] = h;
+      src_l[e * N + m] = (float)(s - (double)h);
+    }
   }
 }
 
 static unsigned moment_threads(int N) { return (unsigned)((256 / N) * N); }
 
 cudaError_t launch_moment(const DevProblem& P, const double* psi, const double* phi_prev, double* phi_out,
-                          double* src, unsigned long long* red, cudaStream_t s) {
+                          double* src, float* src_h, float* src_l, unsigned long long* red, cudaStream_t s) {
   const unsigned th = moment_threads(P.N);
   const int64_t epb = th / P.N;
   const int64_t blocks = (P.E + epb - 1) / epb;
-  moment_kernel<<<(unsigned)blocks, th, th * sizeof(double), s>>>(P, psi, phi_prev, phi_out, src, red);
+  moment_kernel<<<(unsigned)blocks, th, th * sizeof(double), s>>>(P, psi, phi_prev, phi_out, src, src_h, src_l, red);
   return cudaGetLastError();
 }
 
-cudaError_t launch_source(const DevProblem& P, const double* phi, double* src, cudaStream_t s) {
-  return launch_moment(P, nullptr, phi, nullptr, src, nullptr, s);
+cudaError_t launch_source(const DevProblem& P, const double* phi, double* src, float* src_h, float* src_l,
+                          cudaStream_t s) {
+  return launch_moment(P, nullptr, phi, nullptr, src, src_h, src_l, nullptr, s);
+}
+
+// x = h + l with h = fl32(x), l = fl32(x - h).
+__global__ void split_kernel(const double* __restrict__ x, float* __restrict__ h, float* __restrict__ l, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float a = (float)x[i];
+    h[i] = a;
+    l[i] = (float)(x[i] - (double)a);
+  }
+}
+
+cudaError_t launch_split(const double* x, float* h, float* l, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  split_kernel<<<1216, 256, 0, s>>>(x, h, l, n);
+  return cudaGetLastError();
 }
 
 }  // namespace sn

@@ -369,7 +369,10 @@ __device__ __forceinline__ void body64(const DevProblem& Pb, const SweepArgs& sa
   const uint32_t code = valid ? sa.facecode[(int64_t)d * E + e] : 0u;
   const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[(int64_t)d * E + e] : 0;
   if constexpr (DF) wait_upwind<DIM>(Pb, sa, code, e, d, valid);
-  else pdl_wait();                       // sources and upwind traces come from earlier launches
+  else {
+    pdl_wait();                          // sources and upwind traces come from earlier launches
+    pdl_launch_dependents();             // ... and only then may the next level start: one level ahead
+  }
   if (row) b += sa.src[e * N + i];
   int mrank = 0;
   static_for<0, 2 * DIM>([&](auto fconst) {
@@ -425,7 +428,15 @@ __device__ __forceinline__ void body64(const DevProblem& Pb, const SweepArgs& sa
     if (mine) x = xj;
     if (myk >= 0 && myk < j) b = fma(-a[j], xj, b);
   });
-  if (row && myk >= 0) sa.psi_new[((int64_t)d * E + e) * N + myk] = x;
+  if (row && myk >= 0) {
+    const int64_t o = ((int64_t)d * E + e) * N + myk;
+    sa.psi_new[o] = x;
+    if (sa.psi_new_h != nullptr) {       // keep the double-single split of the iterate current
+      const float h = (float)x;
+      sa.psi_new_h[o] = h;
+      sa.psi_new_l[o] = (float)(x - (double)h);
+    }
+  }
   publish<DF, W>(Pb, sa, e, d, valid, i);
 }
 
@@ -478,7 +489,10 @@ __device__ __forceinline__ void bodymx(const DevProblem& Pb, const SweepArgs& sa
   const uint32_t code = valid ? sa.facecode[(int64_t)d * E + e] : 0u;
   const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[(int64_t)d * E + e] : 0;
   if constexpr (DF) wait_upwind<DIM>(Pb, sa, code, e, d, valid);
-  else pdl_wait();                       // sources and upwind traces come from earlier launches
+  else {
+    pdl_wait();                          // sources and upwind traces come from earlier launches
+    pdl_launch_dependents();             // ... and only then may the next level start: one level ahead
+  }
   if (row) b += sa.src[e * N + i];
   int mrank = 0;
   static_for<0, 2 * DIM>([&](auto fconst) {
@@ -509,7 +523,16 @@ __device__ __forceinline__ void bodymx(const DevProblem& Pb, const SweepArgs& sa
     r = fma(-a64[j], xj, r);
   });
   const float dx = gj_apply<N, W>(v, (float)r);
-  if (row && myk >= 0) sa.psi_new[((int64_t)d * E + e) * N + myk] = xh64 + (double)dx;
+  if (row && myk >= 0) {
+    const int64_t o = ((int64_t)d * E + e) * N + myk;
+    const double x = xh64 + (double)dx;
+    sa.psi_new[o] = x;
+    if (sa.psi_new_h != nullptr) {       // keep the double-single split of the iterate current
+      const float h = (float)x;
+      sa.psi_new_h[o] = h;
+      sa.psi_new_l[o] = (float)(x - (double)h);
+    }
+  }
   publish<DF, W>(Pb, sa, e, d, valid, i);
 }
 
@@ -520,7 +543,7 @@ __device__ __forceinline__ void bodymx(const DevProblem& Pb, const SweepArgs& sa
 template <int DIM, int P_, bool DF>
 __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid, int lane) {
   using S = Shape<DIM, P_>;
-  constexpr int N = S::N, NF = S::NF, W = S::W;
+  constexpr int N = S::N, NF = S::NF, W = S::W, NP1 = S::NP1;
   constexpr unsigned FULL = 0xffffffffu;
   const int i = lane % W;
   const int M = Pb.M;
@@ -528,19 +551,19 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
   const int64_t e = pr / M;
   const int d = pr % M;
   const bool row = valid && (i < N);
-  const double om0 = Pb.omega[d * 3 + 0], om1 = Pb.omega[d * 3 + 1], om2 = Pb.omega[d * 3 + 2];
-  float oh[3], ol[3], sh, sl;
-  ds_split(om0, oh[0], ol[0]);
-  ds_split(om1, oh[1], ol[1]);
-  ds_split(om2, oh[2], ol[2]);
-  const double* blk = Pb.elem + e * Pb.blk;
+  float oh[3], ol[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    oh[k] = Pb.om32[d * 6 + 2 * k];
+    ol[k] = Pb.om32[d * 6 + 2 * k + 1];
+  }
   const float* bh = Pb.elem32 + e * Pb.blk;
   const float* bl = Pb.elem32lo + e * Pb.blk;
   float ah[N], al[N];
   float a[N];
-  double b = 0.0;
+  float rbh = 0.0f, rbl = 0.0f;                 // right-hand side in double-single
   if (row) {
-    ds_split(Pb.sig_t[e], sh, sl);
+    const float sh = Pb.st32[2 * e], sl = Pb.st32[2 * e + 1];
     static_for<0, N>([&](auto jconst) {
       constexpr int j = decltype(jconst)::value;
       float h, l, ph, pl;
@@ -556,10 +579,13 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
       ah[j] = h;
       al[j] = l;
     });
-    if (Pb.q_dir != nullptr) {
+    if (Pb.q_dir != nullptr) {           // direction-dependent source (tests): FP64, then split
+      const double* blk = Pb.elem + e * Pb.blk;
       const double* qd = Pb.q_dir + ((int64_t)d * E + e) * N;
+      double qb = 0.0;
 #pragma unroll
-      for (int j = 0; j < N; ++j) b = fma(__ldg(blk + DIM * N * N + i * N + j), qd[j], b);
+      for (int j = 0; j < N; ++j) qb = fma(__ldg(blk + DIM * N * N + i * N + j), qd[j], qb);
+      ds_split(qb, rbh, rbl);
     }
   } else {
     static_for<0, N>([&](auto jconst) {
@@ -569,26 +595,24 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
   }
   const uint32_t code = valid ? sa.facecode[(int64_t)d * E + e] : 0u;
   const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[(int64_t)d * E + e] : 0;
-  if constexpr (DF) wait_upwind<DIM>(Pb, sa, code, e, d, valid);
-  else pdl_wait();                       // sources and upwind traces come from earlier launches
-  if (row) b += sa.src[e * N + i];
+  if constexpr (DF) {
+    wait_upwind<DIM>(Pb, sa, code, e, d, valid);
+  } else {
+    pdl_wait();                          // sources and upwind traces come from earlier launches
+    pdl_launch_dependents();             // ... and only then may the next level start: one level ahead
+  }
+  if (row) ds_add(rbh, rbl, sa.src_h[e * N + i], sa.src_l[e * N + i]);
   int mrank = 0;
   static_for<0, 2 * DIM>([&](auto fconst) {
     constexpr int f = decltype(fconst)::value;
     const uint32_t mode = face_mode(code, f);
     const int fi = row ? on_face<DIM, P_>(f, i) : -1;
     if (mode != MODE_NONE && fi >= 0) {
-      double Brow[NF];
       float Bh[NF], Bl[NF];
       if (mode == MODE_PURE) {
         const int o = (DIM + 1) * N * N + f * DIM * NF * NF + fi * NF;
-        const double* fnm = blk + o;
 #pragma unroll
         for (int fj = 0; fj < NF; ++fj) {
-          double v = om0 * __ldg(fnm + fj);
-          v = fma(om1, __ldg(fnm + NF * NF + fj), v);
-          if (DIM == 3) v = fma(om2, __ldg(fnm + 2 * NF * NF + fj), v);
-          Brow[fj] = -v;
           float h, l, ph, pl;
           ds_mul(oh[0], ol[0], __ldg(bh + o + fj), __ldg(bl + o + fj), h, l);
           ds_mul(oh[1], ol[1], __ldg(bh + o + NF * NF + fj), __ldg(bl + o + NF * NF + fj), ph, pl);
@@ -604,7 +628,6 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
         const int64_t o = (int64_t)(mbase + mrank) * NF * NF + fi * NF;
 #pragma unroll
         for (int fj = 0; fj < NF; ++fj) {
-          Brow[fj] = __ldg(sa.mixedB + o + fj);
           Bh[fj] = __ldg(sa.mixedBh + o + fj);
           Bl[fj] = __ldg(sa.mixedBl + o + fj);
         }
@@ -614,18 +637,50 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
         constexpr int c = fvi<DIM, P_>(f, fj);
         ds_add(ah[c], al[c], Bh[fj], Bl[fj]);
       });
-      face_rhs<DIM, P_, DF>(Pb, sa, code, f, e, d, Brow, b);
+      // b += B trace: upwind neighbour's (hi, lo) split or the incident flux
+      const int64_t nb = Pb.nbr[e * 2 * DIM + f];
+      if (nb >= 0) {
+        const bool lag = face_lagged(code, f);
+        const float* ph_ = lag ? sa.psi_old_h : sa.psi_new_h;
+        const float* pl_ = lag ? sa.psi_old_l : sa.psi_new_l;
+        const int fn = Pb.nbr_face[e * 2 * DIM + f], oc = Pb.orient[e * 2 * DIM + f];
+        const int64_t base = ((int64_t)d * E + nb) * N;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) {
+          int t0, t1;
+          orient_map_idx(DIM, oc, P_, fj % NP1, fj / NP1, t0, t1);
+          const int64_t idx = base + face_vol_index(DIM, P_, fn, t0, t1);
+          float th, tl;
+          if (!lag && DF) {
+            th = __ldcg(ph_ + idx);
+            tl = __ldcg(pl_ + idx);
+          } else {
+            th = __ldg(ph_ + idx);
+            tl = __ldg(pl_ + idx);
+          }
+          float qh, ql;
+          ds_mul(Bh[fj], Bl[fj], th, tl, qh, ql);
+          ds_add(rbh, rbl, qh, ql);
+        }
+      } else if (Pb.psi_inc != nullptr) {
+        const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * 2 * DIM + f]) * NF;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) {
+          float th, tl, qh, ql;
+          ds_split(__ldg(pin + fj), th, tl);
+          ds_mul(Bh[fj], Bl[fj], th, tl, qh, ql);
+          ds_add(rbh, rbl, qh, ql);
+        }
+      }
     }
     if (mode == MODE_MIXED) ++mrank;
   });
   static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = ah[decltype(jconst)::value]; });
   int plk[N], myk;
   float v[N];
-  float bh32, bl32;
-  ds_split(b, bh32, bl32);
   gj32<N, W>(a, v, i, lane, row, plk, myk);
-  const float xhat = gj_apply<N, W>(v, bh32);        // on the pivot lane of step myk
-  float rh = bh32, rl = bl32;
+  const float xhat = gj_apply<N, W>(v, rbh);        // on the pivot lane of step myk
+  float rh = rbh, rl = rbl;
   static_for<0, N>([&](auto jconst) {
     constexpr int j = decltype(jconst)::value;
     const float xj = __shfl_sync(FULL, xhat, plk[j], W);
@@ -635,7 +690,14 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
     ds_add(rh, rl, -ph, -pl);
   });
   const float dx = gj_apply<N, W>(v, rh + rl);
-  if (row && myk >= 0) sa.psi_new[((int64_t)d * E + e) * N + myk] = (double)xhat + (double)dx;
+  if (row && myk >= 0) {
+    float oh2, ol2;
+    ds_two_sum(xhat, dx, oh2, ol2);
+    const int64_t o = ((int64_t)d * E + e) * N + myk;
+    sa.psi_new_h[o] = oh2;
+    sa.psi_new_l[o] = ol2;
+    sa.psi_new[o] = (double)oh2 + (double)ol2;
+  }
   publish<DF, W>(Pb, sa, e, d, valid, i);
 }
 

@@ -29,26 +29,77 @@ def solve_history(ctx, precision=SN_PREC_FP64, tol=1e-11, max_iter=3000):
     return phis
 
 
-def generate(problems, precision=SN_PREC_FP64, stream=None):
-    """Features / targets of every training problem: returns dict of stacked float32 arrays."""
+def batched_histories(problems, start=None, group=128, precision=SN_PREC_FP64, tol=1e-11, max_iter=3000,
+                      stream=None):
+    """Source-iteration histories [phi_0, phi_1, ...] of many problems, solved group by group in
+    batched launches.  start(ctx) -> phi_0 (or None for 0).  Yields (ctx, history); the context is
+    closed after the caller's loop body."""
+    from ._lib import Batch
+    for g0 in range(0, len(problems), group):
+        grp = problems[g0:g0 + group]
+        ctxs = []
+        for prob in grp:
+            c = setup_problem(prob, stream=stream)
+            c.sn_build_graph("face", 10)
+            ctxs.append(c)
+        phi0 = [None if start is None else start(c) for c in ctxs]
+        b = Batch(ctxs, stream)
+        b.sn_batch_si_begin(phi0)
+        hist = [[np.zeros((c._n_elem, c._N)) if p is None else p] for c, p in zip(ctxs, phi0)]
+        done = [False] * len(ctxs)
+        for _ in range(max_iter):
+            res, _ = b.sn_batch_si_step(precision)
+            for k, c in enumerate(ctxs):
+                if done[k]:
+                    continue
+                phi = np.zeros((c._n_elem, c._N))
+                c.sn_si_result(phi, None)
+                hist[k].append(phi)
+                done[k] = res[k] < tol
+            if all(done):
+                break
+        b.close()
+        for c, h in zip(ctxs, hist):
+            yield c, h
+            c.close()
+
+
+def corr_samples(ctx, hist, phi_inf):
+    xs, ts = [], []
+    for it in CORR_ITERS:
+        if it + 1 >= len(hist) - 1:
+            break
+        x, t = ctx.sn_predictor_corr_data(hist[it - 2], hist[it - 1], hist[it], phi_inf)
+        xs.append(x)
+        ts.append(t[:, None])
+    return xs, ts
+
+
+def generate(problems, precision=SN_PREC_FP64, stream=None, group=128):
+    """Stage-1 data (histories from phi = 0): features, initial-guess targets, correction samples."""
     xi, ti, xc, tc = [], [], [], []
-    for prob in problems:
-        ctx = setup_problem(prob, stream=stream)
-        ctx._N = (prob.p + 1) ** prob.mesh.dim
-        ctx.sn_build_graph("face", 10)
-        phis = solve_history(ctx, precision)
-        phi_inf = phis[-1]
+    for ctx, hist in batched_histories(problems, None, group, precision, stream=stream):
+        phi_inf = hist[-1]
         feat, _ref = ctx.sn_predictor_features()
         xi.append(feat)
         ti.append(ctx.sn_predictor_init_targets(phi_inf))
-        for it in CORR_ITERS:
-            if it + 1 >= len(phis) - 1:
-                break
-            x, t = ctx.sn_predictor_corr_data(phis[it - 2], phis[it - 1], phis[it], phi_inf)
-            xc.append(x)
-            tc.append(t[:, None])
-        ctx.close()
+        x, t = corr_samples(ctx, hist, phi_inf)
+        xc += x
+        tc += t
     return dict(xi=np.concatenate(xi), ti=np.concatenate(ti), xc=np.concatenate(xc), tc=np.concatenate(tc))
+
+
+def generate_stage2(problems, model, precision=SN_PREC_FP64, stream=None, group=128):
+    """Correction samples from histories started at the initial-guess model's prediction (the
+    iterates the correction model meets when the predictor is used)."""
+    init, _corr, cfg = build(model, stream=stream)
+    xc, tc = [], []
+    for ctx, hist in batched_histories(problems, lambda c: c.sn_predictor_initial_phi(init, cfg), group, precision,
+                                       stream=stream):
+        x, t = corr_samples(ctx, hist, hist[-1])
+        xc += x
+        tc += t
+    return dict(xc=np.concatenate(xc), tc=np.concatenate(tc))
 
 
 def _norm(x):
@@ -56,6 +107,19 @@ def _norm(x):
     std = x.std(0).astype(np.float32)
     istd = np.where(std > 1e-12, 1.0 / np.maximum(std, 1e-12), 0.0).astype(np.float32)
     return mean, istd
+
+
+def train_corr(model, data, epochs=40, batch_rows=4096, lr=2e-3, seed=0, stream=None):
+    """Retrain the correction MLP on new samples (e.g. generate_stage2); returns the updated model."""
+    rng = np.random.default_rng(seed)
+    cm, cis = _norm(data["xc"])
+    xc = (data["xc"] - cm) * cis
+    pc = rng.permutation(len(xc))
+    corr = MLP(SN_FEATURES + 2, 1, seed=seed + 2, stream=stream)
+    lc = corr.sn_mlp_train(xc[pc], data["tc"][pc], epochs, batch_rows, lr, seed + 4)
+    out = dict(model)
+    out.update(corr_params=corr.get_params(), corr_mean=cm, corr_istd=cis, corr_loss=lc, rows_corr=len(xc))
+    return out
 
 
 def train(data, epochs=40, batch_rows=4096, lr=2e-3, seed=0, stream=None):

@@ -5,7 +5,8 @@ method itself generates, and save the model.
     python -m paper_1810_11080_gb300.train_predictor --solves 2000 --n 8 --out <path.npz>
 
 Training problems use seeds 1000, 1002, ... (mesh seed s, material seed s + 1); evaluation
-problems elsewhere use seeds >= 5000.
+problems elsewhere use seeds >= 5000.  Stage 1 trains the initial-guess model on histories from
+phi = 0; stage 2 retrains the correction model on histories started at the predicted flux.
 """
 import argparse
 import json
@@ -27,9 +28,13 @@ def main():
     stream = torch.cuda.Stream()
     t0 = time.time()
     probs = [si.make_config("3d_smooth_q2_p2_s12", n=args.n, seed=1000 + 2 * k) for k in range(args.solves)]
+    # stage 1: histories from phi = 0 -> initial-guess model (and a first correction model)
     data = learned.generate(probs, stream=stream.cuda_stream)
-    t1 = time.time()
     model = learned.train(data, epochs=args.epochs, stream=stream.cuda_stream)
+    # stage 2: histories started at the predicted flux -> the correction model it will meet
+    data2 = learned.generate_stage2(probs, model, stream=stream.cuda_stream)
+    t1 = time.time()
+    model = learned.train_corr(model, data2, epochs=args.epochs, stream=stream.cuda_stream)
     t2 = time.time()
     model["train_solves"] = args.solves
     model["train_n"] = args.n
