@@ -159,6 +159,30 @@ def ds_fp32_flops_per_update(dim, p, inflow_faces):
 
 FP32_PEAK_TFLOPS = 75.0
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per level launch of the sweep kernel,
+# averaged over the launches of one sweep of this workload, from the ncu launch list summarised in
+# the named profile.  Valid only for the kernel sources it was taken on (SHA-256 of the files
+# below); any later change to them reports null.
+KERNEL_SOURCES = ["paper_1810_11080_gb300/csrc/sweep.cu", "paper_1810_11080_gb300/csrc/sweep_body.cuh",
+                  "paper_1810_11080_gb300/csrc/common.h"]
+TRAFFIC = {}
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_for(kind):
+    t = TRAFFIC.get(kind)
+    if t is None or t["sources_sha256"] != kernel_sources_sha256():
+        return None, None
+    return t["bytes_per_launch"], t["profile"]
+
 
 def run_gpu(args):
     import torch
@@ -257,8 +281,8 @@ def run_gpu(args):
     inflow_faces = dim            # on average dim of the 2 dim faces of an element are inflow faces
 
     def roofline(kind, m):
-        kname = {"fp64": "sweep64_kernel", "mixed": "sweepmx_kernel", "mixed_ds": "sweepds_kernel"}[kind]
-        kname += f"<{dim},{prob.p}> (all level launches of one sweep)"
+        pcode = {"fp64": 0, "mixed": 1, "mixed_ds": 2}[kind]
+        kname = f"sweep_level_kernel<{dim},{prob.p},{pcode}> (all level launches of one sweep)"
         if kind == "mixed_ds":
             fpu = ds_fp32_flops_per_update(dim, prob.p, inflow_faces)
             peak, unit, src = FP32_PEAK_TFLOPS, "TFLOP/s (FP32 pipe)", "FP32 FFMA microbenchmark (of measured)"
@@ -267,9 +291,11 @@ def run_gpu(args):
                 mixed_fp64_flops_per_update(dim, prob.p, inflow_faces)
             peak, unit, src = FP64_PEAK_TFLOPS, "TFLOP/s (FP64 pipe)", "FP64 DFMA microbenchmark (of measured)"
         ach = fpu * updates / (m["sweep_ms_per_step"] / 1e3) / 1e12
+        traffic, tsrc = traffic_for(kind)
         return {"bound": "alu", "kernel": kname, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                "traffic": None, "peak_source": src, "flops_per_update": fpu,
-                "sweep_ms_per_step": m["sweep_ms_per_step"]}
+                "traffic": traffic, "traffic_unit": "bytes per level launch (sweep average)",
+                "traffic_source": tsrc, "launches_per_step": m["launches"] // max(1, args.steps),
+                "peak_source": src, "flops_per_update": fpu, "sweep_ms_per_step": m["sweep_ms_per_step"]}
 
     out = {
         "metric": METRIC, "value": meas[head]["value"], "unit": "updates/s", "n_gpus": ws, "steps": args.steps,

@@ -16,8 +16,14 @@ __device__ __forceinline__ void batch_task(const DevProblem& Pb, const SweepArgs
   solve_item<DIM, P_, PREC, DF>(Pb, sa, pr < 0 ? 0 : pr, pr >= 0, lane);
 }
 
+// Register budget of the largest body the kernel holds (2D p = 3; 3D p = 2 with one block per SM
+// less, as every order's body shares the budget).
+template <int DIM, int PREC>
+constexpr int batch_minb() {
+  return DIM == 2 ? sweep_minb<2, 3, PREC>() : (sweep_minb<3, 2, PREC>() > 2 ? sweep_minb<3, 2, PREC>() - 1 : 2);
+}
 template <int DIM, int PREC, bool DF>
-__global__ void __launch_bounds__(128) sweep_batch_kernel(const DevProblem* __restrict__ probs,
+__global__ void __launch_bounds__(128, (batch_minb<DIM, PREC>())) sweep_batch_kernel(const DevProblem* __restrict__ probs,
                                                           const SweepArgs* __restrict__ args,
                                                           const int4* __restrict__ tasks, int64_t ntasks,
                                                           unsigned long long* head, int* err) {

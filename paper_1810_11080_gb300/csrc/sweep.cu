@@ -24,7 +24,7 @@ namespace sn {
 
 // One wavefront level: pairs[0, count) are mutually independent.
 template <int DIM, int P_, int PREC>
-__global__ void __launch_bounds__(128) sweep_level_kernel(DevProblem Pb, SweepArgs sa, const int32_t* __restrict__ pairs,
+__global__ void __launch_bounds__(128, (sweep_minb<DIM, P_, PREC>())) sweep_level_kernel(DevProblem Pb, SweepArgs sa, const int32_t* __restrict__ pairs,
                                                           int64_t count) {
   using S = Shape<DIM, P_>;
   const int lane = threadIdx.x & 31;
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(128) sweep_level_kernel(DevProblem Pb, SweepAr
 // the queue head; a pair waits only for its kept upwind neighbours (always handed out earlier,
 // hence held by running warps: no deadlock whatever the grid size).
 template <int DIM, int P_, int PREC>
-__global__ void __launch_bounds__(128) sweep_flow_kernel(DevProblem Pb, SweepArgs sa, const int32_t* __restrict__ pairs,
+__global__ void __launch_bounds__(128, (sweep_minb<DIM, P_, PREC>())) sweep_flow_kernel(DevProblem Pb, SweepArgs sa, const int32_t* __restrict__ pairs,
                                                          int64_t count, unsigned long long* head) {
   using S = Shape<DIM, P_>;
   constexpr unsigned FULL = 0xffffffffu;

@@ -39,7 +39,26 @@ struct Shape {
   static constexpr int NF = ipow(NP1, DIM - 1);
   static constexpr int W = N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32;
   static constexpr int SPW = 32 / W;
+  // Gauss-Jordan steps of the double-single form taken before the wait for upwind data (the
+  // rest follow it, interleaved with the trace loads): balances the two halves of a pair's work.
+  static constexpr int GJ_PRE = 0;
+  // Double-single form: inflow face blocks enter the matrix before the wait (and are formed
+  // again after it for the right-hand side) in 2D; in 3D (6 faces of up to 9 nodes) forming them
+  // twice costs more than it saves, and all face work follows the wait.
+  static constexpr bool FACES_PRE = DIM == 2;
 };
+
+// Resident 128-thread blocks per SM the sweep kernels are compiled for, i.e. a register budget
+// of 65536 / (128 minb) per thread.  Double-single form: 96 registers hold a 2D row without
+// spills; the 3D p = 2 row (N = 27) gets 128 (a few spilled values), which measured faster than
+// 168 without spills because the next level's blocks then fit beside the current level's.  The
+// FP64 and FP64-residual forms get budgets without spills.
+template <int DIM, int P_, int PREC>
+constexpr int sweep_minb() {
+  if (DIM == 3 && P_ == 2) return PREC == SN_PREC_MIXED_DS ? 4 : (PREC == SN_PREC_FP64 ? 3 : 2);
+  if (PREC == SN_PREC_FP64) return DIM == 2 ? 6 : 5;
+  return PREC == SN_PREC_MIXED ? 4 : 5;
+}
 
 // Face-node index of volume node i on local face f, or -1.
 template <int DIM, int P_>
@@ -52,6 +71,35 @@ __device__ __forceinline__ int on_face(int f, int i) {
   const int o0 = axis == 0 ? t1 : t0;
   const int o1 = axis == 2 ? t1 : t2;
   return DIM == 2 ? o0 : o0 + n * o1;
+}
+
+// Volume index, in the neighbour's node numbering, of face node fj = I + (p+1) J of our face,
+// written as c0 + ci I + cj J for the neighbour's face fn and orientation code oc (bit 2 swaps
+// the face axes, bit 0 flips the first, bit 1 the second): the same map as orient_map_idx
+// followed by face_vol_index, with the per-face constants computed once.
+template <int DIM, int P_>
+__device__ __forceinline__ void trace_affine(int fn, int oc, int& c0, int& ci, int& cj) {
+  constexpr int n = P_ + 1;
+  const int axis = fn >> 1, side = fn & 1;
+  if constexpr (DIM == 2) {
+    const int A = axis == 0 ? side * P_ : n * side * P_;
+    const int B = axis == 0 ? n : 1;
+    const bool flip = oc & 1;
+    c0 = flip ? A + B * P_ : A;
+    ci = flip ? -B : B;
+    cj = 0;
+  } else {
+    // neighbour face coordinates (t0, t1) -> volume index A + B0 t0 + B1 t1
+    const int A = axis == 0 ? side * P_ : (axis == 1 ? n * side * P_ : n * n * side * P_);
+    const int B0 = axis == 0 ? n : 1;
+    const int B1 = axis == 2 ? n : n * n;
+    const bool f0 = oc & 1, f1 = oc & 2, sw = oc & 4;
+    // t0 = f0 ? p - u0 : u0, t1 = f1 ? p - u1 : u1, (u0, u1) = sw ? (J, I) : (I, J)
+    const int b0 = f0 ? -B0 : B0, b1 = f1 ? -B1 : B1;
+    c0 = A + (f0 ? B0 * P_ : 0) + (f1 ? B1 * P_ : 0);
+    ci = sw ? b1 : b0;
+    cj = sw ? b0 : b1;
+  }
 }
 
 // ---- double-single (FP32 pair) arithmetic: error-free transformations (Knuth two-sum,
@@ -285,38 +333,71 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // Row-per-lane Gauss-Jordan on the segment: on return the lane that was chosen as pivot of
 // step k (plk[k], myk == k) holds in v[] row k of A^{-1}, with columns indexed by the original
 // row (= lane) index: x_k = sum_j v[j] b_j.  All rows are updated at every step, so there are
-// N dependent steps and no triangular solves.
-template <int N, int W>
-__device__ __forceinline__ void gj32(float (&a)[N], float (&v)[N], int i, int lane, bool row, int (&plk)[N],
-                                     int& myk) {
-  constexpr unsigned FULL = 0xffffffffu;
-  bool used = !row;
-  myk = -1;
+// N dependent steps and no triangular solves.  Pivot rows are not scaled during the
+// elimination (row i -= (a_ik / a_pk) row p for i != p, one multiply-add per entry); after the
+// last step row p of [A | V] is a_pk e_k^T | a_pk (A^{-1})_k, and V is scaled by 1/a_pk once.
+struct GJState {
+  bool used;      // this lane's row has been a pivot row (or is not a row)
+  int myk;        // step at which it was the pivot row, or -1
+  float myinv;    // 1 / pivot of that step
+};
+
+template <int N>
+__device__ __forceinline__ void gj32_init(float (&v)[N], int i, bool row, GJState& st) {
+  st.used = !row;
+  st.myk = -1;
+  st.myinv = 0.0f;
   static_for<0, N>([&](auto jconst) { v[decltype(jconst)::value] = (row && decltype(jconst)::value == i) ? 1.0f : 0.0f; });
-  static_for<0, N>([&](auto kconst) {
+}
+
+// Steps [K0, K1) of the elimination.
+template <int N, int W, int K0, int K1>
+__device__ __forceinline__ void gj32_steps(float (&a)[N], float (&v)[N], int lane, int (&plk)[N], GJState& st) {
+  constexpr unsigned FULL = 0xffffffffu;
+  static_for<K0, K1>([&](auto kconst) {
     constexpr int k = decltype(kconst)::value;
-    const unsigned key = used ? 0u : ((__float_as_uint(a[k]) & 0x7fffffe0u) | (unsigned)(31 - lane));
+    const unsigned key = st.used ? 0u : ((__float_as_uint(a[k]) & 0x7fffffe0u) | (unsigned)(31 - lane));
     const int pl = seg_argmax_key<W>(key, lane);
     plk[k] = pl;
     const float piv = __shfl_sync(FULL, a[k], pl, W);
     const float inv = rcp_approx(piv);
     const bool me = (lane == pl);
     if (me) {
-      used = true;
-      myk = k;
+      st.used = true;
+      st.myk = k;
+      st.myinv = inv;
     }
     const float l = me ? 0.0f : a[k] * inv;
     static_for<k + 1, N>([&](auto jconst) {
       constexpr int j = decltype(jconst)::value;
-      const float u = __shfl_sync(FULL, a[j], pl, W);
-      a[j] = me ? a[j] * inv : fmaf(-l, u, a[j]);
+      a[j] = fmaf(-l, __shfl_sync(FULL, a[j], pl, W), a[j]);
     });
     static_for<0, N>([&](auto jconst) {
       constexpr int j = decltype(jconst)::value;
-      const float u = __shfl_sync(FULL, v[j], pl, W);
-      v[j] = me ? v[j] * inv : fmaf(-l, u, v[j]);
+      v[j] = fmaf(-l, __shfl_sync(FULL, v[j], pl, W), v[j]);
     });
   });
+}
+
+template <int N>
+__device__ __forceinline__ void gj32_finish(float (&v)[N], const GJState& st) {
+  static_for<0, N>([&](auto jconst) { v[decltype(jconst)::value] *= st.myinv; });
+}
+
+// Row-per-lane Gauss-Jordan on the segment: on return the lane that was chosen as pivot of
+// step k (plk[k], myk == k) holds in v[] row k of A^{-1}, with columns indexed by the original
+// row (= lane) index: x_k = sum_j v[j] b_j.  All rows are updated at every step, so there are
+// N dependent steps and no triangular solves.  Pivot rows are not scaled during the
+// elimination (row i -= (a_ik / a_pk) row p for i != p, one multiply-add per entry); after the
+// last step row p of [A | V] is a_pk e_k^T | a_pk (A^{-1})_k, and V is scaled by 1/a_pk once.
+template <int N, int W>
+__device__ __forceinline__ void gj32(float (&a)[N], float (&v)[N], int i, int lane, bool row, int (&plk)[N],
+                                     int& myk) {
+  GJState st;
+  gj32_init<N>(v, i, row, st);
+  gj32_steps<N, W, 0, N>(a, v, lane, plk, st);
+  gj32_finish<N>(v, st);
+  myk = st.myk;
 }
 
 // y_k = sum_j v[j] r_j on the pivot lane of step k; r_j lives on lane j of the segment.
@@ -538,8 +619,48 @@ __device__ __forceinline__ void bodymx(const DevProblem& Pb, const SweepArgs& sa
 
 // ------------------------------------------------------------------ mixed form, double-single residual
 // The row of A is assembled once in double-single from the (hi, lo) FP32 split of the element
-// factors; its hi part is the FP32 matrix that is factored; r = b - A xhat is accumulated in
-// double-single; b stays FP64.
+// factors; its hi part is the FP32 matrix that is inverted; r = b - A xhat is accumulated in
+// double-single.  A (volume terms and inflow face blocks) and its inverse depend only on the
+// element, the direction and the face modes, not on upwind fluxes.  The work of a pair is
+// therefore split around the wait for upwind data: assembly, face blocks and the first GJ_PRE
+// elimination steps before it (overlapping the previous level), the remaining steps, the
+// right-hand side and the two applications of the inverse after it.
+
+// Inflow block row fi of face f in double-single: -(Omega . FN_f) for a whole-inflow face, the
+// stored block for a partially-inflow one (slot o_mixed).  NC: read-only cache loads.
+template <int DIM, int P_, bool NC>
+__device__ __forceinline__ void ds_block_row(const float* bh, const float* bl, const SweepArgs& sa, uint32_t mode,
+                                             int f, int fi, int64_t o_mixed, const float (&oh)[3],
+                                             const float (&ol)[3], float (&Bh)[Shape<DIM, P_>::NF],
+                                             float (&Bl)[Shape<DIM, P_>::NF]) {
+  using S = Shape<DIM, P_>;
+  constexpr int N = S::N, NF = S::NF;
+  auto ld = [](const float* p) { return NC ? __ldg(p) : *p; };
+  if (mode == MODE_PURE) {
+    const int o = (DIM + 1) * N * N + f * DIM * NF * NF + fi * NF;
+#pragma unroll
+    for (int fj = 0; fj < NF; ++fj) {
+      float h, l, ph, pl;
+      ds_mul(oh[0], ol[0], ld(bh + o + fj), ld(bl + o + fj), h, l);
+      ds_mul(oh[1], ol[1], ld(bh + o + NF * NF + fj), ld(bl + o + NF * NF + fj), ph, pl);
+      ds_add(h, l, ph, pl);
+      if (DIM == 3) {
+        ds_mul(oh[2], ol[2], ld(bh + o + 2 * NF * NF + fj), ld(bl + o + 2 * NF * NF + fj), ph, pl);
+        ds_add(h, l, ph, pl);
+      }
+      Bh[fj] = -h;
+      Bl[fj] = -l;
+    }
+  } else {
+    const int64_t o = o_mixed * NF * NF + fi * NF;
+#pragma unroll
+    for (int fj = 0; fj < NF; ++fj) {
+      Bh[fj] = ld(sa.mixedBh + o + fj);
+      Bl[fj] = ld(sa.mixedBl + o + fj);
+    }
+  }
+}
+
 template <int DIM, int P_, bool DF>
 __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid, int lane) {
   using S = Shape<DIM, P_>;
@@ -595,6 +716,41 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
   }
   const uint32_t code = valid ? sa.facecode[(int64_t)d * E + e] : 0u;
   const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[(int64_t)d * E + e] : 0;
+  // inflow face blocks into the matrix
+  if constexpr (S::FACES_PRE) {
+    int mrank = 0;
+    static_for<0, 2 * DIM>([&](auto fconst) {
+      constexpr int f = decltype(fconst)::value;
+      const uint32_t mode = face_mode(code, f);
+      const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+      if (mode != MODE_NONE && fi >= 0) {
+        float Bh[NF], Bl[NF];
+        ds_block_row<DIM, P_, true>(bh, bl, sa, mode, f, fi, mbase + mrank, oh, ol, Bh, Bl);
+        static_for<0, NF>([&](auto jconst) {
+          constexpr int fj = decltype(jconst)::value;
+          constexpr int c = fvi<DIM, P_>(f, fj);
+          ds_add(ah[c], al[c], Bh[fj], Bl[fj]);
+        });
+      }
+      if (mode == MODE_MIXED) ++mrank;
+    });
+  }
+  // mesh connectivity of the faces (static data)
+  int64_t nbv[2 * DIM];
+  int fov[2 * DIM];
+  static_for<0, 2 * DIM>([&](auto fconst) {
+    constexpr int f = decltype(fconst)::value;
+    nbv[f] = valid ? Pb.nbr[e * 2 * DIM + f] : -1;
+    fov[f] = valid ? (Pb.nbr_face[e * 2 * DIM + f] | (Pb.orient[e * 2 * DIM + f] << 8)) : 0;
+  });
+  int plk[N];
+  float v[N];
+  GJState gst;
+  gj32_init<N>(v, i, row, gst);
+  if constexpr (S::FACES_PRE) {
+    static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = ah[decltype(jconst)::value]; });
+    gj32_steps<N, W, 0, S::GJ_PRE>(a, v, lane, plk, gst);
+  }
   if constexpr (DF) {
     wait_upwind<DIM>(Pb, sa, code, e, d, valid);
   } else {
@@ -602,94 +758,87 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
     pdl_launch_dependents();             // ... and only then may the next level start: one level ahead
   }
   if (row) ds_add(rbh, rbl, sa.src_h[e * N + i], sa.src_l[e * N + i]);
-  int mrank = 0;
-  static_for<0, 2 * DIM>([&](auto fconst) {
-    constexpr int f = decltype(fconst)::value;
-    const uint32_t mode = face_mode(code, f);
-    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
-    if (mode != MODE_NONE && fi >= 0) {
-      float Bh[NF], Bl[NF];
-      if (mode == MODE_PURE) {
-        const int o = (DIM + 1) * N * N + f * DIM * NF * NF + fi * NF;
-#pragma unroll
-        for (int fj = 0; fj < NF; ++fj) {
-          float h, l, ph, pl;
-          ds_mul(oh[0], ol[0], __ldg(bh + o + fj), __ldg(bl + o + fj), h, l);
-          ds_mul(oh[1], ol[1], __ldg(bh + o + NF * NF + fj), __ldg(bl + o + NF * NF + fj), ph, pl);
-          ds_add(h, l, ph, pl);
-          if (DIM == 3) {
-            ds_mul(oh[2], ol[2], __ldg(bh + o + 2 * NF * NF + fj), __ldg(bl + o + 2 * NF * NF + fj), ph, pl);
-            ds_add(h, l, ph, pl);
-          }
-          Bh[fj] = -h;
-          Bl[fj] = -l;
+  {
+    int mrank = 0;
+    static_for<0, 2 * DIM>([&](auto fconst) {
+      constexpr int f = decltype(fconst)::value;
+      const uint32_t mode = face_mode(code, f);
+      const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+      const int64_t nb = nbv[f];
+      const bool has_trace = nb >= 0 || Pb.psi_inc != nullptr;
+      if (mode != MODE_NONE && fi >= 0 && (!S::FACES_PRE || has_trace)) {
+        float Bh[NF], Bl[NF];
+        if constexpr (!S::FACES_PRE) {
+          ds_block_row<DIM, P_, true>(bh, bl, sa, mode, f, fi, mbase + mrank, oh, ol, Bh, Bl);
+          static_for<0, NF>([&](auto jconst) {
+            constexpr int fj = decltype(jconst)::value;
+            constexpr int c = fvi<DIM, P_>(f, fj);
+            ds_add(ah[c], al[c], Bh[fj], Bl[fj]);
+          });
         }
-      } else {
-        const int64_t o = (int64_t)(mbase + mrank) * NF * NF + fi * NF;
+        if (has_trace) {
+          float th[NF], tl[NF];
+          if (nb >= 0) {                 // upwind neighbour's (hi, lo) split of the trace
+            const bool lag = face_lagged(code, f);
+            int c0, ci, cj;
+            trace_affine<DIM, P_>(fov[f] & 0xff, fov[f] >> 8, c0, ci, cj);
+            const int64_t base = ((int64_t)d * E + nb) * N + c0;
+            const float* ph_ = (lag ? sa.psi_old_h : sa.psi_new_h) + base;
+            const float* pl_ = (lag ? sa.psi_old_l : sa.psi_new_l) + base;
 #pragma unroll
-        for (int fj = 0; fj < NF; ++fj) {
-          Bh[fj] = __ldg(sa.mixedBh + o + fj);
-          Bl[fj] = __ldg(sa.mixedBl + o + fj);
+            for (int fj = 0; fj < NF; ++fj) {
+              const int o = ci * (fj % NP1) + cj * (fj / NP1);
+              if (!lag && DF) {
+                th[fj] = __ldcg(ph_ + o);
+                tl[fj] = __ldcg(pl_ + o);
+              } else {
+                th[fj] = __ldg(ph_ + o);
+                tl[fj] = __ldg(pl_ + o);
+              }
+            }
+          } else {                       // incident flux on the domain boundary
+            const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * 2 * DIM + f]) * NF;
+#pragma unroll
+            for (int fj = 0; fj < NF; ++fj) ds_split(__ldg(pin + fj), th[fj], tl[fj]);
+          }
+          if constexpr (S::FACES_PRE) ds_block_row<DIM, P_, false>(bh, bl, sa, mode, f, fi, mbase + mrank, oh, ol, Bh, Bl);
+          float sh2 = 0.0f, sl2 = 0.0f;  // second accumulator: two independent chains
+#pragma unroll
+          for (int fj = 0; fj < NF; ++fj) {
+            float qh, ql;
+            ds_mul(Bh[fj], Bl[fj], th[fj], tl[fj], qh, ql);
+            if (fj & 1) ds_add(sh2, sl2, qh, ql);
+            else ds_add(rbh, rbl, qh, ql);
+          }
+          ds_add(rbh, rbl, sh2, sl2);
         }
       }
-      static_for<0, NF>([&](auto jconst) {
-        constexpr int fj = decltype(jconst)::value;
-        constexpr int c = fvi<DIM, P_>(f, fj);
-        ds_add(ah[c], al[c], Bh[fj], Bl[fj]);
-      });
-      // b += B trace: upwind neighbour's (hi, lo) split or the incident flux
-      const int64_t nb = Pb.nbr[e * 2 * DIM + f];
-      if (nb >= 0) {
-        const bool lag = face_lagged(code, f);
-        const float* ph_ = lag ? sa.psi_old_h : sa.psi_new_h;
-        const float* pl_ = lag ? sa.psi_old_l : sa.psi_new_l;
-        const int fn = Pb.nbr_face[e * 2 * DIM + f], oc = Pb.orient[e * 2 * DIM + f];
-        const int64_t base = ((int64_t)d * E + nb) * N;
-#pragma unroll
-        for (int fj = 0; fj < NF; ++fj) {
-          int t0, t1;
-          orient_map_idx(DIM, oc, P_, fj % NP1, fj / NP1, t0, t1);
-          const int64_t idx = base + face_vol_index(DIM, P_, fn, t0, t1);
-          float th, tl;
-          if (!lag && DF) {
-            th = __ldcg(ph_ + idx);
-            tl = __ldcg(pl_ + idx);
-          } else {
-            th = __ldg(ph_ + idx);
-            tl = __ldg(pl_ + idx);
-          }
-          float qh, ql;
-          ds_mul(Bh[fj], Bl[fj], th, tl, qh, ql);
-          ds_add(rbh, rbl, qh, ql);
-        }
-      } else if (Pb.psi_inc != nullptr) {
-        const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * 2 * DIM + f]) * NF;
-#pragma unroll
-        for (int fj = 0; fj < NF; ++fj) {
-          float th, tl, qh, ql;
-          ds_split(__ldg(pin + fj), th, tl);
-          ds_mul(Bh[fj], Bl[fj], th, tl, qh, ql);
-          ds_add(rbh, rbl, qh, ql);
-        }
-      }
-    }
-    if (mode == MODE_MIXED) ++mrank;
-  });
-  static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = ah[decltype(jconst)::value]; });
-  int plk[N], myk;
-  float v[N];
-  gj32<N, W>(a, v, i, lane, row, plk, myk);
+      if (mode == MODE_MIXED) ++mrank;
+    });
+  }
+  if constexpr (!S::FACES_PRE) {
+    static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = ah[decltype(jconst)::value]; });
+    gj32_steps<N, W, 0, N>(a, v, lane, plk, gst);
+  } else {
+    gj32_steps<N, W, S::GJ_PRE, N>(a, v, lane, plk, gst);
+  }
+  gj32_finish<N>(v, gst);
+  const int myk = gst.myk;
   const float xhat = gj_apply<N, W>(v, rbh);        // on the pivot lane of step myk
-  float rh = rbh, rl = rbl;
+  // r = b - A xhat in double-single, four independent accumulation chains
+  float rh[4] = {rbh, 0.0f, 0.0f, 0.0f}, rl[4] = {rbl, 0.0f, 0.0f, 0.0f};
   static_for<0, N>([&](auto jconst) {
     constexpr int j = decltype(jconst)::value;
     const float xj = __shfl_sync(FULL, xhat, plk[j], W);
     float ph = ah[j] * xj;
     float pl = fmaf(ah[j], xj, -ph);
     pl = fmaf(al[j], xj, pl);
-    ds_add(rh, rl, -ph, -pl);
+    ds_add(rh[j & 3], rl[j & 3], -ph, -pl);
   });
-  const float dx = gj_apply<N, W>(v, rh + rl);
+  ds_add(rh[0], rl[0], rh[1], rl[1]);
+  ds_add(rh[2], rl[2], rh[3], rl[3]);
+  ds_add(rh[0], rl[0], rh[2], rl[2]);
+  const float dx = gj_apply<N, W>(v, rh[0] + rl[0]);
   if (row && myk >= 0) {
     float oh2, ol2;
     ds_two_sum(xhat, dx, oh2, ol2);

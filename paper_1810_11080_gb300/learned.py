@@ -14,26 +14,37 @@ from .problem import setup_problem
 CORR_ITERS = (3, 4, 6, 8, 11, 15, 20, 27, 36, 48, 64)
 
 
+# Iterates a correction sample needs: phi_{it-2}, phi_{it-1}, phi_it for it in CORR_ITERS.
+KEEP = frozenset(k for it in CORR_ITERS for k in (it - 2, it - 1, it))
+
+
 def solve_history(ctx, precision=SN_PREC_FP64, tol=1e-11, max_iter=3000):
-    """Plain source iteration from phi = 0, returning every iterate [phi_0 = 0, phi_1, ...]."""
+    """Plain source iteration from phi = 0: ({iteration: phi} for the iterates in KEEP and the
+    last one, number of iterations)."""
     E, N = ctx._n_elem, ctx._N
     ctx.sn_si_begin()
-    phis = [np.zeros((E, N))]
-    for _ in range(max_iter):
+    hist = {0: np.zeros((E, N))}
+    n = 0
+    for n in range(1, max_iter + 1):
         res, _ = ctx.sn_si_step(precision)
-        phi = np.zeros((E, N))
-        ctx.sn_si_result(phi, None)
-        phis.append(phi)
+        if n in KEEP or res < tol:
+            phi = np.zeros((E, N))
+            ctx.sn_si_result(phi, None)
+            hist[n] = phi
         if res < tol:
             break
-    return phis
+    if n not in hist:
+        hist[n] = np.zeros((E, N))
+        ctx.sn_si_result(hist[n], None)
+    return hist, n
 
 
 def batched_histories(problems, start=None, group=128, precision=SN_PREC_FP64, tol=1e-11, max_iter=3000,
                       stream=None):
-    """Source-iteration histories [phi_0, phi_1, ...] of many problems, solved group by group in
-    batched launches.  start(ctx) -> phi_0 (or None for 0).  Yields (ctx, history); the context is
-    closed after the caller's loop body."""
+    """Source-iteration histories of many problems, solved group by group in batched launches.
+    start(ctx) -> phi_0 (or None for 0).  Yields (ctx, {iteration: phi}, last iteration) with the
+    iterates in KEEP and the last one (the converged flux); the context is closed after the
+    caller's loop body."""
     from ._lib import Batch
     for g0 in range(0, len(problems), group):
         grp = problems[g0:g0 + group]
@@ -45,29 +56,34 @@ def batched_histories(problems, start=None, group=128, precision=SN_PREC_FP64, t
         phi0 = [None if start is None else start(c) for c in ctxs]
         b = Batch(ctxs, stream)
         b.sn_batch_si_begin(phi0)
-        hist = [[np.zeros((c._n_elem, c._N)) if p is None else p] for c, p in zip(ctxs, phi0)]
+        hist = [{0: np.zeros((c._n_elem, c._N)) if p is None else p} for c, p in zip(ctxs, phi0)]
+        last = [0] * len(ctxs)
         done = [False] * len(ctxs)
-        for _ in range(max_iter):
+        for n in range(1, max_iter + 1):
             res, _ = b.sn_batch_si_step(precision)
             for k, c in enumerate(ctxs):
                 if done[k]:
                     continue
-                phi = np.zeros((c._n_elem, c._N))
-                c.sn_si_result(phi, None)
-                hist[k].append(phi)
+                last[k] = n
                 done[k] = res[k] < tol
+                if n in KEEP or done[k] or n == max_iter:
+                    phi = np.zeros((c._n_elem, c._N))
+                    c.sn_si_result(phi, None)
+                    hist[k][n] = phi
             if all(done):
                 break
         b.close()
-        for c, h in zip(ctxs, hist):
-            yield c, h
+        for c, h, n in zip(ctxs, hist, last):
+            yield c, h, n
             c.close()
 
 
-def corr_samples(ctx, hist, phi_inf):
+def corr_samples(ctx, hist, n):
+    """Correction samples at the iterations in CORR_ITERS that precede the last iterate n - 1."""
+    phi_inf = hist[n]
     xs, ts = [], []
     for it in CORR_ITERS:
-        if it + 1 >= len(hist) - 1:
+        if it + 1 >= n:
             break
         x, t = ctx.sn_predictor_corr_data(hist[it - 2], hist[it - 1], hist[it], phi_inf)
         xs.append(x)
@@ -78,12 +94,11 @@ def corr_samples(ctx, hist, phi_inf):
 def generate(problems, precision=SN_PREC_FP64, stream=None, group=128):
     """Stage-1 data (histories from phi = 0): features, initial-guess targets, correction samples."""
     xi, ti, xc, tc = [], [], [], []
-    for ctx, hist in batched_histories(problems, None, group, precision, stream=stream):
-        phi_inf = hist[-1]
+    for ctx, hist, n in batched_histories(problems, None, group, precision, stream=stream):
         feat, _ref = ctx.sn_predictor_features()
         xi.append(feat)
-        ti.append(ctx.sn_predictor_init_targets(phi_inf))
-        x, t = corr_samples(ctx, hist, phi_inf)
+        ti.append(ctx.sn_predictor_init_targets(hist[n]))
+        x, t = corr_samples(ctx, hist, n)
         xc += x
         tc += t
     return dict(xi=np.concatenate(xi), ti=np.concatenate(ti), xc=np.concatenate(xc), tc=np.concatenate(tc))
@@ -94,9 +109,9 @@ def generate_stage2(problems, model, precision=SN_PREC_FP64, stream=None, group=
     iterates the correction model meets when the predictor is used)."""
     init, _corr, cfg = build(model, stream=stream)
     xc, tc = [], []
-    for ctx, hist in batched_histories(problems, lambda c: c.sn_predictor_initial_phi(init, cfg), group, precision,
-                                       stream=stream):
-        x, t = corr_samples(ctx, hist, hist[-1])
+    for ctx, hist, n in batched_histories(problems, lambda c: c.sn_predictor_initial_phi(init, cfg), group,
+                                          precision, stream=stream):
+        x, t = corr_samples(ctx, hist, n)
         xc += x
         tc += t
     return dict(xc=np.concatenate(xc), tc=np.concatenate(tc))

@@ -26,6 +26,7 @@ CASES = {
     "2d_reoriented_6_p2": lambda: si.make_config("2d_sine_q2_p1_s4", n=6, p=2, reorient_seed=3),
     "3d_twist_4_p2_s8": lambda: si.make_config("3d_twist_q2_p2_s8", n=4),
     "3d_twist_3_p1_s4_reoriented": lambda: si.make_config("3d_twist_q2_p2_s8", n=3, p=1, sn=4, reorient_seed=9),
+    "3d_twist_3_p2_s4_reoriented": lambda: si.make_config("3d_twist_q2_p2_s8", n=3, p=2, sn=4, reorient_seed=5),
     "3d_smooth_3_p2_s4": lambda: si.make_config("3d_smooth_q2_p2_s12", n=3, sn=4),
 }
 
@@ -121,7 +122,7 @@ MIXED_TOL = 1e-8     # single mixed sweep vs the FP64 oracle (FP32 LU + one FP64
 
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("case", ["2d_sine_16", "2d_smooth_10_p3_s8", "3d_twist_4_p2_s8", "2d_reoriented_6_p2",
-                                  "3d_twist_3_p1_s4_reoriented"])
+                                  "3d_twist_3_p1_s4_reoriented", "3d_twist_3_p2_s4_reoriented"])
 def test_mixed_sweep_accuracy(case, prec):
     prob = CASES[case]()
     disc, G = oracle_graph(prob, "face")
