@@ -34,11 +34,12 @@ __global__ void __launch_bounds__(128, (sweep_minb<DIM, P_, PREC>())) sweep_leve
   solve_item<DIM, P_, PREC, false>(Pb, sa, pr < 0 ? 0 : pr, pr >= 0, lane);
 }
 
-// Whole sweep in one launch: warps take S::SPW consecutive pairs of the level-ordered list from
+// Whole sweep in one launch (one resident block per SM less than the level kernel: the queue
+// loop holds a few more values): warps take S::SPW consecutive pairs of the level-ordered list from
 // the queue head; a pair waits only for its kept upwind neighbours (always handed out earlier,
 // hence held by running warps: no deadlock whatever the grid size).
 template <int DIM, int P_, int PREC>
-__global__ void __launch_bounds__(128, (sweep_minb<DIM, P_, PREC>())) sweep_flow_kernel(DevProblem Pb, SweepArgs sa, const int32_t* __restrict__ pairs,
+__global__ void __launch_bounds__(128, (sweep_minb<DIM, P_, PREC>() > 2 ? sweep_minb<DIM, P_, PREC>() - 1 : 2)) sweep_flow_kernel(DevProblem Pb, SweepArgs sa, const int32_t* __restrict__ pairs,
                                                          int64_t count, unsigned long long* head) {
   using S = Shape<DIM, P_>;
   constexpr unsigned FULL = 0xffffffffu;

@@ -39,9 +39,6 @@ struct Shape {
   static constexpr int NF = ipow(NP1, DIM - 1);
   static constexpr int W = N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32;
   static constexpr int SPW = 32 / W;
-  // Gauss-Jordan steps of the double-single form taken before the wait for upwind data (the
-  // rest follow it, interleaved with the trace loads): balances the two halves of a pair's work.
-  static constexpr int GJ_PRE = 0;
   // Double-single form: inflow face blocks enter the matrix before the wait (and are formed
   // again after it for the right-hand side) in 2D; in 3D (6 faces of up to 9 nodes) forming them
   // twice costs more than it saves, and all face work follows the wait.
@@ -620,11 +617,10 @@ __device__ __forceinline__ void bodymx(const DevProblem& Pb, const SweepArgs& sa
 // ------------------------------------------------------------------ mixed form, double-single residual
 // The row of A is assembled once in double-single from the (hi, lo) FP32 split of the element
 // factors; its hi part is the FP32 matrix that is inverted; r = b - A xhat is accumulated in
-// double-single.  A (volume terms and inflow face blocks) and its inverse depend only on the
-// element, the direction and the face modes, not on upwind fluxes.  The work of a pair is
-// therefore split around the wait for upwind data: assembly, face blocks and the first GJ_PRE
-// elimination steps before it (overlapping the previous level), the remaining steps, the
-// right-hand side and the two applications of the inverse after it.
+// double-single.  The volume part of A (and in 2D its inflow face blocks) depends only on the
+// element, the direction and the face modes, not on upwind fluxes: it is assembled before the
+// wait for upwind data, overlapping the previous level; the right-hand side, the inverse and
+// its two applications follow the wait.
 
 // Inflow block row fi of face f in double-single: -(Omega . FN_f) for a whole-inflow face, the
 // stored block for a partially-inflow one (slot o_mixed).  NC: read-only cache loads.
@@ -743,14 +739,6 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
     nbv[f] = valid ? Pb.nbr[e * 2 * DIM + f] : -1;
     fov[f] = valid ? (Pb.nbr_face[e * 2 * DIM + f] | (Pb.orient[e * 2 * DIM + f] << 8)) : 0;
   });
-  int plk[N];
-  float v[N];
-  GJState gst;
-  gj32_init<N>(v, i, row, gst);
-  if constexpr (S::FACES_PRE) {
-    static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = ah[decltype(jconst)::value]; });
-    gj32_steps<N, W, 0, S::GJ_PRE>(a, v, lane, plk, gst);
-  }
   if constexpr (DF) {
     wait_upwind<DIM>(Pb, sa, code, e, d, valid);
   } else {
@@ -776,30 +764,24 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
             ds_add(ah[c], al[c], Bh[fj], Bl[fj]);
           });
         }
-        if (has_trace) {
+        if (nb >= 0) {                   // upwind neighbour's (hi, lo) split of the trace
+          const bool lag = face_lagged(code, f);
+          int c0, ci, cj;
+          trace_affine<DIM, P_>(fov[f] & 0xff, fov[f] >> 8, c0, ci, cj);
+          const int64_t base = ((int64_t)d * E + nb) * N + c0;
+          const float* ph_ = (lag ? sa.psi_old_h : sa.psi_new_h) + base;
+          const float* pl_ = (lag ? sa.psi_old_l : sa.psi_new_l) + base;
           float th[NF], tl[NF];
-          if (nb >= 0) {                 // upwind neighbour's (hi, lo) split of the trace
-            const bool lag = face_lagged(code, f);
-            int c0, ci, cj;
-            trace_affine<DIM, P_>(fov[f] & 0xff, fov[f] >> 8, c0, ci, cj);
-            const int64_t base = ((int64_t)d * E + nb) * N + c0;
-            const float* ph_ = (lag ? sa.psi_old_h : sa.psi_new_h) + base;
-            const float* pl_ = (lag ? sa.psi_old_l : sa.psi_new_l) + base;
 #pragma unroll
-            for (int fj = 0; fj < NF; ++fj) {
-              const int o = ci * (fj % NP1) + cj * (fj / NP1);
-              if (!lag && DF) {
-                th[fj] = __ldcg(ph_ + o);
-                tl[fj] = __ldcg(pl_ + o);
-              } else {
-                th[fj] = __ldg(ph_ + o);
-                tl[fj] = __ldg(pl_ + o);
-              }
+          for (int fj = 0; fj < NF; ++fj) {
+            const int o = ci * (fj % NP1) + cj * (fj / NP1);
+            if (!lag && DF) {
+              th[fj] = __ldcg(ph_ + o);
+              tl[fj] = __ldcg(pl_ + o);
+            } else {
+              th[fj] = __ldg(ph_ + o);
+              tl[fj] = __ldg(pl_ + o);
             }
-          } else {                       // incident flux on the domain boundary
-            const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * 2 * DIM + f]) * NF;
-#pragma unroll
-            for (int fj = 0; fj < NF; ++fj) ds_split(__ldg(pin + fj), th[fj], tl[fj]);
           }
           if constexpr (S::FACES_PRE) ds_block_row<DIM, P_, false>(bh, bl, sa, mode, f, fi, mbase + mrank, oh, ol, Bh, Bl);
           float sh2 = 0.0f, sl2 = 0.0f;  // second accumulator: two independent chains
@@ -811,19 +793,25 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
             else ds_add(rbh, rbl, qh, ql);
           }
           ds_add(rbh, rbl, sh2, sl2);
+        } else if (Pb.psi_inc != nullptr) {  // incident flux on the domain boundary
+          if constexpr (S::FACES_PRE) ds_block_row<DIM, P_, false>(bh, bl, sa, mode, f, fi, mbase + mrank, oh, ol, Bh, Bl);
+          const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * 2 * DIM + f]) * NF;
+#pragma unroll
+          for (int fj = 0; fj < NF; ++fj) {
+            float th, tl, qh, ql;
+            ds_split(__ldg(pin + fj), th, tl);
+            ds_mul(Bh[fj], Bl[fj], th, tl, qh, ql);
+            ds_add(rbh, rbl, qh, ql);
+          }
         }
       }
       if (mode == MODE_MIXED) ++mrank;
     });
   }
-  if constexpr (!S::FACES_PRE) {
-    static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = ah[decltype(jconst)::value]; });
-    gj32_steps<N, W, 0, N>(a, v, lane, plk, gst);
-  } else {
-    gj32_steps<N, W, S::GJ_PRE, N>(a, v, lane, plk, gst);
-  }
-  gj32_finish<N>(v, gst);
-  const int myk = gst.myk;
+  static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = ah[decltype(jconst)::value]; });
+  int plk[N], myk;
+  float v[N];
+  gj32<N, W>(a, v, i, lane, row, plk, myk);
   const float xhat = gj_apply<N, W>(v, rbh);        // on the pivot lane of step myk
   // r = b - A xhat in double-single, four independent accumulation chains
   float rh[4] = {rbh, 0.0f, 0.0f, 0.0f}, rl[4] = {rbl, 0.0f, 0.0f, 0.0f};
