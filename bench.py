@@ -165,7 +165,10 @@ FP32_PEAK_TFLOPS = 75.0
 # below); any later change to them reports null.
 KERNEL_SOURCES = ["paper_1810_11080_gb300/csrc/sweep.cu", "paper_1810_11080_gb300/csrc/sweep_body.cuh",
                   "paper_1810_11080_gb300/csrc/common.h"]
-TRAFFIC = {}
+TRAFFIC = {
+    "mixed_ds": {"bytes_per_launch": 2982834, "profile": "profiles/sweep_level_kernel_ds_2d_p3_s8_128x128.md",
+                 "sources_sha256": "716dcfe540a61a9a265c03324ff16c9078b8db5fceca48d8ac55a46608feed5d"},
+}
 
 
 def kernel_sources_sha256():
