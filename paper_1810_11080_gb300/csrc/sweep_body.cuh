@@ -231,77 +231,6 @@ __device__ __forceinline__ void brow64(const double* blk, const SweepArgs& sa, u
   }
 }
 
-// ---- FP32 pivoted LU of the segment's rows with multipliers kept in a[k]; returns plk, myk, myinv.
-template <int N, int W>
-__device__ __forceinline__ void lu32(float (&a)[N], float& bx, int i, bool row, int (&plk)[N], int& myk,
-                                     float& myinv) {
-  constexpr unsigned FULL = 0xffffffffu;
-  bool used = !row;
-  myk = -1;
-  myinv = 0.0f;
-  static_for<0, N>([&](auto kconst) {
-    constexpr int k = decltype(kconst)::value;
-    float v = used ? -1.0f : fabsf(a[k]);
-    int idx = i;
-#pragma unroll
-    for (int off = W / 2; off > 0; off >>= 1) {
-      const float v2 = __shfl_xor_sync(FULL, v, off, W);
-      const int i2 = __shfl_xor_sync(FULL, idx, off, W);
-      if (v2 > v || (v2 == v && i2 < idx)) {
-        v = v2;
-        idx = i2;
-      }
-    }
-    const int pl = idx;
-    plk[k] = pl;
-    const float piv = __shfl_sync(FULL, a[k], pl, W);
-    const float inv = 1.0f / piv;
-    if (i == pl && !used) {
-      used = true;
-      myk = k;
-      myinv = inv;
-    }
-    const bool elim = !used;
-    const float l = a[k] * inv;
-    if (elim) a[k] = l;
-    static_for<k + 1, N>([&](auto jconst) {
-      constexpr int j = decltype(jconst)::value;
-      const float u = __shfl_sync(FULL, a[j], pl, W);
-      if (elim) a[j] = fmaf(-l, u, a[j]);
-    });
-    const float ub = __shfl_sync(FULL, bx, pl, W);
-    if (elim) bx = fmaf(-l, ub, bx);
-  });
-}
-
-template <int N, int W>
-__device__ __forceinline__ float back_sub32(const float (&a)[N], float rhs, const int (&plk)[N], int myk,
-                                            float myinv) {
-  constexpr unsigned FULL = 0xffffffffu;
-  float xo = 0.0f;
-  static_for<0, N>([&](auto jconst) {
-    constexpr int j = N - 1 - decltype(jconst)::value;
-    const bool mine = (myk == j);
-    const float xl = mine ? rhs * myinv : 0.0f;
-    const float xj = __shfl_sync(FULL, xl, plk[j], W);
-    if (mine) xo = xj;
-    if (myk >= 0 && myk < j) rhs = fmaf(-a[j], xj, rhs);
-  });
-  return xo;
-}
-
-// Forward replay of the kept multipliers on a new right-hand side.
-template <int N, int W>
-__device__ __forceinline__ float forward32(const float (&a)[N], float r, const int (&plk)[N], int myk, bool row) {
-  constexpr unsigned FULL = 0xffffffffu;
-  static_for<0, N>([&](auto kconst) {
-    constexpr int k = decltype(kconst)::value;
-    const float rb = __shfl_sync(FULL, r, plk[k], W);
-    if (myk > k || (myk < 0 && row)) r = fmaf(-a[k], rb, r);
-  });
-  return r;
-}
-
 // ---- latency-oriented FP32 solve: Gauss-Jordan inverse with partial pivoting.
 // Pivot search: one integer max per segment over key = (bits(|a|) with the 5 low mantissa bits
 // cleared) | (31 - lane): the largest |a| (to 2^-18 relative) wins, ties go to the lowest lane.
@@ -354,10 +283,10 @@ __device__ __forceinline__ void gj32_steps(float (&a)[N], float (&v)[N], int lan
   static_for<K0, K1>([&](auto kconst) {
     constexpr int k = decltype(kconst)::value;
     const unsigned key = st.used ? 0u : ((__float_as_uint(a[k]) & 0x7fffffe0u) | (unsigned)(31 - lane));
+    const float own_inv = rcp_approx(a[k]);      // every lane, while the pivot search runs
     const int pl = seg_argmax_key<W>(key, lane);
     plk[k] = pl;
-    const float piv = __shfl_sync(FULL, a[k], pl, W);
-    const float inv = rcp_approx(piv);
+    const float inv = __shfl_sync(FULL, own_inv, pl, W);
     const bool me = (lane == pl);
     if (me) {
       st.used = true;
