@@ -48,6 +48,33 @@ __device__ void split_2d(const DevProblem& P, const double* ctrl, int f, const d
   brk[3] = 1.0;
 }
 
+// The same breakpoints from the three reference normals n(0), n(1/2), n(1) of the face
+// (direction independent, computed once per face).
+__device__ void split_2d_cached(const double* nref, const double* om, double* brk) {
+  const double g0 = dot_omega(2, om, nref), gh = dot_omega(2, om, nref + 2), g1 = dot_omega(2, om, nref + 4);
+  const double c0 = g0;
+  const double c2 = 2.0 * ((g0 - 2.0 * gh) + g1);
+  const double c1 = (g1 - g0) - c2;
+  double ra = 2.0, rb = 2.0;     // 2.0 = no root
+  if (c2 == 0.0) {
+    if (c1 != 0.0) ra = -c0 / c1;
+  } else {
+    const double disc = c1 * c1 - (4.0 * c2) * c0;
+    if (disc >= 0.0) {
+      const double sq = sqrt(disc);
+      const double qq = -0.5 * (c1 + (c1 >= 0.0 ? sq : -sq));
+      ra = qq / c2;
+      if (qq != 0.0) rb = c0 / qq;
+    }
+  }
+  ra = (ra > 0.0 && ra < 1.0) ? ra : 1.0;
+  rb = (rb > 0.0 && rb < 1.0) ? rb : 1.0;
+  brk[0] = 0.0;
+  brk[1] = fmin(ra, rb);
+  brk[2] = fmax(ra, rb);
+  brk[3] = 1.0;
+}
+
 __device__ inline int face_npoints(const DevProblem& P) {
   return (P.dim == 2) ? 3 * P.nf : P.K * P.K * P.nf * P.nf;
 }
@@ -77,10 +104,8 @@ __device__ inline PointData face_point(const DevProblem& P, const double* brk, i
 // Per-point data of one (face, direction) into shared memory; a = max(-g,0) w (owner
 // receiving) and max(g,0) w (other side receiving); basis values of both sides' face nodes.
 // Layout per point: [a_o, a_n, phi_o[Nf], phi_n[Nf]].
-__device__ void fill_points(const DevProblem& P, const double* ctrl, int f, int code, bool has_nbr,
-                            const double* om, double* sp, int lane) {
-  double brk[4] = {0.0, 1.0, 1.0, 1.0};
-  if (P.dim == 2) split_2d(P, ctrl, f, om, brk);
+__device__ void fill_points_brk(const DevProblem& P, const double* ctrl, int f, int code, bool has_nbr,
+                                const double* om, const double* brk, double* sp, int lane) {
   const int np = face_npoints(P);
   const int Nf = P.Nf, np1 = P.p + 1;
   const int stride = 2 + 2 * Nf;
@@ -101,6 +126,54 @@ __device__ void fill_points(const DevProblem& P, const double* ctrl, int f, int 
       orient_map(P.dim, code, pd.s0, pd.s1, t0, t1);
       for (int i = 0; i < Nf; ++i) o[2 + Nf + i] = face_basis(P.dim, gll, np1, i, t0, t1);
     }
+  }
+  __syncwarp();
+}
+
+__device__ void fill_points(const DevProblem& P, const double* ctrl, int f, int code, bool has_nbr,
+                            const double* om, double* sp, int lane) {
+  double brk[4] = {0.0, 1.0, 1.0, 1.0};
+  if (P.dim == 2) split_2d(P, ctrl, f, om, brk);
+  fill_points_brk(P, ctrl, f, code, has_nbr, om, brk, sp, lane);
+}
+
+// Direction-independent point data of a face for the unsplit rule (breakpoints 0, 1, 1, 1 in
+// 2D; the composite rule in 3D): sp rows [-, -, phi_o[Nf], phi_n[Nf]] and wn rows [w, n[dim]].
+// The per-direction inflow amounts are then set by cache_amounts with the same operations as
+// fill_points_brk.
+__device__ void fill_cache(const DevProblem& P, const double* ctrl, int f, int code, double* sp, double* wn,
+                           int lane) {
+  const double brk[4] = {0.0, 1.0, 1.0, 1.0};
+  const int np = face_npoints(P);
+  const int Nf = P.Nf, np1 = P.p + 1, dim = P.dim;
+  const int stride = 2 + 2 * Nf;
+  const double* geo = tabp(P, P.off_geo);
+  const double* gll = tabp(P, P.off_gll);
+  for (int q = lane; q < np; q += 32) {
+    PointData pd = face_point(P, brk, q);
+    double nv[3];
+    face_normal(dim, P.r, geo, ctrl, f, pd.s0, pd.s1, nv);
+    double* w = wn + q * (1 + dim);
+    w[0] = pd.w;
+    for (int c = 0; c < dim; ++c) w[1 + c] = nv[c];
+    double* o = sp + q * stride;
+    for (int i = 0; i < Nf; ++i) o[2 + i] = face_basis(dim, gll, np1, i, pd.s0, pd.s1);
+    double t0, t1;
+    orient_map(dim, code, pd.s0, pd.s1, t0, t1);
+    for (int i = 0; i < Nf; ++i) o[2 + Nf + i] = face_basis(dim, gll, np1, i, t0, t1);
+  }
+  __syncwarp();
+}
+
+__device__ void cache_amounts(const DevProblem& P, const double* wn, const double* om, double* sp, int np, int lane) {
+  const int dim = P.dim, stride = 2 + 2 * P.Nf;
+  for (int q = lane; q < np; q += 32) {
+    const double* w = wn + q * (1 + dim);
+    const double g = dot_omega(dim, om, w + 1);
+    const double mg = -g;
+    double* o = sp + q * stride;
+    o[0] = (mg > 0.0 ? mg : 0.0) * w[0];
+    o[1] = (g > 0.0 ? g : 0.0) * w[0];
   }
   __syncwarp();
 }
@@ -243,61 +316,98 @@ cudaError_t launch_mass_lu(const DevProblem& P, double* lu, int32_t* perm, cudaS
 }
 
 // ------------------------------------------------------------------ edge weights
-// One warp per (interior face, direction).  iface rows: owner, f, nbr, f_nbr, orient.
-__global__ void weights_kernel(DevProblem P, const int32_t* __restrict__ iface, int64_t n_iface, int weighting,
-                               const double* __restrict__ mt_lu, const int32_t* __restrict__ mt_perm,
-                               double* __restrict__ z_o, double* __restrict__ z_n, uint32_t* facecode,
-                               int shm_per_warp) {
+// One warp per interior face, all directions.  The unsplit rule's point data (normals, both
+// sides' basis values) are computed once per face; a direction whose 2D split has no root in
+// (0, 1) uses them (its breakpoints are exactly 0, 1, 1, 1, so the points, weights and normals
+// are the same numbers), and of that rule only the first piece's n_f points have nonzero
+// weight: the zero-length pieces add (+0 a) phi phi = +-0 terms, which leave a sum that started
+// from +0.0 unchanged, so they are skipped.  Directions whose split has roots recompute their
+// points as fill_points does.  iface rows: owner, f, nbr, f_nbr, orient.
+__global__ void weights_face_kernel(DevProblem P, const int32_t* __restrict__ iface, int64_t n_iface,
+                                    int weighting, const double* __restrict__ mt_lu,
+                                    const int32_t* __restrict__ mt_perm, double* __restrict__ z_o,
+                                    double* __restrict__ z_n, uint32_t* facecode, int shm_per_warp) {
   extern __shared__ double sh[];
   const int warp_in_block = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_in_block;
-  if (item >= n_iface * P.M) return;     // whole warp exits together
-  const int64_t fi = item / P.M;
-  const int d = (int)(item % P.M);
+  const int64_t fi = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_in_block;
+  if (fi >= n_iface) return;     // whole warp exits together
   const int32_t* row = iface + fi * 5;
   const int64_t owner = row[0], nbr = row[2];
   const int f = row[1], fn = row[3], code = row[4];
+  const int np = face_npoints(P);
+  const int Nf = P.Nf, dim = P.dim;
+  const int stride = 2 + 2 * Nf;
   double* wsh = sh + (size_t)warp_in_block * shm_per_warp;
   double* ctrl = wsh;                                   // Nv * dim
-  double* sp = ctrl + P.Nv * P.dim;                     // points
-  const int np = face_npoints(P);
-  const int Nf = P.Nf;
-  const int stride = 2 + 2 * Nf;
-  double* fb = sp + np * stride;                        // [2][Nf][Nf]
+  double* nref = ctrl + P.Nv * dim;                     // 3 x 2 (2D)
+  double* cache = nref + 6;                             // np x stride
+  double* wn = cache + np * stride;                     // np x (1 + dim)
+  double* scratch = wn + np * (1 + dim);                // np x stride (2D split directions)
+  double* fb = scratch + (dim == 2 ? np * stride : 0);  // [2][Nf][Nf]
   copy_ctrl(P, owner, ctrl, lane);
-  double om[3] = {P.omega[d * 3 + 0], P.omega[d * 3 + 1], P.omega[d * 3 + 2]};
-  fill_points(P, ctrl, f, code, true, om, sp, lane);
-  double mo = 0.0, mn = 0.0;
-  for (int t = lane; t < Nf * Nf; t += 32) {
-    const int i = t / Nf, j = t % Nf;
-    const double bo = block_entry(sp, np, stride, 0, 2, 2 + Nf, i, j);        // owner <- neighbour
-    const double bn = block_entry(sp, np, stride, 1, 2 + Nf, 2, i, j);        // neighbour <- owner
-    fb[t] = bo;
-    fb[Nf * Nf + t] = bn;
-    mo = fmax(mo, fabs(bo));
-    mn = fmax(mn, fabs(bn));
+  if (dim == 2 && lane < 3) {
+    const double* geo = tabp(P, P.off_geo);
+    double nv[3];
+    face_normal(2, P.r, geo, ctrl, f, lane == 0 ? 0.0 : (lane == 1 ? 0.5 : 1.0), 0.0, nv);
+    nref[2 * lane] = nv[0];
+    nref[2 * lane + 1] = nv[1];
   }
-  __syncwarp();
-  mo = warp_max(mo);
-  mn = warp_max(mn);
-  const bool eo = mo > 0.0, en = mn > 0.0;
-  double wo = 0.0, wn = 0.0;
-  if (weighting == SN_WEIGHT_UNITY) {
-    wo = eo ? 1.0 : 0.0;
-    wn = en ? 1.0 : 0.0;
-  } else if (weighting == SN_WEIGHT_FACE) {
-    wo = mo;
-    wn = mn;
-  } else {
-    wo = eo ? siginv_weight(P, fb, owner, f, mt_lu, mt_perm, lane) : 0.0;
-    wn = en ? siginv_weight(P, fb + Nf * Nf, nbr, fn, mt_lu, mt_perm, lane) : 0.0;
+  fill_cache(P, ctrl, f, code, cache, wn, lane);
+  for (int d = 0; d < P.M; ++d) {
+    const double om[3] = {P.omega[d * 3 + 0], P.omega[d * 3 + 1], P.omega[d * 3 + 2]};
+    double brk[4] = {0.0, 1.0, 1.0, 1.0};
+    if (dim == 2) split_2d_cached(nref, om, brk);
+    const bool unsplit = brk[1] == 1.0 && brk[2] == 1.0;
+    const double* sp;
+    int npe;
+    if (unsplit) {
+      npe = dim == 2 ? P.nf : np;
+      cache_amounts(P, wn, om, cache, npe, lane);
+      sp = cache;
+    } else {
+      fill_points_brk(P, ctrl, f, code, true, om, brk, scratch, lane);
+      sp = scratch;
+      npe = np;
+    }
+    double mo = 0.0, mn = 0.0;
+    for (int t = lane; t < Nf * Nf; t += 32) {
+      const int i = t / Nf, j = t % Nf;
+      const double bo = block_entry(sp, npe, stride, 0, 2, 2 + Nf, i, j);        // owner <- neighbour
+      const double bn = block_entry(sp, npe, stride, 1, 2 + Nf, 2, i, j);        // neighbour <- owner
+      fb[t] = bo;
+      fb[Nf * Nf + t] = bn;
+      mo = fmax(mo, fabs(bo));
+      mn = fmax(mn, fabs(bn));
+    }
+    __syncwarp();
+    mo = warp_max(mo);
+    mn = warp_max(mn);
+    const bool eo = mo > 0.0, en = mn > 0.0;
+    double wo = 0.0, wv = 0.0;
+    if (weighting == SN_WEIGHT_UNITY) {
+      wo = eo ? 1.0 : 0.0;
+      wv = en ? 1.0 : 0.0;
+    } else if (weighting == SN_WEIGHT_FACE) {
+      wo = mo;
+      wv = mn;
+    } else {
+      wo = eo ? siginv_weight(P, fb, owner, f, mt_lu, mt_perm, lane) : 0.0;
+      wv = en ? siginv_weight(P, fb + Nf * Nf, nbr, fn, mt_lu, mt_perm, lane) : 0.0;
+    }
+    if (lane == 0) {
+      z_o[fi * P.M + d] = wo;
+      z_n[fi * P.M + d] = wv;
+      if (eo) atomicOr(&facecode[(int64_t)d * P.E + owner], (en ? MODE_MIXED : MODE_PURE) << (2 * f));
+      if (en) atomicOr(&facecode[(int64_t)d * P.E + nbr], (eo ? MODE_MIXED : MODE_PURE) << (2 * fn));
+    }
+    __syncwarp();                        // fb and the point data are rewritten for the next direction
   }
-  if (lane == 0) {
-    z_o[fi * P.M + d] = wo;
-    z_n[fi * P.M + d] = wn;
-    if (eo) atomicOr(&facecode[(int64_t)d * P.E + owner], (en ? MODE_MIXED : MODE_PURE) << (2 * f));
-    if (en) atomicOr(&facecode[(int64_t)d * P.E + nbr], (eo ? MODE_MIXED : MODE_PURE) << (2 * fn));
-  }
+}
+
+static int weights_face_shm_per_warp(const DevProblem& P) {
+  const int np = (P.dim == 2) ? 3 * P.nf : P.K * P.K * P.nf * P.nf;
+  const int stride = 2 + 2 * P.Nf;
+  return P.Nv * P.dim + 6 + np * stride + np * (1 + P.dim) + (P.dim == 2 ? np * stride : 0) + 2 * P.Nf * P.Nf;
 }
 
 static int weights_shm_per_warp(const DevProblem& P) {
@@ -309,15 +419,14 @@ cudaError_t launch_weights(const DevProblem& P, const int32_t* iface, int64_t n_
                            const double* mt_lu, const int32_t* mt_perm, double* z_o, double* z_n,
                            uint32_t* facecode, cudaStream_t s) {
   if (n_iface == 0) return cudaSuccess;
-  const int spw = weights_shm_per_warp(P);
+  const int spw = weights_face_shm_per_warp(P);
   int warps = 4;
   while (warps > 1 && (size_t)warps * spw * sizeof(double) > 96 * 1024) warps >>= 1;
   const size_t shmem = (size_t)warps * spw * sizeof(double);
-  cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-  const int64_t items = n_iface * P.M;
-  const int64_t blocks = (items + warps - 1) / warps;
-  weights_kernel<<<(unsigned)blocks, warps * 32, shmem, s>>>(P, iface, n_iface, weighting, mt_lu, mt_perm, z_o, z_n,
-                                                            facecode, spw);
+  cudaFuncSetAttribute(weights_face_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+  const int64_t blocks = (n_iface + warps - 1) / warps;
+  weights_face_kernel<<<(unsigned)blocks, warps * 32, shmem, s>>>(P, iface, n_iface, weighting, mt_lu, mt_perm, z_o,
+                                                                 z_n, facecode, spw);
   return cudaGetLastError();
 }
 
