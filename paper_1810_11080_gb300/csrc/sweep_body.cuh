@@ -256,84 +256,57 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// Row-per-lane Gauss-Jordan on the segment: on return the lane that was chosen as pivot of
-// step k (plk[k], myk == k) holds in v[] row k of A^{-1}, with columns indexed by the original
-// row (= lane) index: x_k = sum_j v[j] b_j.  All rows are updated at every step, so there are
-// N dependent steps and no triangular solves.  Pivot rows are not scaled during the
-// elimination (row i -= (a_ik / a_pk) row p for i != p, one multiply-add per entry); after the
-// last step row p of [A | V] is a_pk e_k^T | a_pk (A^{-1})_k, and V is scaled by 1/a_pk once.
-struct GJState {
-  bool used;      // this lane's row has been a pivot row (or is not a row)
-  int myk;        // step at which it was the pivot row, or -1
-  float myinv;    // 1 / pivot of that step
-};
-
-template <int N>
-__device__ __forceinline__ void gj32_init(float (&v)[N], int i, bool row, GJState& st) {
-  st.used = !row;
-  st.myk = -1;
-  st.myinv = 0.0f;
-  static_for<0, N>([&](auto jconst) { v[decltype(jconst)::value] = (row && decltype(jconst)::value == i) ? 1.0f : 0.0f; });
-}
-
-// Steps [K0, K1) of the elimination.
-template <int N, int W, int K0, int K1>
-__device__ __forceinline__ void gj32_steps(float (&a)[N], float (&v)[N], int lane, int (&plk)[N], GJState& st) {
+// Row-per-lane Gauss-Jordan on the segment, [A | V] with V = I at the start.  All rows are
+// updated at every step, so there are N dependent steps and no triangular solves.  Pivot rows
+// are not scaled during the elimination (row i -= (a_ik / a_pk) row p for i != p, one
+// multiply-add per entry); V is scaled by 1/a_pk once at the end.  V's columns are kept in
+// pivot-step order: column m holds the identity column of the row chosen at step m.  Before
+// step k the pivot row's V part is nonzero only in columns 0..k-1 plus its own identity entry,
+// which enters column k at that step, so step k updates V's columns 0..k only (k + 1 shuffles
+// instead of N).  On return the lane chosen at step k (plk[k], myk == k) holds row k of A^{-1}
+// in step order: x_k = sum_m v[m] b_{plk[m]}.
+template <int N, int W>
+__device__ __forceinline__ void gj32(float (&a)[N], float (&v)[N], int lane, bool row, int (&plk)[N], int& myk) {
   constexpr unsigned FULL = 0xffffffffu;
-  static_for<K0, K1>([&](auto kconst) {
+  bool used = !row;
+  float myinv = 0.0f;
+  myk = -1;
+  static_for<0, N>([&](auto jconst) { v[decltype(jconst)::value] = 0.0f; });
+  static_for<0, N>([&](auto kconst) {
     constexpr int k = decltype(kconst)::value;
-    const unsigned key = st.used ? 0u : ((__float_as_uint(a[k]) & 0x7fffffe0u) | (unsigned)(31 - lane));
+    const unsigned key = used ? 0u : ((__float_as_uint(a[k]) & 0x7fffffe0u) | (unsigned)(31 - lane));
     const float own_inv = rcp_approx(a[k]);      // every lane, while the pivot search runs
     const int pl = seg_argmax_key<W>(key, lane);
     plk[k] = pl;
     const float inv = __shfl_sync(FULL, own_inv, pl, W);
     const bool me = (lane == pl);
     if (me) {
-      st.used = true;
-      st.myk = k;
-      st.myinv = inv;
+      used = true;
+      myk = k;
+      myinv = inv;
+      v[k] = 1.0f;                               // the pivot row's identity entry, in column k
     }
     const float l = me ? 0.0f : a[k] * inv;
     static_for<k + 1, N>([&](auto jconst) {
       constexpr int j = decltype(jconst)::value;
       a[j] = fmaf(-l, __shfl_sync(FULL, a[j], pl, W), a[j]);
     });
-    static_for<0, N>([&](auto jconst) {
+    static_for<0, k + 1>([&](auto jconst) {
       constexpr int j = decltype(jconst)::value;
       v[j] = fmaf(-l, __shfl_sync(FULL, v[j], pl, W), v[j]);
     });
   });
+  static_for<0, N>([&](auto jconst) { v[decltype(jconst)::value] *= myinv; });
 }
 
-template <int N>
-__device__ __forceinline__ void gj32_finish(float (&v)[N], const GJState& st) {
-  static_for<0, N>([&](auto jconst) { v[decltype(jconst)::value] *= st.myinv; });
-}
-
-// Row-per-lane Gauss-Jordan on the segment: on return the lane that was chosen as pivot of
-// step k (plk[k], myk == k) holds in v[] row k of A^{-1}, with columns indexed by the original
-// row (= lane) index: x_k = sum_j v[j] b_j.  All rows are updated at every step, so there are
-// N dependent steps and no triangular solves.  Pivot rows are not scaled during the
-// elimination (row i -= (a_ik / a_pk) row p for i != p, one multiply-add per entry); after the
-// last step row p of [A | V] is a_pk e_k^T | a_pk (A^{-1})_k, and V is scaled by 1/a_pk once.
+// y_k = sum_m v[m] r_{plk[m]} on the pivot lane of step k; r_j lives on lane j of the segment.
 template <int N, int W>
-__device__ __forceinline__ void gj32(float (&a)[N], float (&v)[N], int i, int lane, bool row, int (&plk)[N],
-                                     int& myk) {
-  GJState st;
-  gj32_init<N>(v, i, row, st);
-  gj32_steps<N, W, 0, N>(a, v, lane, plk, st);
-  gj32_finish<N>(v, st);
-  myk = st.myk;
-}
-
-// y_k = sum_j v[j] r_j on the pivot lane of step k; r_j lives on lane j of the segment.
-template <int N, int W>
-__device__ __forceinline__ float gj_apply(const float (&v)[N], float r) {
+__device__ __forceinline__ float gj_apply(const float (&v)[N], float r, const int (&plk)[N]) {
   constexpr unsigned FULL = 0xffffffffu;
   float s0 = 0.0f, s1 = 0.0f;
   static_for<0, N>([&](auto jconst) {
     constexpr int j = decltype(jconst)::value;
-    const float rj = __shfl_sync(FULL, r, j, W);
+    const float rj = __shfl_sync(FULL, r, plk[j], W);
     if (j & 1) s1 = fmaf(v[j], rj, s1);
     else s0 = fmaf(v[j], rj, s0);
   });
@@ -520,8 +493,8 @@ __device__ __forceinline__ void bodymx(const DevProblem& Pb, const SweepArgs& sa
   });
   int plk[N], myk;
   float v[N];
-  gj32<N, W>(a, v, i, lane, row, plk, myk);
-  const float xhat = gj_apply<N, W>(v, (float)b);     // on the pivot lane of step myk
+  gj32<N, W>(a, v, lane, row, plk, myk);
+  const float xhat = gj_apply<N, W>(v, (float)b, plk);     // on the pivot lane of step myk
   const double xh64 = (double)xhat;
   double r = b;
   static_for<0, N>([&](auto jconst) {
@@ -529,7 +502,7 @@ __device__ __forceinline__ void bodymx(const DevProblem& Pb, const SweepArgs& sa
     const double xj = __shfl_sync(FULL, xh64, plk[j], W);
     r = fma(-a64[j], xj, r);
   });
-  const float dx = gj_apply<N, W>(v, (float)r);
+  const float dx = gj_apply<N, W>(v, (float)r, plk);
   if (row && myk >= 0) {
     const int64_t o = ((int64_t)d * E + e) * N + myk;
     const double x = xh64 + (double)dx;
@@ -740,8 +713,8 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
   static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = ah[decltype(jconst)::value]; });
   int plk[N], myk;
   float v[N];
-  gj32<N, W>(a, v, i, lane, row, plk, myk);
-  const float xhat = gj_apply<N, W>(v, rbh);        // on the pivot lane of step myk
+  gj32<N, W>(a, v, lane, row, plk, myk);
+  const float xhat = gj_apply<N, W>(v, rbh, plk);        // on the pivot lane of step myk
   // r = b - A xhat in double-single, four independent accumulation chains
   float rh[4] = {rbh, 0.0f, 0.0f, 0.0f}, rl[4] = {rbl, 0.0f, 0.0f, 0.0f};
   static_for<0, N>([&](auto jconst) {
@@ -755,7 +728,7 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
   ds_add(rh[0], rl[0], rh[1], rl[1]);
   ds_add(rh[2], rl[2], rh[3], rl[3]);
   ds_add(rh[0], rl[0], rh[2], rl[2]);
-  const float dx = gj_apply<N, W>(v, rh[0] + rl[0]);
+  const float dx = gj_apply<N, W>(v, rh[0] + rl[0], plk);
   if (row && myk >= 0) {
     float oh2, ol2;
     ds_two_sum(xhat, dx, oh2, ol2);

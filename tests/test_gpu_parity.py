@@ -74,6 +74,20 @@ def test_fp64_sweep_parity_with_direction_sources_and_inflow():
     assert rel_l2(out, ref) <= FP64_TOL
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("p", [2, 3])
+def test_mixed_sweep_with_direction_sources_and_inflow(p, prec):
+    prob = si.make_config("2d_sine_q2_p1_s4", n=6, p=p)
+    prob, _f, _fac = annulus_mms(prob)
+    disc, G = oracle_graph(prob, "face")
+    ctx, _ = gpu_ctx(prob, "face")
+    phi, psi_old = random_state(prob, seed=3)
+    ref = Sweeper(disc, G).sweep(phi, psi_old)
+    out = np.zeros_like(psi_old)
+    ctx.sn_sweep(phi, psi_old, out, prec)
+    assert rel_l2(out, ref) <= MIXED_TOL
+
+
 def test_fp64_sweep_device_pointers_match_host_pointers():
     prob = si.make_config("2d_smooth_q3_p3_s8", n=8)
     ctx, _ = gpu_ctx(prob, "face")
