@@ -238,7 +238,7 @@ sn_status sn_batch_source_iterate(sn_batch* batch, double tol, int max_iter, int
 /* ---- Learned flux predictor (this project's addition; the paper has none).  A per-element
  * MLP -- x -> tanh(x W1 + b1) -> tanh(. W2 + b2) -> . W3 + b3, width 64, BF16 weights, FP32
  * accumulation, trained by Adam on the device -- supplies the initial scalar flux of source
- * iteration and a post-sweep correction; plain source iteration is the fallback and the judge
+ * iteration and a post-sweep correction; plain source iteration is the fallback and the arbiter
  * of convergence.  Packed parameters: W1 [n_in][64], b1 [64], W2 [64][64], b2 [64],
  * W3 [64][n_out], b3 [n_out] (FP32 masters). */
 #define SN_FEATURES 16

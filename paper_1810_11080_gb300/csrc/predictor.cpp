@@ -1,6 +1,6 @@
 // Learned flux predictor (C ABI, include/snsweep.h): the per-element MLP object with its
 // training loop, the predictor data calls, and source iteration with a predicted initial
-// scalar flux and a learned post-sweep correction.  Plain source iteration stays the judge:
+// scalar flux and a learned post-sweep correction.  Plain source iteration stays the arbiter:
 // a correction is kept only if the next plain residual is below the one before it, and
 // convergence is only declared on a step whose input came from a plain step.
 #include <algorithm>
