@@ -204,13 +204,23 @@ def run_gpu(args):
     t0 = time.time()
     gstats = ctx.sn_build_graph("face", 10)
     t_graph = time.time() - t0
-    ctx.sn_set_launch(g.SN_LAUNCH_DATAFLOW if args.launch == "dataflow" else g.SN_LAUNCH_LEVELS)
+
+    def set_schedule(prec):
+        """Launch schedule of a form: the library's autotuner (levels or dataflow, CTAs per SM),
+        or the one named by --launch."""
+        if args.launch == "auto":
+            mode, bps = ctx.sn_autotune(prec)
+        else:
+            mode, bps = (g.SN_LAUNCH_DATAFLOW if args.launch == "dataflow" else g.SN_LAUNCH_LEVELS), 0
+            ctx.sn_set_launch(mode, bps)
+        return {"mode": "dataflow" if mode == g.SN_LAUNCH_DATAFLOW else "levels", "blocks_per_sm": bps}
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
 
     def timed_steps(prec):
+        sched = set_schedule(prec)
         ctx.sn_si_begin(None)
         for _ in range(args.warmup):
             ctx.sn_si_step(prec)
@@ -233,7 +243,11 @@ def run_gpu(args):
         ms_total = max_over_ranks(ev0.elapsed_time(ev1))
         return dict(value=job_throughput(ws, updates, args.steps, ms_total), ms_per_step=ms_total / args.steps,
                     sweep_ms_per_step=sweep_ms / args.steps, launches=int(ctx.sn_kernel_launches() - l0),
-                    clocks=clk)
+                    clocks=clk, schedule=sched)
+
+    def use_schedule(sched):
+        ctx.sn_set_launch(g.SN_LAUNCH_DATAFLOW if sched["mode"] == "dataflow" else g.SN_LAUNCH_LEVELS,
+                          sched["blocks_per_sm"])
 
     forms = {"fp64": g.SN_PREC_FP64, "mixed": g.SN_PREC_MIXED, "mixed_ds": g.SN_PREC_MIXED_DS}
     meas = {k: timed_steps(v) for k, v in forms.items()}
@@ -250,6 +264,7 @@ def run_gpu(args):
     phi2_h = torch.zeros((E, N), dtype=torch.float64, pin_memory=True).numpy()
     psa = torch.zeros((M, E, N), dtype=torch.float64, pin_memory=True).numpy()
     psb = torch.zeros((M, E, N), dtype=torch.float64, pin_memory=True).numpy()
+    use_schedule(meas[head]["schedule"])
     for _ in range(max(1, args.warmup)):
         ctx.sn_sweep(phi_h, psa, psb, hp)
         ctx.sn_moment(psb, phi_h, phi2_h)
@@ -272,6 +287,7 @@ def run_gpu(args):
     phis = {}
     for k, prec in forms.items():
         phis[k] = np.zeros((E, N))
+        use_schedule(meas[k]["schedule"])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = ctx.sn_source_iterate(1e-8, 2000, prec, phi_out=phis[k])
@@ -285,7 +301,9 @@ def run_gpu(args):
 
     def roofline(kind, m):
         pcode = {"fp64": 0, "mixed": 1, "mixed_ds": 2}[kind]
-        kname = f"sweep_level_kernel<{dim},{prob.p},{pcode}> (all level launches of one sweep)"
+        flow = m["schedule"]["mode"] == "dataflow"
+        kname = (f"sweep_flow_kernel<{dim},{prob.p},{pcode}> (one persistent launch per sweep)" if flow else
+                 f"sweep_level_kernel<{dim},{prob.p},{pcode}> (all level launches of one sweep)")
         if kind == "mixed_ds":
             fpu = ds_fp32_flops_per_update(dim, prob.p, inflow_faces)
             peak, unit, src = FP32_PEAK_TFLOPS, "TFLOP/s (FP32 pipe)", "FP32 FFMA microbenchmark (of measured)"
@@ -294,7 +312,7 @@ def run_gpu(args):
                 mixed_fp64_flops_per_update(dim, prob.p, inflow_faces)
             peak, unit, src = FP64_PEAK_TFLOPS, "TFLOP/s (FP64 pipe)", "FP64 DFMA microbenchmark (of measured)"
         ach = fpu * updates / (m["sweep_ms_per_step"] / 1e3) / 1e12
-        traffic, tsrc = traffic_for(kind)
+        traffic, tsrc = (None, None) if flow else traffic_for(kind)
         return {"bound": "alu", "kernel": kname, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
                 "traffic": traffic, "traffic_unit": "bytes per level launch (sweep average)",
                 "traffic_source": tsrc, "launches_per_step": m["launches"] // max(1, args.steps),
@@ -306,7 +324,7 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[head], "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "precision": PRECISION_DESC[head],
                    "weighting": "face", "parallelism": "replicas" if ws > 1 else "single",
-                   "launch": args.launch,
+                   "launch": args.launch, "schedule": meas[head]["schedule"],
                    "l2": "inputs larger than L2 (psi 2x84 MB + element factors 117 MB + FP32 copy 59 MB)"},
         "roofline": roofline(head, meas[head]),
         "e2e": {"value": updates * args.steps / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": h2d,
@@ -314,6 +332,7 @@ def run_gpu(args):
         "gpu_launches": meas[head]["launches"],
         "clocks": meas[head]["clocks"],
         "forms": {k: {"value": meas[k]["value"], "ms_per_step": meas[k]["ms_per_step"], "dtype": DTYPES[k],
+                      "schedule": meas[k]["schedule"],
                       "precision": PRECISION_DESC[k], "roofline": roofline(k, meas[k]),
                       "gpu_launches": meas[k]["launches"], "clocks": meas[k]["clocks"],
                       "time_to_1e-8_s": tts[k]["seconds"], "iters_to_1e-8": tts[k]["iters"],
@@ -528,8 +547,8 @@ def main():
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D twisted-mesh measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-predictor measurement")
     ap.add_argument("--learned-n", type=int, default=24, help="mesh size n^3 of the learned-predictor measurement")
-    ap.add_argument("--launch", default="levels", choices=["levels", "dataflow"],
-                    help="sweep schedule: one launch per level, or one persistent dataflow launch")
+    ap.add_argument("--launch", default="auto", choices=["auto", "levels", "dataflow"],
+                    help="sweep schedule per form: the autotuner's choice, one launch per level, or one persistent dataflow launch")
     ap.add_argument("--form", default="mixed_ds", choices=["fp64", "mixed", "mixed_ds"],
                     help="form reported as the headline value (all three are measured)")
     ap.add_argument("--quick", action="store_true",
