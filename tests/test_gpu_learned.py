@@ -113,6 +113,7 @@ def test_trained_predictor_gains_over_plain_source_iteration():
     from paper_1810_11080_gb300 import learned
     stream = torch.cuda.Stream()
     init, corr, cfg = learned.build(learned.load(MODEL), stream=stream.cuda_stream)
+    total_plain = total_learned = 0
     for seed in (5000, 5002):
         prob = si.make_config("3d_smooth_q2_p2_s12", n=12, seed=seed)
         ctx = g.setup_problem(prob, stream=stream.cuda_stream)
@@ -125,3 +126,6 @@ def test_trained_predictor_gains_over_plain_source_iteration():
               f"{res['ms_total']:.0f} ms (accepted {res['accepted']}, rejected {res['rejected']})")
         assert res["converged"] and res["iters"] < plain["iters"]
         assert np.linalg.norm(phi_learn - phi_plain) / np.linalg.norm(phi_plain) <= 1e-6
+        total_plain += plain["iters"]
+        total_learned += res["iters"]
+    assert total_learned <= 0.9 * total_plain, (total_learned, total_plain)
