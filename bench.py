@@ -196,7 +196,11 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
-    prob = make_problem()
+    if args.quick and args.quick_workload:
+        import sn_inputs as si
+        prob = si.make_config(args.quick_workload)
+    else:
+        prob = make_problem()
     dim, E, N, M = prob.mesh.dim, prob.mesh.n_elem, (prob.p + 1) ** prob.mesh.dim, len(prob.w)
     updates = E * M
     stream = torch.cuda.Stream(device=local)
@@ -255,7 +259,7 @@ def run_gpu(args):
     hp = forms[head]
     if args.quick:
         if rank == 0:
-            return {"metric": METRIC, "quick": True,
+            return {"metric": METRIC, "quick": True, "workload": args.quick_workload or WORKLOAD,
                     **{k: {kk: vv for kk, vv in m.items() if kk != "clocks"} for k, m in meas.items()}}
         return None
 
@@ -553,6 +557,9 @@ def main():
                     help="form reported as the headline value (all three are measured)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no e2e, time-to-tolerance or CPU legs): for profiler launch lists")
+    ap.add_argument("--quick-workload", default=None,
+                    choices=["2d_sine_q2_p1_s4", "2d_smooth_q3_p3_s8", "3d_twist_q2_p2_s8", "3d_smooth_q2_p2_s12"],
+                    help="with --quick: time this configuration instead of the default workload")
     ap.add_argument("--cpu-sample-dirs", type=int, default=1)
     args = ap.parse_args()
     if args.warmup < 3:
