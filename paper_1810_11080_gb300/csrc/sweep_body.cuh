@@ -614,8 +614,13 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
   }
   const uint32_t code = valid ? sa.facecode[(int64_t)d * E + e] : 0u;
   const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[(int64_t)d * E + e] : 0;
-  // inflow face blocks into the matrix
+  // inflow face blocks into the matrix; in 2D the block rows are also kept in shared memory
+  // ([face][entry][hi, lo][lane] per warp of a 128-thread block) for the right-hand side after
+  // the wait
+  float* bsave = nullptr;
   if constexpr (S::FACES_PRE) {
+    __shared__ float bsave_all[4][2 * DIM][NF][2][32];
+    bsave = &bsave_all[(threadIdx.x >> 5) & 3][0][0][0][0];
     int mrank = 0;
     static_for<0, 2 * DIM>([&](auto fconst) {
       constexpr int f = decltype(fconst)::value;
@@ -628,6 +633,8 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
           constexpr int fj = decltype(jconst)::value;
           constexpr int c = fvi<DIM, P_>(f, fj);
           ds_add(ah[c], al[c], Bh[fj], Bl[fj]);
+          bsave[((f * NF + fj) * 2 + 0) * 32 + lane] = Bh[fj];
+          bsave[((f * NF + fj) * 2 + 1) * 32 + lane] = Bl[fj];
         });
       }
       if (mode == MODE_MIXED) ++mrank;
@@ -685,7 +692,13 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
               tl[fj] = __ldg(pl_ + o);
             }
           }
-          if constexpr (S::FACES_PRE) ds_block_row<DIM, P_, false>(bh, bl, sa, mode, f, fi, mbase + mrank, oh, ol, Bh, Bl);
+          if constexpr (S::FACES_PRE) {
+#pragma unroll
+            for (int fj = 0; fj < NF; ++fj) {
+              Bh[fj] = bsave[((f * NF + fj) * 2 + 0) * 32 + lane];
+              Bl[fj] = bsave[((f * NF + fj) * 2 + 1) * 32 + lane];
+            }
+          }
           float sh2 = 0.0f, sl2 = 0.0f;  // second accumulator: two independent chains
 #pragma unroll
           for (int fj = 0; fj < NF; ++fj) {
@@ -696,7 +709,13 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
           }
           ds_add(rbh, rbl, sh2, sl2);
         } else if (Pb.psi_inc != nullptr) {  // incident flux on the domain boundary
-          if constexpr (S::FACES_PRE) ds_block_row<DIM, P_, false>(bh, bl, sa, mode, f, fi, mbase + mrank, oh, ol, Bh, Bl);
+          if constexpr (S::FACES_PRE) {
+#pragma unroll
+            for (int fj = 0; fj < NF; ++fj) {
+              Bh[fj] = bsave[((f * NF + fj) * 2 + 0) * 32 + lane];
+              Bl[fj] = bsave[((f * NF + fj) * 2 + 1) * 32 + lane];
+            }
+          }
           const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * 2 * DIM + f]) * NF;
 #pragma unroll
           for (int fj = 0; fj < NF; ++fj) {
