@@ -1,0 +1,46 @@
+"""bench.py's output contract, checked without a GPU: the reference arm (the oracle timed on the
+host) prints one JSON line with the keys the bench contract names, and the per-launch DRAM
+traffic is only reported for the kernel sources it was captured on."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference"
+    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] >= 3 and d["n_gpus"] == 1
+    assert d["higher_is_better"] is True and d["vs_baseline"] is None
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_is_reported_only_for_the_captured_sources():
+    sys.path.insert(0, ROOT)
+    import bench
+    h = bench.kernel_sources_sha256()
+    assert h == bench.kernel_sources_sha256() and len(h) == 64
+    saved = dict(bench.TRAFFIC)
+    try:
+        bench.TRAFFIC["mixed_ds"] = {"bytes_per_launch": 123, "profile": "p.md", "sources_sha256": h}
+        assert bench.traffic_for("mixed_ds") == (123, "p.md")
+        bench.TRAFFIC["mixed_ds"] = {"bytes_per_launch": 123, "profile": "p.md", "sources_sha256": "0" * 64}
+        assert bench.traffic_for("mixed_ds") == (None, None)
+        assert bench.traffic_for("fp64") == (None, None) or "fp64" in saved
+    finally:
+        bench.TRAFFIC.clear()
+        bench.TRAFFIC.update(saved)
