@@ -1,7 +1,7 @@
 // FP64 / FP32 fused multiply-add throughput of one GPU: 8 independent FMA chains per thread,
 // 16-way unrolled, on SMs x {4,8} blocks of 256 threads.  Used to measure the FP64 pipe peak
 // that the sweep roofline is reported against (the measured peaks file has HBM and BF16 only).
-// Build: nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o fmabench fmabench.cu
+// Build and run: nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o /tmp/fp_peaks bench_fp_peaks.cu && /tmp/fp_peaks
 #include <cstdio>
 #include <cuda_runtime.h>
 template <typename T>

@@ -112,6 +112,20 @@ sn_status sn_set_discretization(sn_ctx* ctx, int p, int face_subdiv);
  * (2D problems use the first two components), w [n_dir] > 0.  n_dir in 1..4096. */
 sn_status sn_set_quadrature(sn_ctx* ctx, int n_dir, const double* omega, const double* w);
 
+/* Level-symmetric S_N set [Sec. 2, after eq. 2: omega_d > 0, sum omega_d = 4 pi; the paper's
+ * results use level-symmetric S2 / S4 sets].  Needs no context and no GPU.
+ *   N in {2, 4, 6, 8, 12}; dim 3: all eight octants, N(N+2) directions, weights (pi/2) x the
+ *   octant point weight; dim 2: the four octants with Omega_z > 0 (the problem does not depend
+ *   on z, each direction stands for its mirror image), N(N+2)/2 directions, weights pi x the
+ *   octant point weight.  Construction: mu_i^2 = mu_1^2 + (i-1) 2 (1 - 3 mu_1^2)/(N-2); octant
+ *   points = level-index triples (i, j, k), i + j + k = N/2 + 2 (i fastest, then j, then k),
+ *   weighted by the published 7-digit class weights normalised to sum 1 per octant; octants in
+ *   sign order (+,+,+), (-,+,+), (+,-,+), (-,-,+), then the same with Omega_z < 0.
+ *   *n_dir receives the number of directions.  omega [n_dir][3] and w [n_dir] are host arrays
+ *   written when both are non-NULL (both NULL: size query only).
+ * Errors: SN_EINVAL (N not tabulated, dim not 2 or 3, n_dir NULL, exactly one of omega / w NULL). */
+sn_status sn_quadrature_level_symmetric(int N, int dim, int* n_dir, double* omega, double* w);
+
 /* Materials and sources [Sec. 2, eqs. 1, 8].
  *   sigma_t, sigma_s [n_elem] element-constant cross sections (sigma_t > 0, sigma_s >= 0).
  *   q        [n_elem][N] nodal isotropic source, or NULL (= 0).
@@ -142,6 +156,15 @@ sn_status sn_build_graph(sn_ctx* ctx, int weighting, int exact_max, sn_graph_sta
  *   blocks_per_sm: CTAs of 128 threads per SM for the dataflow grid (0 = occupancy limit).
  * May be called at any time; applies to later sweeps. */
 sn_status sn_set_launch(sn_ctx* ctx, int mode, int blocks_per_sm);
+
+/* Poll limit of one dependency wait of the dataflow schedule (no counterpart in the paper):
+ * a warp that has polled an upwind completion flag `polls` times without seeing it set stops
+ * waiting, sets the sweep's device error word and lets every other wait and the work queue stop
+ * early; the kernel then returns normally and the sweep call reports SN_ETIMEOUT (its results
+ * are not valid).  0 restores the default of 2^20 polls (~0.1-1 s); small values make a wait
+ * give up on purpose, which is how the timeout path is tested.  Applies to later sweeps of the
+ * context and of batches created afterwards.  Errors: SN_EINVAL (polls < 0). */
+sn_status sn_set_spin_limit(sn_ctx* ctx, int64_t polls);
 
 /* Autotuner (no counterpart in the paper): times three source iterations of every candidate
  * schedule -- per-level launches, or the dataflow launch with 1, 2, 4 or the maximum resident
@@ -305,9 +328,10 @@ sn_status sn_source_iterate_learned(sn_ctx* ctx, double tol, int max_iter, int p
  * Computes, on `cuda_stream` of device `device`, the same values as sn_moment:
  *   phi_out[e][m] = sum_d w[d] psi[d][e][m]   (d ascending)
  *   *residual     = max |phi_out - phi_prev| / max |phi_out|   (phi_prev NULL = 0)
- * w [n_dir], psi [n_dir][n_elem][n_dofs], phi_prev / phi_out [n_elem][n_dofs]: DEVICE pointers,
- * caller-owned (SN_EINVAL for host pointers).  residual: host pointer or NULL; when given, the
- * call synchronises the stream.  No scattering source is produced (there is no context).
+ * w [n_dir], psi [n_dir][n_elem][n_dofs], phi_prev / phi_out [n_elem][n_dofs]: caller-owned
+ * pointers to memory of `device` or managed memory (SN_EINVAL for host pointers and for buffers
+ * of another device).  residual: host pointer or NULL; when given, the call synchronises the
+ * stream.  The calling thread's current device is the same on return as before the call.  No scattering source is produced (there is no context).
  * Limit: n_elem * n_dofs <= 4,194,304 (SN_EINVAL beyond): the reduction scratch is a fixed
  * 256 KiB file-scope device array that every GPU loading the library holds until exit.  Calls
  * share that array and it keeps the last call's contents (every call overwrites what it

@@ -27,7 +27,8 @@ EXPORTED = ["sn_create", "sn_destroy", "sn_last_error", "sn_set_mesh", "sn_set_d
             "sn_batch_set_launch", "sn_batch_tune", "sn_batch_si_begin", "sn_batch_si_step",
             "sn_batch_source_iterate", "sn_mlp_create", "sn_mlp_destroy", "sn_mlp_num_params", "sn_mlp_params",
             "sn_mlp_forward", "sn_mlp_grad", "sn_mlp_train", "sn_predictor_features", "sn_predictor_init_targets",
-            "sn_predictor_corr_data", "sn_source_iterate_learned", "sn_predictor_initial_phi"]
+            "sn_predictor_corr_data", "sn_source_iterate_learned", "sn_predictor_initial_phi",
+            "sn_quadrature_level_symmetric", "sn_set_spin_limit"]
 
 
 class sn_graph_stats(ctypes.Structure):
@@ -109,6 +110,8 @@ def load(path=LIB_PATH):
                                           ctypes.POINTER(sn_si_stats), ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32)]),
         "sn_moment_noalloc": (I, [I, P, I, I64, I, P, P, P, P, ctypes.POINTER(D)]),
+        "sn_quadrature_level_symmetric": (I, [I, I, ctypes.POINTER(I), P, P]),
+        "sn_set_spin_limit": (I, [P, I64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -159,6 +162,20 @@ def sn_moment_noalloc(device, stream, w, psi, phi_prev, phi_out):
     if st != SN_OK:
         raise SnError(st, "sn_moment_noalloc failed (device pointers only; n_elem*n_dofs <= 4194304)")
     return r.value
+
+
+def sn_quadrature_level_symmetric(N, dim):
+    """Level-symmetric S_N set from the library (host arrays): returns (omega [M][3], w [M])."""
+    n = ctypes.c_int()
+    st = lib().sn_quadrature_level_symmetric(int(N), int(dim), ctypes.byref(n), None, None)
+    if st != SN_OK:
+        raise SnError(st, f"sn_quadrature_level_symmetric(N={N}, dim={dim}) failed")
+    omega = np.zeros((n.value, 3))
+    w = np.zeros(n.value)
+    st = lib().sn_quadrature_level_symmetric(int(N), int(dim), ctypes.byref(n), omega.ctypes.data, w.ctypes.data)
+    if st != SN_OK:
+        raise SnError(st, f"sn_quadrature_level_symmetric(N={N}, dim={dim}) failed")
+    return omega, w
 
 
 class Context:
@@ -252,6 +269,9 @@ class Context:
 
     def sn_set_launch(self, mode, blocks_per_sm=0):
         return self._check(self._lib.sn_set_launch(self._c, int(mode), int(blocks_per_sm)))
+
+    def sn_set_spin_limit(self, polls):
+        return self._check(self._lib.sn_set_spin_limit(self._c, int(polls)))
 
     def sn_autotune(self, precision=SN_PREC_MIXED_DS):
         m, b = ctypes.c_int(), ctypes.c_int()

@@ -48,7 +48,7 @@ def build(verbose=False, extra_nvcc=()):
         "batch.cu": [],
         "mlp.cu": [],
     }
-    cpp = ["api.cpp", "batch_api.cpp", "predictor.cpp", "tables.cpp", "fas.cpp"]
+    cpp = ["api.cpp", "batch_api.cpp", "predictor.cpp", "tables.cpp", "fas.cpp", "quadrature.cpp"]
     jobs = []
     for src, flags in cu.items():
         obj = os.path.join(BUILD, src + ".o")

@@ -368,16 +368,22 @@ sn_status sn_set_quadrature(sn_ctx* c, int n_dir, const double* omega, const dou
 }
 
 namespace {
-sn_status upload(sn_ctx* c, double*& dst, const double* src, size_t n, bool check_pos, bool allow_zero) {
-  std::vector<double> h(n);
+// Host copy of a caller array (host or device pointer), checked: finite, and for cross sections
+// > 0 (or >= 0 with allow_zero).
+sn_status fetch_checked(sn_ctx* c, std::vector<double>& h, const double* src, size_t n, bool check_pos,
+                        bool allow_zero) {
+  h.resize(n);
   if (is_device_ptr(src)) SN_CUDA(c, cudaMemcpy(h.data(), src, n * 8, cudaMemcpyDeviceToHost));
   else std::memcpy(h.data(), src, n * 8);
   for (double v : h) {
     SN_REQ(c, std::isfinite(v), SN_EINVAL, "non-finite material or source value");
     if (check_pos) SN_REQ(c, allow_zero ? v >= 0.0 : v > 0.0, SN_EINVAL, "cross section out of range");
   }
-  SN_CUDA(c, dalloc(dst, n));
-  SN_CUDA(c, cudaMemcpy(dst, h.data(), n * 8, cudaMemcpyHostToDevice));
+  return SN_OK;
+}
+sn_status upload(sn_ctx* c, double*& dst, const std::vector<double>& h) {
+  SN_CUDA(c, dalloc(dst, h.size()));
+  SN_CUDA(c, cudaMemcpy(dst, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
   return SN_OK;
 }
 }  // namespace
@@ -388,25 +394,30 @@ sn_status sn_set_materials(sn_ctx* c, const double* sigma_t, const double* sigma
   SN_REQ(c, c->mesh_set && c->disc_set && c->quad_set, SN_ESTATE, "mesh, discretization and quadrature first");
   SN_REQ(c, sigma_t && sigma_s, SN_EINVAL, "null cross sections");
   cudaSetDevice(c->device);
+  // every array is checked before anything is replaced: a rejected call changes nothing
+  std::vector<double> ht, hs, hq, hqd, hpi;
   sn_status st;
-  if ((st = upload(c, c->d_sig_t, sigma_t, c->E, true, false)) != SN_OK) return st;
-  if ((st = upload(c, c->d_sig_s, sigma_s, c->E, true, true)) != SN_OK) return st;
+  if ((st = fetch_checked(c, ht, sigma_t, c->E, true, false)) != SN_OK) return st;
+  if ((st = fetch_checked(c, hs, sigma_s, c->E, true, true)) != SN_OK) return st;
   if (q) {
-    if ((st = upload(c, c->d_q, q, (size_t)c->E * c->N, false, false)) != SN_OK) return st;
+    if ((st = fetch_checked(c, hq, q, (size_t)c->E * c->N, false, false)) != SN_OK) return st;
   } else {
-    SN_CUDA(c, dalloc(c->d_q, (size_t)c->E * c->N));
-    SN_CUDA(c, cudaMemset(c->d_q, 0, (size_t)c->E * c->N * 8));
+    hq.assign((size_t)c->E * c->N, 0.0);
   }
-  dfree(c->d_qdir);
-  dfree(c->d_psi_inc);
-  if (q_dir && (st = upload(c, c->d_qdir, q_dir, (size_t)c->M * c->E * c->N, false, false)) != SN_OK) return st;
-  if (psi_inc && c->n_bdr > 0 &&
-      (st = upload(c, c->d_psi_inc, psi_inc, (size_t)c->M * c->n_bdr * c->Nf, false, false)) != SN_OK)
+  if (q_dir && (st = fetch_checked(c, hqd, q_dir, (size_t)c->M * c->E * c->N, false, false)) != SN_OK) return st;
+  const bool has_inc = psi_inc && c->n_bdr > 0;
+  if (has_inc && (st = fetch_checked(c, hpi, psi_inc, (size_t)c->M * c->n_bdr * c->Nf, false, false)) != SN_OK)
     return st;
   // sigma_t enters the graph (siginvface weights): rebuild it
-  if (c->graph_ready) {
-    free_graph_state(c);
-  }
+  if (c->graph_ready) free_graph_state(c);
+  c->mat_set = false;
+  if ((st = upload(c, c->d_sig_t, ht)) != SN_OK) return st;
+  if ((st = upload(c, c->d_sig_s, hs)) != SN_OK) return st;
+  if ((st = upload(c, c->d_q, hq)) != SN_OK) return st;
+  dfree(c->d_qdir);
+  dfree(c->d_psi_inc);
+  if (q_dir && (st = upload(c, c->d_qdir, hqd)) != SN_OK) return st;
+  if (has_inc && (st = upload(c, c->d_psi_inc, hpi)) != SN_OK) return st;
   c->mat_set = true;
   return SN_OK;
 }
@@ -682,6 +693,15 @@ sn_status sn_set_launch(sn_ctx* c, int mode, int blocks_per_sm) {
   return SN_OK;
 }
 
+sn_status sn_set_spin_limit(sn_ctx* c, int64_t polls) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, polls >= 0, SN_EINVAL, "polls must be >= 0");
+  c->spin_limit = (long long)polls;
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);   // captured launches hold the old limit
+  c->graphs.clear();
+  return SN_OK;
+}
+
 sn_status sn_autotune(sn_ctx* c, int precision, int* mode_out, int* blocks_per_sm_out) {
   if (!c) return SN_EINVAL;
   SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
@@ -743,7 +763,7 @@ sn_status run_levels(sn_ctx* c, int prec, const double* psi_old, double* psi_new
   unsigned long long* head = c->d_red + 3;
   SweepArgs sa{c->d_facecode, c->d_mixed_off, c->d_mixedB, c->d_mixedB32, c->d_mixedB32lo, c->d_src,
                psi_old, psi_new, c->d_done, err, c->d_pairs,
-               c->d_srch, c->d_srcl, nullptr, nullptr, nullptr, nullptr};
+               c->d_srch, c->d_srcl, nullptr, nullptr, nullptr, nullptr, c->spin_limit};
   // (hi, lo) splits of the two iterates: the context's own buffers, or scratch for caller buffers
   bool convert_old = false;
   const size_t npsi = (size_t)c->M * c->E * c->N;

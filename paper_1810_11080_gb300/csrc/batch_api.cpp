@@ -142,7 +142,7 @@ sn_status sn_batch_create(sn_batch** out, int n_problems, sn_ctx* const* problem
     sn_ctx* c = b->ctx[k];
     SweepArgs base{c->d_facecode, c->d_mixed_off, c->d_mixedB, c->d_mixedB32, c->d_mixedB32lo, c->d_src,
                    nullptr, nullptr, b->d_done + done_off[k], errw, c->d_pairs,
-                   c->d_srch, c->d_srcl, nullptr, nullptr, nullptr, nullptr};
+                   c->d_srch, c->d_srcl, nullptr, nullptr, nullptr, nullptr, c->spin_limit};
     args0[k] = base;
     args0[k].psi_old = c->d_psi[0];
     args0[k].psi_new = c->d_psi[1];

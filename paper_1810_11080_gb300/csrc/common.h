@@ -94,6 +94,7 @@ struct SweepArgs {
   const float* psi_old_l;
   float* psi_new_h;
   float* psi_new_l;
+  long long spin_limit;       // dataflow schedule: polls of one upwind flag before giving up (<= 0: SPIN_LIMIT)
 };
 
 // Per-problem pointers of the fused moment / source kernel in a batch.
@@ -212,6 +213,7 @@ struct sn_ctx {
   int* d_flag = nullptr;
   int* d_done = nullptr;                 // [M][E] dataflow completion flags
   int launch_mode = 0;                   // SN_LAUNCH_LEVELS / SN_LAUNCH_DATAFLOW
+  long long spin_limit = 0;              // dataflow wait limit (0: the kernels' default)
   int blocks_per_sm = 0;                 // dataflow grid: 0 = occupancy limit
   int si_cur = 0;                 // which psi buffer holds the current iterate
   bool si_ready = false;

@@ -87,14 +87,32 @@ __global__ void noalloc_finish_kernel(int nblocks, double* scratch) {
   }
 }
 
-bool on_device(const void* p) {
+// True for managed memory, or device memory that lives on `device` (a buffer on another GPU
+// would be read without peer access by kernels launched on `device`).
+bool on_device(const void* p, int device) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == device);
 }
+
+// Makes `device` current for the lifetime of the guard and gives the calling thread its
+// previous current device back on every return path.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t set(int device) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+    return cudaSetDevice(device);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 // Device address of the scratch array on `device` (which must be current); looked up on the
 // first call for that device.
@@ -125,12 +143,14 @@ extern "C" sn_status sn_moment_noalloc(int device, void* cuda_stream, int n_dir,
   const int64_t blocks = (n + NOALLOC_THREADS - 1) / NOALLOC_THREADS;
   if (blocks > NOALLOC_MAX_BLOCKS) return SN_EINVAL;     // beyond the static scratch
   if (!w || !psi || !phi_out) return SN_EINVAL;
-  if (cudaSetDevice(device) != cudaSuccess) {
+  DeviceGuard guard;
+  if (guard.set(device) != cudaSuccess) {
     cudaGetLastError();
     return SN_ECUDA;
   }
-  if (!on_device(w) || !on_device(psi) || !on_device(phi_out) || (phi_prev && !on_device(phi_prev)))
-    return SN_EINVAL;                                     // device buffers only: nothing is staged
+  if (!on_device(w, device) || !on_device(psi, device) || !on_device(phi_out, device) ||
+      (phi_prev && !on_device(phi_prev, device)))
+    return SN_EINVAL;                                     // buffers of this device only: nothing is staged
   double* scratch = nullptr;
   sn_status st = scratch_for(device, &scratch);
   if (st != SN_OK) return st;

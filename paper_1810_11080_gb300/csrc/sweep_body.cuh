@@ -133,7 +133,7 @@ __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepc
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // ---- dataflow synchronisation
-constexpr long long SPIN_LIMIT = 1LL << 20;     // ~0.1-1 s of polling before giving up
+constexpr long long SPIN_LIMIT = 1LL << 20;     // default: ~0.1-1 s of polling before giving up
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -151,11 +151,12 @@ __device__ __forceinline__ double trace_load(const double* p) {
 }
 
 // Wait until every kept upwind neighbour of (e, d) has published its angular flux.  A wait that
-// exceeds SPIN_LIMIT polls sets *err and gives up (the result is then wrong and the host
-// reports SN_ETIMEOUT); it never traps.
+// exceeds its poll limit (sa.spin_limit, or SPIN_LIMIT when that is <= 0) sets *err and gives up
+// (the result is then wrong and the host reports SN_ETIMEOUT); it never traps.
 template <int DIM>
 __device__ void wait_upwind(const DevProblem& Pb, const SweepArgs& sa, uint32_t code, int64_t e, int d, bool valid) {
   if (!valid) return;
+  const long long limit = sa.spin_limit > 0 ? sa.spin_limit : SPIN_LIMIT;
 #pragma unroll
   for (int f = 0; f < 2 * DIM; ++f) {
     if (face_mode(code, f) == MODE_NONE || face_lagged(code, f)) continue;
@@ -164,7 +165,7 @@ __device__ void wait_upwind(const DevProblem& Pb, const SweepArgs& sa, uint32_t 
     const int* flag = sa.done + (int64_t)d * Pb.E + nb;
     long long spins = 0;
     while (ld_acquire(flag) == 0) {
-      if (++spins > SPIN_LIMIT) {
+      if (++spins > limit) {
         atomicExch(sa.err, 1);
         break;
       }

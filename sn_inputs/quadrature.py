@@ -41,7 +41,10 @@ def level_symmetric(N, dim):
     pts = [(i, j, k) for k in range(1, n + 1) for j in range(1, n + 1) for i in range(1, n + 1)
            if i + j + k == n + 2]
     pw = np.array([table[tuple(sorted(p))] for p in pts], dtype=np.float64)
-    pw = pw / pw.sum()
+    tot = 0.0
+    for x in pw:             # left to right in point order (a fixed summation order)
+        tot = tot + float(x)
+    pw = pw / tot
     base = np.array([[mus[i - 1], mus[j - 1], mus[k - 1]] for (i, j, k) in pts], dtype=np.float64)
     if dim == 3:
         signs = [(sx, sy, sz) for sz in (1, -1) for sy in (1, -1) for sx in (1, -1)]

@@ -208,3 +208,84 @@ def test_reoriented_elements_give_the_same_solution():
         R = Sweeper(D, build_graph(D, "face")).source_iterate(tol=1e-13)
         out.append(np.einsum("emn,en->e", D.M, R["phi"]))     # int_e phi, numbering-independent
     assert np.allclose(out[0], out[1], rtol=1e-11, atol=0)
+
+
+# ---------------------------------------------------------------- 3D (hexahedra)
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_affine_hex_mass_and_streaming_match_closed_form(p):
+    """Affine hexes: M = |J| (M1 x M1 x M1) and S^k = |J| sum_j (J^-1)_jk D_j with D_j the 1D
+    derivative matrix on axis j (tensor products from numpy polynomials, not the oracle)."""
+    A = np.array([[1.1, 0.2, -0.1], [0.05, 0.9, 0.3], [-0.2, 0.1, 1.3]])
+    n = 2
+    prob = si.make_config("3d_twist_q2_p2_s8", n=n, p=p, sn=2)
+    prob.mesh = si.structured_mesh((n, n, n), 2, affine_disp(A, np.array([0.1, -0.2, 0.05])))
+    D = Discretization(prob)
+    L = lagrange_poly_1d(gll_nodes(p))
+    M1 = np.array([[integ01(a * b) for b in L] for a in L])
+    D1 = np.array([[integ01(np.polyder(a) * b) for b in L] for a in L])
+    J = A / n
+    dJ = np.linalg.det(J)
+    Jinv = np.linalg.inv(J)
+    kron3 = lambda z, y, x: np.kron(z, np.kron(y, x))     # node m = i0 + (p+1) i1 + (p+1)^2 i2
+    M_ex = dJ * kron3(M1, M1, M1)
+    d = [kron3(M1, M1, D1), kron3(M1, D1, M1), kron3(D1, M1, M1)]
+    S_ex = [dJ * sum(Jinv[j, k] * d[j] for j in range(3)) for k in range(3)]
+    for e in range(D.E):
+        assert np.allclose(D.M[e], M_ex, atol=1e-14)
+        for k in range(3):
+            assert np.allclose(D.S[e, k], S_ex[k], atol=1e-13)
+
+
+@pytest.mark.parametrize("p,sn,reorient", [(1, 4, None), (2, 2, None), (2, 2, 5), (1, 4, 5)])
+@pytest.mark.parametrize("weighting", ["unity", "face", "siginvface"])
+def test_converged_lagged_si_equals_dense_coupled_solve_on_hexes(p, sn, reorient, weighting):
+    """2x2x2 hexes twisted 60 degrees (cyclic: arcs are lagged), with and without a random
+    renumbering of every element's nodes (orientation codes that swap the face axes)."""
+    prob = si.make_config("3d_twist_q2_p2_s8", n=2, p=p, sn=sn, reorient_seed=reorient)
+    if reorient is not None:
+        assert np.any(prob.mesh.orient >= 4)
+    D = Discretization(prob)
+    G = build_graph(D, weighting)
+    assert len(G["removed"]) > 0
+    R = Sweeper(D, G).source_iterate(tol=1e-13)
+    _, phi_ref = global_solve(D)
+    assert np.abs(R["phi"] - phi_ref).max() <= 1e-10 * np.abs(phi_ref).max()
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_pure_absorber_attenuation_converges_on_twisted_hexes(p):
+    """exp(-sigma_t (x - x_in)/mu) solves the pure-absorber S_N equation on any domain; on the
+    twisted (curved-faced, cyclic) hex meshes the L2 error must fall at order p + 1."""
+    errs = []
+    for n in (2, 4, 8):
+        prob = si.make_config("3d_twist_q2_p2_s8", n=n, p=p, sn=2)
+        prob, exact = attenuation(prob, sigma_t=2.0)
+        D = Discretization(prob)
+        R = Sweeper(D, build_graph(D, "face")).source_iterate(tol=1e-13)
+        e2 = 0.0
+        for d in range(D.M_dirs):
+            psi_q = np.einsum("qm,em->eq", D.B, R["psi"][d])
+            e2 += D.w[d] * _l2(D, psi_q - exact(D.xq, d)) ** 2
+        errs.append(np.sqrt(e2))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders[-1] >= p + 1 - 0.2, (errs, orders)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_reoriented_hexes_give_the_same_solution(p):
+    """Renumbering every element's local nodes by a rotation of the reference cube (orientation
+    codes with the swap bit) must not change the physical solution: a wrong neighbour face-node
+    map or orientation transform fails here."""
+    base = si.make_config("3d_twist_q2_p2_s8", n=3, p=p, sn=2)
+    rot = si.make_config("3d_twist_q2_p2_s8", n=3, p=p, sn=2, reorient_seed=11)
+    assert np.any(rot.mesh.orient >= 4) and np.any(rot.mesh.orient & 3)
+    out = []
+    for prob in (base, rot):
+        prob, _ = attenuation(prob, sigma_t=1.5)
+        prob.sigma_s = 0.5 * prob.sigma_t
+        prob.q = np.ones_like(prob.q)
+        D = Discretization(prob)
+        R = Sweeper(D, build_graph(D, "face")).source_iterate(tol=1e-13)
+        out.append(np.einsum("emn,en->e", D.M, R["phi"]))     # int_e phi, numbering-independent
+    assert np.allclose(out[0], out[1], rtol=1e-11, atol=0)

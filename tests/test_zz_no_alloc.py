@@ -48,3 +48,19 @@ def test_noalloc_moment_rejects_sizes_beyond_its_scratch():
     big_elem = 4194304 // 16 + 1
     st = lib.sn_moment_noalloc(0, None, 4, big_elem, 16, None, None, None, None, None)
     assert st == 1      # SN_EINVAL, before touching any pointer
+
+
+def test_noalloc_moment_rejects_host_buffers_and_keeps_the_current_device():
+    import ctypes
+    import paper_1810_11080_gb300 as g
+    lib = g.lib()
+    before = torch.cuda.current_device()
+    E, N, M = 8, 4, 3
+    w = torch.ones(M, dtype=torch.float64, device="cuda")
+    psi_host = np.ones((M, E, N))
+    out = torch.zeros((E, N), dtype=torch.float64, device="cuda")
+    st = lib.sn_moment_noalloc(0, None, M, E, N, ctypes.c_void_p(w.data_ptr()),
+                               psi_host.ctypes.data_as(ctypes.c_void_p), None,
+                               ctypes.c_void_p(out.data_ptr()), None)
+    assert st == 1      # SN_EINVAL: psi is host memory, nothing is staged
+    assert torch.cuda.current_device() == before
