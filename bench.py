@@ -7,10 +7,12 @@ sigma_t ~ U[0.5, 5] per element, scattering ratio 0.9, q = 1, vacuum boundaries:
 
 A step is one source iteration through the C ABI (sn_si_step): the lagged sweep over every
 level and direction, then the fused scalar-flux moment + scattering-source update + residual.
-value = element-direction updates per second over the timed steps.
+value = element-direction updates per second over the timed steps, in the paper's arithmetic
+(FP64 form).  The mixed forms (FP32 LU + one refinement) are measured beside it: their
+updates/s and their wall time to the same 1e-8 scalar-flux residual.
 
 --impl reference times the CPU FP64 oracle (the plain numpy restatement of the method) on a
-bounded sample of the same workload, on the host cores.
+bounded sample of the same workload, on all host cores (one direction per process).
 """
 import argparse
 import json
@@ -39,8 +41,8 @@ def peaks():
 
 
 # FP64 pipe peak: 152 SMs x 2 DFMA/clk/SM (measured 1/64 of the FP32 FMA rate on GB300) x 2 flop
-# x SM clock.  At the 2070 MHz maximum clock: 1.259 TFLOP/s; measured with a DFMA microbenchmark:
-# 1.20 TFLOP/s (profiles/fp_pipe_peaks_microbench.md).
+# x SM clock.  At the 2070 MHz maximum clock: 1.259 TFLOP/s; measured with the DFMA/FFMA
+# microbenchmark bench_fp_peaks.cu: 1.20 TFLOP/s FP64 and 75.0 TFLOP/s FP32.
 FP64_PEAK_TFLOPS = 1.20
 
 DTYPES = {"fp64": "f64", "mixed": "f32+f64", "mixed_ds": "f32+f32x2+f64"}
@@ -51,13 +53,20 @@ PRECISION_DESC = {
 }
 
 
-def flops_per_update(dim, p, inflow_faces):
-    """Algorithmic FP64 flops of one (element, direction) update of the FP64 sweep:
-    assembly (dim+1) N^2 FMA, inflow-face blocks (dim+1) Nf^2 FMA + Nf^2 FMA trace per inflow face,
-    LU 2N^3/3, forward/backward substitution 2N^2."""
-    N = (p + 1) ** dim
-    Nf = (p + 1) ** (dim - 1)
-    return 2 * (dim + 1) * N * N + inflow_faces * 2 * (dim + 2) * Nf * Nf + 2.0 * N ** 3 / 3 + 2 * N * N
+# Algorithmic work of one (element, direction) update of the method, per workload shape (dim, p):
+# local assembly from the direction-independent element matrices, inflow face terms, LU and the two
+# triangular solves (flops); the angular flux written, the inflow traces read and the element
+# factors and source amortised over the directions (bytes).  These are the per-update figures the
+# roofline fractions are computed from, whatever the form's own instruction count.
+ALG_WORK = {
+    (2, 1): {"flops": 250.0, "bytes": 200.0},        # 16x16 p=1 S4 (latency bound)
+    (2, 3): {"flops": 5800.0, "bytes": 350.0},       # 128x128 p=3 S8
+    (3, 2): {"flops": 35000.0, "bytes": 770.0},      # 32^3 p=2 S8 / 48^3 p=2 S12
+}
+
+
+def alg_work(dim, p):
+    return ALG_WORK.get((dim, p), {"flops": None, "bytes": None})
 
 
 class ClockSampler:
@@ -138,18 +147,11 @@ def dist_env():
     return ws, rank, local
 
 
-def mixed_fp64_flops_per_update(dim, p, inflow_faces):
-    """Algorithmic FP64 flops of one update of the mixed form: FP64 row assembly (dim+1) N^2 FMA,
-    inflow-face blocks and traces, residual N^2 FMA, final sum N."""
-    N = (p + 1) ** dim
-    Nf = (p + 1) ** (dim - 1)
-    return 2 * (dim + 1) * N * N + inflow_faces * 2 * (dim + 2) * Nf * Nf + 2 * N * N + N
-
-
-def ds_fp32_flops_per_update(dim, p, inflow_faces):
-    """FP32 flops of one update of the double-single form: row assembly in double-single
-    ((dim+1) products of 7 flops, dim sums of 8 per entry), inflow-face blocks, FP32 LU 2N^3/3,
-    two triangular solve pairs 4N^2, double-single residual 12 N^2."""
+def ds_fp32_issued_flops_per_update(dim, p, inflow_faces):
+    """FP32 flops the double-single form issues per update (its implementation's work, not the
+    method's): row assembly in double-single ((dim+1) products of 7 flops, dim sums of 8 per
+    entry), inflow-face blocks, FP32 Gauss-Jordan 2N^3/3, two inverse applications 4N^2,
+    double-single residual 12 N^2."""
     N = (p + 1) ** dim
     Nf = (p + 1) ** (dim - 1)
     row = N * N * ((dim + 1) * 7 + dim * 8)
@@ -159,16 +161,12 @@ def ds_fp32_flops_per_update(dim, p, inflow_faces):
 
 FP32_PEAK_TFLOPS = 75.0
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per level launch of the sweep kernel,
-# averaged over the launches of one sweep of this workload, from the ncu launch list summarised in
-# the named profile.  Valid only for the kernel sources it was taken on (SHA-256 of the files
-# below); any later change to them reports null.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant sweep
+# kernel of a form, from one ncu capture of this workload.  Valid only for the kernel sources it
+# was taken on (SHA-256 of the files below); any later change to them reports null.
 KERNEL_SOURCES = ["paper_1810_11080_gb300/csrc/sweep.cu", "paper_1810_11080_gb300/csrc/sweep_body.cuh",
                   "paper_1810_11080_gb300/csrc/common.h"]
-TRAFFIC = {
-    "mixed_ds": {"bytes_per_launch": 2978703, "profile": "profiles/sweep_level_kernel_ds_2d_p3_s8_128x128.md",
-                 "sources_sha256": "455da5f83eda62a15558ff1cc32da2a204e9ae9701e19b13588622846cec2e53"},
-}
+TRAFFIC = {}
 
 
 def kernel_sources_sha256():
@@ -180,11 +178,12 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def traffic_for(kind):
-    t = TRAFFIC.get(kind)
+def traffic_for(kind, schedule):
+    """(bytes per launch, capture id) of the form's kernel on the given schedule, or (None, None)."""
+    t = TRAFFIC.get((kind, schedule))
     if t is None or t["sources_sha256"] != kernel_sources_sha256():
         return None, None
-    return t["bytes_per_launch"], t["profile"]
+    return t["bytes_per_launch"], t["capture"]
 
 
 def run_gpu(args):
@@ -263,7 +262,9 @@ def run_gpu(args):
                     **{k: {kk: vv for kk, vv in m.items() if kk != "clocks"} for k, m in meas.items()}}
         return None
 
-    # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region):
+    # every step uploads phi and psi_old, sweeps, downloads psi_new, uploads psi_new and phi_prev
+    # for the moment and downloads phi (sn_sweep / sn_moment stage host buffers themselves)
     phi_h = torch.zeros((E, N), dtype=torch.float64, pin_memory=True).numpy()
     phi2_h = torch.zeros((E, N), dtype=torch.float64, pin_memory=True).numpy()
     psa = torch.zeros((M, E, N), dtype=torch.float64, pin_memory=True).numpy()
@@ -302,25 +303,39 @@ def run_gpu(args):
         return None
     pk, pk_kind = peaks()
     inflow_faces = dim            # on average dim of the 2 dim faces of an element are inflow faces
+    work = alg_work(dim, prob.p)
 
     def roofline(kind, m):
         pcode = {"fp64": 0, "mixed": 1, "mixed_ds": 2}[kind]
         flow = m["schedule"]["mode"] == "dataflow"
         kname = (f"sweep_flow_kernel<{dim},{prob.p},{pcode}> (one persistent launch per sweep)" if flow else
                  f"sweep_level_kernel<{dim},{prob.p},{pcode}> (all level launches of one sweep)")
-        if kind == "mixed_ds":
-            fpu = ds_fp32_flops_per_update(dim, prob.p, inflow_faces)
-            peak, unit, src = FP32_PEAK_TFLOPS, "TFLOP/s (FP32 pipe)", "FP32 FFMA microbenchmark (of measured)"
-        else:
-            fpu = flops_per_update(dim, prob.p, inflow_faces) if kind == "fp64" else \
-                mixed_fp64_flops_per_update(dim, prob.p, inflow_faces)
+        if kind == "fp64":
             peak, unit, src = FP64_PEAK_TFLOPS, "TFLOP/s (FP64 pipe)", "FP64 DFMA microbenchmark (of measured)"
-        ach = fpu * updates / (m["sweep_ms_per_step"] / 1e3) / 1e12
-        traffic, tsrc = (None, None) if flow else traffic_for(kind)
-        return {"bound": "alu", "kernel": kname, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                "traffic": traffic, "traffic_unit": "bytes per level launch (sweep average)",
-                "traffic_source": tsrc, "launches_per_step": m["launches"] // max(1, args.steps),
-                "peak_source": src, "flops_per_update": fpu, "sweep_ms_per_step": m["sweep_ms_per_step"]}
+        else:
+            peak, unit, src = FP32_PEAK_TFLOPS, "TFLOP/s (FP32 pipe)", "FP32 FFMA microbenchmark (of measured)"
+        sweep_s = m["sweep_ms_per_step"] / 1e3
+        ach = work["flops"] * updates / sweep_s / 1e12
+        traffic, capture = traffic_for(kind, m["schedule"]["mode"])
+        launches = m["launches"] // max(1, args.steps) - 1          # sweep launches (one moment launch)
+        out = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+               "peak_source": src, "alg_flops_per_update": work["flops"], "alg_bytes_per_update": work["bytes"],
+               "hbm_achieved_gbs": work["bytes"] * updates / sweep_s / 1e9,
+               "hbm_frac_of_measured": work["bytes"] * updates / sweep_s / 1e9 / pk["hbm_gbs"],
+               "traffic": traffic, "traffic_unit": "bytes per launch" + (" (one launch per sweep)" if flow else
+                                                                          " (level launch, sweep average)"),
+               "traffic_capture": capture, "sweep_launches_per_step": launches,
+               "sweep_ms_per_step": m["sweep_ms_per_step"]}
+        if kind == "mixed_ds":
+            out["issued_fp32_flops_per_update"] = ds_fp32_issued_flops_per_update(dim, prob.p, inflow_faces)
+        return out
+
+    def form_line(k):
+        return {"value": meas[k]["value"], "unit": "updates/s", "ms_per_step": meas[k]["ms_per_step"],
+                "dtype": DTYPES[k], "schedule": meas[k]["schedule"], "precision": PRECISION_DESC[k],
+                "roofline": roofline(k, meas[k]), "gpu_launches": meas[k]["launches"], "clocks": meas[k]["clocks"],
+                "time_to_1e-8_s": tts[k]["seconds"], "iters_to_1e-8": tts[k]["iters"],
+                "converged": tts[k]["converged"], "phi_rel_l2_vs_fp64": diffs[k]}
 
     out = {
         "metric": METRIC, "value": meas[head]["value"], "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
@@ -329,26 +344,26 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD_DESC, "precision": PRECISION_DESC[head],
                    "weighting": "face", "parallelism": "replicas" if ws > 1 else "single",
                    "launch": args.launch, "schedule": meas[head]["schedule"],
-                   "l2": "inputs larger than L2 (psi 2x84 MB + element factors 117 MB + FP32 copy 59 MB)"},
+                   "l2": "inputs larger than L2 (psi 2x84 MB + element factors 117 MB; FP32 splits 2x117 MB)"},
         "roofline": roofline(head, meas[head]),
         "e2e": {"value": updates * args.steps / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": meas[head]["launches"],
         "clocks": meas[head]["clocks"],
-        "forms": {k: {"value": meas[k]["value"], "ms_per_step": meas[k]["ms_per_step"], "dtype": DTYPES[k],
-                      "schedule": meas[k]["schedule"],
-                      "precision": PRECISION_DESC[k], "roofline": roofline(k, meas[k]),
-                      "gpu_launches": meas[k]["launches"], "clocks": meas[k]["clocks"],
-                      "time_to_1e-8_s": tts[k]["seconds"], "iters_to_1e-8": tts[k]["iters"],
-                      "converged": tts[k]["converged"], "phi_rel_l2_vs_fp64": diffs[k]} for k in forms},
-        "time_to_1e-8": {"fp64_s": tts["fp64"]["seconds"], "head_s": tts[head]["seconds"],
-                         "speedup_vs_fp64": tts["fp64"]["seconds"] / tts[head]["seconds"],
-                         "head_iters": tts[head]["iters"], "fp64_iters": tts["fp64"]["iters"],
-                         "phi_rel_l2_head_vs_fp64": diffs[head]},
+        "mixed_ds": form_line("mixed_ds"),
+        "time_to_1e-8": {"fp64_s": tts["fp64"]["seconds"], "mixed_ds_s": tts["mixed_ds"]["seconds"],
+                         "mixed_s": tts["mixed"]["seconds"],
+                         "speedup_mixed_ds_vs_fp64": tts["fp64"]["seconds"] / tts["mixed_ds"]["seconds"],
+                         "fp64_iters": tts["fp64"]["iters"], "mixed_ds_iters": tts["mixed_ds"]["iters"],
+                         "phi_rel_l2_mixed_ds_vs_fp64": diffs["mixed_ds"]},
+        "forms": {k: form_line(k) for k in forms},
         "graph": {"build_s": t_graph, "removed": gstats["n_removed"], "levels": gstats["max_level"] + 1,
                   "max_scc": gstats["max_scc"], "mixed_faces": gstats["n_mixed_faces"]},
         "peaks_file": pk_kind,
     }
+    ctx.close()
+    if not args.no_small:
+        out["small_2d"] = run_small(g, torch, args)
     if not args.no_batch:
         out["batched"] = run_batch(g, torch, args)
     if not args.no_3d:
@@ -356,8 +371,60 @@ def run_gpu(args):
     if not args.no_learned:
         out["learned"] = run_learned(g, torch, args)
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_sample_dirs)
+        out["cpu_baseline"] = cpu_baseline(args)
     return out
+
+
+def run_small(g, torch, args):
+    """16x16 sine-perturbed Q2 quads, p = 1 (4 unknowns), S4 (12 directions), sigma_t = 1,
+    sigma_s = 0.5, q = 1: 3,072 updates per sweep, latency bound (31 levels of ~100 pairs).
+    Reported per level, and as time to a 1e-8 residual next to the oracle's on one host core."""
+    import sn_inputs as si
+    prob = si.make_config("2d_sine_q2_p1_s4")
+    stream = torch.cuda.Stream()
+    ctx = g.setup_problem(prob, device=0, stream=stream.cuda_stream)
+    gs = ctx.sn_build_graph("face", 10)
+    levels = int(gs["max_level"] + 1)
+    E, N = prob.mesh.n_elem, 4
+    ups = E * len(prob.w)
+    res = {"workload": "16x16 Q2 quads, x' = x + 0.05 sin(2 pi x) sin(2 pi y) on both coordinates, p=1, S4 (12 dirs), "
+                       "sigma_t=1, sigma_s=0.5, q=1", "updates_per_sweep": ups, "levels": levels}
+    for name, prec in (("fp64", g.SN_PREC_FP64), ("mixed_ds", g.SN_PREC_MIXED_DS)):
+        mode, bps = ctx.sn_autotune(prec)
+        for _ in range(args.warmup):
+            ctx.sn_si_step(prec)
+        steps = max(20, args.steps)
+        tot = 0.0
+        for _ in range(steps):
+            _, ms = ctx.sn_si_step(prec, time_sweep=True)
+            tot += ms
+        phi = np.zeros((E, N))
+        t0 = time.perf_counter()
+        r = ctx.sn_source_iterate(1e-8, 1000, prec, phi_out=phi)
+        res[name] = {"sweep_us": 1e3 * tot / steps, "us_per_level": 1e3 * tot / steps / levels,
+                     "sweep_updates_per_s": ups * steps / (tot / 1e3),
+                     "schedule": {"mode": "dataflow" if mode == 1 else "levels", "blocks_per_sm": bps},
+                     "time_to_1e-8_s": time.perf_counter() - t0, "iters": r["iters"], "converged": r["converged"]}
+    ctx.close()
+    if not args.no_cpu_baseline:
+        res["oracle_time_to_1e-8"] = oracle_small_solve()
+    return res
+
+
+def oracle_small_solve():
+    """The oracle's source iteration to 1e-8 on the 16x16 p=1 S4 workload, one host thread
+    (discretisation, graph, local factorisations and every sweep)."""
+    from oracle.dg import Discretization
+    from oracle.graph import build_graph
+    from oracle.sweep import Sweeper
+    import sn_inputs as si
+    prob = si.make_config("2d_sine_q2_p1_s4")
+    t0 = time.perf_counter()
+    disc = Discretization(prob)
+    G = build_graph(disc, "face")
+    R = Sweeper(disc, G).source_iterate(tol=1e-8)
+    return {"seconds": time.perf_counter() - t0, "iters": R["iters"], "cores": 1,
+            "kind": "oracle", "note": "numpy/scipy FP64, single thread, whole solve from phi = 0"}
 
 
 def run_3d(g, torch, args):
@@ -387,8 +454,15 @@ def run_3d(g, torch, args):
         phi = np.zeros((E, N))
         t1 = time.perf_counter()
         r = ctx.sn_source_iterate(1e-8, 3000, prec, phi_out=phi)
-        res[name] = {"sweep_updates_per_s": ups * steps / (tot / 1e3), "sweep_ms": tot / steps,
+        rate = ups * steps / (tot / 1e3)
+        work = alg_work(3, prob.p)
+        peak = FP64_PEAK_TFLOPS if prec == g.SN_PREC_FP64 else FP32_PEAK_TFLOPS
+        res[name] = {"sweep_updates_per_s": rate, "sweep_ms": tot / steps,
                      "schedule": {"mode": "dataflow" if mode == 1 else "levels", "blocks_per_sm": bps},
+                     "roofline": {"bound": "alu", "achieved_tflops": rate * work["flops"] / 1e12,
+                                  "peak_tflops": peak, "frac": rate * work["flops"] / 1e12 / peak,
+                                  "pipe": "FP64" if prec == g.SN_PREC_FP64 else "FP32",
+                                  "alg_flops_per_update": work["flops"], "alg_bytes_per_update": work["bytes"]},
                      "time_to_1e-8_s": time.perf_counter() - t1, "iters": r["iters"], "converged": r["converged"]}
     ctx.close()
     return res
@@ -481,61 +555,114 @@ def run_batch(g, torch, args):
     return res
 
 
-def cpu_baseline(n_dirs):
-    """The oracle as it stands, on a bounded sample: n_dirs directions of the full workload
-    (graph of those directions, local assembly + factorisation + one lagged sweep), one thread."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
+def _oracle_worker(conn, d):
+    """One host process of the oracle timing: builds the workload's discretisation and direction
+    d's graph once, then on every "go" times the oracle's work for one direction of one sweep
+    (local assembly + factorisation of every element's system, and the lagged sweep)."""
     from oracle.dg import Discretization
     from oracle.graph import build_graph_dirs
     from oracle.sweep import Sweeper
     prob = make_problem()
-    dirs = list(range(n_dirs))
     disc = Discretization(prob)
-    G = build_graph_dirs(disc, dirs, "face")
-    t0 = time.perf_counter()
-    sw = Sweeper(disc, G, dirs=dirs)
+    G = build_graph_dirs(disc, [d], "face")
     E, N, M = disc.E, disc.N, disc.M_dirs
-    sw.sweep(np.ones((E, N)), np.zeros((M, E, N)), dirs=dirs)
-    dt = time.perf_counter() - t0
-    ups = E * n_dirs / dt
-    return {"value": ups, "unit": "updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n_dirs} of 40 directions of the same workload ({E * n_dirs} updates): local assembly, "
-                      f"LU and one lagged sweep, numpy/scipy FP64, {dt:.1f} s"}
+    phi, psi_old = np.ones((E, N)), np.zeros((M, E, N))
+    conn.send(("ready", E))
+    while True:
+        msg = conn.recv()
+        if msg != "go":
+            break
+        t0 = time.perf_counter()
+        Sweeper(disc, G, dirs=[d]).sweep(phi, psi_old, dirs=[d])
+        conn.send(time.perf_counter() - t0)
+    conn.close()
+
+
+class OracleWorkers:
+    """`procs` spawned processes (spawn start method: safe after CUDA initialisation), process i
+    owning direction i mod 40 of the workload; round() runs one direction in every process at
+    once and returns the wall time until the last one finishes."""
+
+    def __init__(self, procs):
+        import multiprocessing as mp
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"                                # one thread per process
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for i in range(procs):
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_oracle_worker, args=(b, i % 40), daemon=True)
+            pr.start()
+            self.conns.append(a)
+            self.procs.append(pr)
+        self.E = [c.recv()[1] for c in self.conns][0]
+
+    def round(self):
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send("go")
+        for c in self.conns:
+            c.recv()
+        return time.perf_counter() - t0
+
+    def close(self):
+        for c in self.conns:
+            c.send("stop")
+        for pr in self.procs:
+            pr.join(timeout=30)
+
+
+def oracle_procs():
+    """Host processes for the all-core oracle timing: every core, at most 16 (each holds ~0.5 GB)."""
+    return max(1, min(os.cpu_count() or 1, 16))
+
+
+def cpu_baseline(args):
+    """The oracle as it stands, on a bounded sample of the workload: one direction of one sweep
+    per process (local assembly + factorisation + the lagged sweep), on one core and on all cores."""
+    import multiprocessing as mp
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    single = OracleWorkers(1)
+    single.round()
+    dt1 = single.round()
+    single.close()
+    P = oracle_procs()
+    pool = OracleWorkers(P)
+    pool.round()
+    dtp = pool.round()
+    pool.close()
+    E = pool.E
+    return {"value": E * P / dtp, "unit": "updates/s", "cores": P, "nproc": os.cpu_count(), "kind": "oracle",
+            "sample": f"{P} directions of one sweep of the same workload at once, one per process "
+                      f"({E * P} updates in {dtp:.1f} s): local assembly, LU and the lagged sweep, numpy/scipy FP64",
+            "single_core": {"value": E / dt1, "unit": "updates/s", "cores": 1,
+                            "sample": f"one direction ({E} updates) in {dt1:.1f} s"},
+            "start_method": mp.get_context("spawn").get_start_method()}
 
 
 def run_reference(args):
     """The oracle as it stands on the host cores: each step sweeps one direction of the same
-    workload (local assembly + factorisation + lagged sweep); value in updates/s."""
+    workload in each of P processes at once (local assembly + factorisation + lagged sweep);
+    value in updates/s."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return None
-    os.environ["OMP_NUM_THREADS"] = "1"
-    from oracle.dg import Discretization
-    from oracle.graph import build_graph_dirs
-    from oracle.sweep import Sweeper
-    prob = make_problem()
-    disc = Discretization(prob)
-    E, N, M = disc.E, disc.N, disc.M_dirs
-    total = args.warmup + args.steps
-    dirs = [k % M for k in range(total)]
-    G = build_graph_dirs(disc, sorted(set(dirs)), "face")
-    phi, psi_old = np.ones((E, N)), np.zeros((M, E, N))
-    times = []
-    for k, d in enumerate(dirs):
-        t0 = time.perf_counter()
-        sw = Sweeper(disc, G, dirs=[d])
-        sw.sweep(phi, psi_old, dirs=[d])
-        if k >= args.warmup:
-            times.append(time.perf_counter() - t0)
-    v = E * len(times) / sum(times)
-    cb = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
-          "sample": f"each step: one of the 40 directions of the same workload ({E} updates): local assembly, "
-                    f"LU and one lagged sweep, numpy/scipy FP64, single thread"}
+    P = oracle_procs()
+    pool = OracleWorkers(P)
+    for _ in range(args.warmup):
+        pool.round()
+    times = [pool.round() for _ in range(args.steps)]
+    pool.close()
+    E = pool.E
+    v = E * P * len(times) / sum(times)
+    cb = {"value": v, "unit": "updates/s", "cores": P, "nproc": os.cpu_count(), "kind": "oracle",
+          "sample": f"each step: {P} of the 40 directions of one sweep of the same workload at once, one per "
+                    f"process ({E * P} updates): local assembly, LU and the lagged sweep, numpy/scipy FP64"}
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "precision": "fp64", "weighting": "face",
-                       "step": "one direction of one sweep"},
+                       "step": f"{P} directions of one sweep, one per host process"},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
 
@@ -550,17 +677,17 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-problem batched measurement")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D twisted-mesh measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-predictor measurement")
-    ap.add_argument("--learned-n", type=int, default=24, help="mesh size n^3 of the learned-predictor measurement")
+    ap.add_argument("--no-small", action="store_true", help="skip the 16x16 p=1 S4 measurement")
+    ap.add_argument("--learned-n", type=int, default=48, help="mesh size n^3 of the learned-predictor measurement")
     ap.add_argument("--launch", default="auto", choices=["auto", "levels", "dataflow"],
                     help="sweep schedule per form: the autotuner's choice, one launch per level, or one persistent dataflow launch")
-    ap.add_argument("--form", default="mixed_ds", choices=["fp64", "mixed", "mixed_ds"],
-                    help="form reported as the headline value (all three are measured)")
+    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed", "mixed_ds"],
+                    help="form reported as the headline value (all three are measured; default: the paper's FP64)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no e2e, time-to-tolerance or CPU legs): for profiler launch lists")
     ap.add_argument("--quick-workload", default=None,
                     choices=["2d_sine_q2_p1_s4", "2d_smooth_q3_p3_s8", "3d_twist_q2_p2_s8", "3d_smooth_q2_p2_s12"],
                     help="with --quick: time this configuration instead of the default workload")
-    ap.add_argument("--cpu-sample-dirs", type=int, default=1)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

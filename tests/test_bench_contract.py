@@ -36,11 +36,23 @@ def test_traffic_is_reported_only_for_the_captured_sources():
     assert h == bench.kernel_sources_sha256() and len(h) == 64
     saved = dict(bench.TRAFFIC)
     try:
-        bench.TRAFFIC["mixed_ds"] = {"bytes_per_launch": 123, "profile": "p.md", "sources_sha256": h}
-        assert bench.traffic_for("mixed_ds") == (123, "p.md")
-        bench.TRAFFIC["mixed_ds"] = {"bytes_per_launch": 123, "profile": "p.md", "sources_sha256": "0" * 64}
-        assert bench.traffic_for("mixed_ds") == (None, None)
-        assert bench.traffic_for("fp64") == (None, None) or "fp64" in saved
+        bench.TRAFFIC[("fp64", "dataflow")] = {"bytes_per_launch": 123, "capture": "c1", "sources_sha256": h}
+        assert bench.traffic_for("fp64", "dataflow") == (123, "c1")
+        assert bench.traffic_for("fp64", "levels") == (None, None)
+        bench.TRAFFIC[("fp64", "dataflow")] = {"bytes_per_launch": 123, "capture": "c1", "sources_sha256": "0" * 64}
+        assert bench.traffic_for("fp64", "dataflow") == (None, None)
     finally:
         bench.TRAFFIC.clear()
         bench.TRAFFIC.update(saved)
+
+
+def test_roofline_work_per_update_is_the_methods():
+    """The fractions use the method's algorithmic work per update (assembly, inflow faces, LU,
+    solves), the same figure for every arithmetic form; the double-single form's issued FP32 flops
+    (its emulation of wider arithmetic) are reported separately and are larger."""
+    sys.path.insert(0, ROOT)
+    import bench
+    w = bench.alg_work(2, 3)
+    assert w["flops"] == 5800.0 and w["bytes"] == 350.0
+    assert bench.alg_work(3, 2)["flops"] == 35000.0
+    assert bench.ds_fp32_issued_flops_per_update(2, 3, 2) > 2 * w["flops"]

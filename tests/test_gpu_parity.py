@@ -85,7 +85,7 @@ def test_mixed_sweep_with_direction_sources_and_inflow(p, prec):
     ref = Sweeper(disc, G).sweep(phi, psi_old)
     out = np.zeros_like(psi_old)
     ctx.sn_sweep(phi, psi_old, out, prec)
-    assert rel_l2(out, ref) <= MIXED_TOL
+    check_mixed(out, ref, f"mixed(prec={prec}) MMS p={p}")
 
 
 def test_fp64_sweep_device_pointers_match_host_pointers():
@@ -131,7 +131,23 @@ def test_moment_and_residual_match_numpy():
     assert abs(r - np.abs(ref - phi_prev).max() / np.abs(ref).max()) <= 1e-14
 
 
-MIXED_TOL = 1e-8     # single mixed sweep vs the FP64 oracle (FP32 LU + one FP64-residual refinement)
+# Mixed forms vs the FP64 oracle.  One sweep: measured relative L2 1.9e-14 .. 1.4e-13 on the cases
+# below (both mixed forms), so 1e-11 leaves two orders of magnitude of margin; element-wise the
+# error is bounded relative to each value (plus a floor at 1e-12 of the largest value, for values
+# near zero).  Converged scalar flux after the same number of iterations: measured ~1e-12.
+MIXED_TOL = 1e-11
+MIXED_ELEM_RTOL, MIXED_ELEM_ATOL = 1e-10, 1e-12
+MIXED_SI_TOL = 1e-10
+
+
+def check_mixed(out, ref, what):
+    err = rel_l2(out, ref)
+    scale = np.abs(ref).max()
+    elem = np.abs(out - ref) / (np.abs(ref) + MIXED_ELEM_ATOL / MIXED_ELEM_RTOL * scale)
+    print(f"{what}: rel L2 {err:.3e}, max |diff|/max|ref| {np.abs(out - ref).max() / scale:.3e}, "
+          f"element-wise {elem.max():.3e} (of {MIXED_ELEM_RTOL:.0e})")
+    assert err <= MIXED_TOL, (what, err)
+    assert np.all(np.abs(out - ref) <= MIXED_ELEM_RTOL * np.abs(ref) + MIXED_ELEM_ATOL * scale), (what, elem.max())
 
 
 @pytest.mark.parametrize("prec", [1, 2])
@@ -145,9 +161,7 @@ def test_mixed_sweep_accuracy(case, prec):
     ref = Sweeper(disc, G).sweep(phi, psi_old)
     out = np.zeros_like(psi_old)
     ctx.sn_sweep(phi, psi_old, out, prec)
-    err = rel_l2(out, ref)
-    print(f"mixed(prec={prec}) single-sweep rel L2 {case}: {err:.3e}")
-    assert err <= MIXED_TOL, err
+    check_mixed(out, ref, f"mixed(prec={prec}) single sweep {case}")
 
 
 @pytest.mark.parametrize("prec", [1, 2])
@@ -161,9 +175,18 @@ def test_mixed_source_iteration_reaches_same_tolerance(case, prec):
     phi = np.zeros((E, N))
     res = ctx.sn_source_iterate(1e-8, 500, prec, phi_out=phi)
     assert res["converged"]
-    err = rel_l2(phi, ref["phi"])
-    print(f"mixed(prec={prec}) converged phi rel L2 {case}: {err:.3e} iters {res['iters']}")
-    assert err <= 1e-7
+    # same number of iterations as the oracle at the same tolerance: the difference is then the
+    # arithmetic's alone, not the iteration error
+    ref8 = Sweeper(disc, G).source_iterate(tol=1e-8)
+    assert abs(res["iters"] - ref8["iters"]) <= 1
+    phi_k = np.zeros((E, N))
+    res_k = ctx.sn_source_iterate(1e-300, ref8["iters"], prec, phi_out=phi_k)
+    assert res_k["iters"] == ref8["iters"]
+    err = rel_l2(phi_k, ref8["phi"])
+    print(f"mixed(prec={prec}) phi after {ref8['iters']} iterations, rel L2 vs oracle {case}: {err:.3e}; "
+          f"converged vs oracle fixed point {rel_l2(phi, ref['phi']):.3e}")
+    assert err <= MIXED_SI_TOL
+    assert rel_l2(phi, ref["phi"]) <= 1e-6          # 1e-8 residual: the iteration error dominates
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
@@ -197,3 +220,55 @@ def test_dataflow_source_iteration(prec):
     res = ctx.sn_source_iterate(1e-10, 500, prec, phi_out=phi)
     assert res["converged"]
     assert rel_l2(phi, ref["phi"]) <= 1e-9
+
+
+# ---------------------------------------------------------------- benchmark-size cases
+# The full 2D workload (128 x 128 Q3 quads, p = 3, S8: ~2,570 pairs per wavefront level) and a
+# 3D 8^3 twisted mesh (p = 2, S8): the GPU sweeps every direction, the oracle a sample of them
+# (one sweep of one direction only depends on that direction's graph and data).
+
+@pytest.fixture(scope="module")
+def bench_2d():
+    from oracle.dg import Discretization
+    from oracle.graph import build_graph_dirs
+    prob = si.make_config("2d_smooth_q3_p3_s8")
+    dirs = [0, 17, 38]
+    disc = Discretization(prob)
+    G = build_graph_dirs(disc, dirs, "face")
+    phi, psi_old = random_state(prob, seed=21)
+    ref = Sweeper(disc, G, dirs=dirs).sweep(phi, psi_old, dirs=dirs)
+    ctx, _ = gpu_ctx(prob, "face")
+    return prob, dirs, phi, psi_old, ref, ctx
+
+
+@pytest.fixture(scope="module")
+def bench_3d():
+    from oracle.dg import Discretization
+    from oracle.graph import build_graph_dirs
+    prob = si.make_config("3d_twist_q2_p2_s8", n=8)
+    dirs = [0, 13, 27, 41, 55, 69, 79]
+    disc = Discretization(prob)
+    G = build_graph_dirs(disc, dirs, "face")
+    phi, psi_old = random_state(prob, seed=22)
+    ref = Sweeper(disc, G, dirs=dirs).sweep(phi, psi_old, dirs=dirs)
+    ctx, _ = gpu_ctx(prob, "face")
+    return prob, dirs, phi, psi_old, ref, ctx
+
+
+@pytest.mark.parametrize("launch", ["levels", "dataflow"])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("shape", ["bench_2d", "bench_3d"])
+def test_benchmark_size_sweep_parity(shape, prec, launch, request):
+    import paper_1810_11080_gb300 as g
+    prob, dirs, phi, psi_old, ref, ctx = request.getfixturevalue(shape)
+    ctx.sn_set_launch(g.SN_LAUNCH_DATAFLOW if launch == "dataflow" else g.SN_LAUNCH_LEVELS, 0)
+    out = np.full_like(psi_old, np.nan)
+    ctx.sn_sweep(phi, psi_old, out, prec)
+    assert np.all(np.isfinite(out))
+    o, r = out[dirs], ref[dirs]
+    if prec == 0:
+        err = rel_l2(o, r)
+        print(f"{shape} fp64 {launch}: rel L2 {err:.3e}")
+        assert err <= FP64_TOL, err
+    else:
+        check_mixed(o, r, f"{shape} prec={prec} {launch}")
