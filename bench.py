@@ -166,7 +166,15 @@ FP32_PEAK_TFLOPS = 75.0
 # was taken on (SHA-256 of the files below); any later change to them reports null.
 KERNEL_SOURCES = ["paper_1810_11080_gb300/csrc/sweep.cu", "paper_1810_11080_gb300/csrc/sweep_body.cuh",
                   "paper_1810_11080_gb300/csrc/common.h"]
-TRAFFIC = {}
+TRAFFIC = {
+    # one launch = one sweep: the whole launch captured (350.3 MB read + 154.6 MB written)
+    ("fp64", "dataflow"): {"bytes_per_launch": 504885760, "capture": "ncu --set full, sweep_flow_kernel<2,3,0>, "
+                           "first timed launch", "sources_sha256": "19dfca2fad2059fa3bd974b94c9b5c6306f594fa3f737cc9f4077892309646d1"},
+    # three mid-sweep level launches (5,000-5,080 pairs, 5.69-5.72 MB read, cold caches), scaled to the
+    # sweep's average level of 2,570 pairs at the captured 1,124 bytes per pair
+    ("mixed_ds", "levels"): {"bytes_per_launch": 2888000, "capture": "ncu --set full, sweep_level_kernel<2,3,2>, "
+                             "levels 128-130 scaled per pair", "sources_sha256": "19dfca2fad2059fa3bd974b94c9b5c6306f594fa3f737cc9f4077892309646d1"},
+}
 
 
 def kernel_sources_sha256():
@@ -253,14 +261,16 @@ def run_gpu(args):
                           sched["blocks_per_sm"])
 
     forms = {"fp64": g.SN_PREC_FP64, "mixed": g.SN_PREC_MIXED, "mixed_ds": g.SN_PREC_MIXED_DS}
+    if args.quick and args.quick_forms:
+        forms = {k: forms[k] for k in args.quick_forms.split(",")}
     meas = {k: timed_steps(v) for k, v in forms.items()}
-    head = args.form
-    hp = forms[head]
     if args.quick:
         if rank == 0:
             return {"metric": METRIC, "quick": True, "workload": args.quick_workload or WORKLOAD,
                     **{k: {kk: vv for kk, vv in m.items() if kk != "clocks"} for k, m in meas.items()}}
         return None
+    head = args.form
+    hp = forms[head]
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region):
     # every step uploads phi and psi_old, sweeps, downloads psi_new, uploads psi_new and phi_prev
@@ -685,6 +695,8 @@ def main():
                     help="form reported as the headline value (all three are measured; default: the paper's FP64)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no e2e, time-to-tolerance or CPU legs): for profiler launch lists")
+    ap.add_argument("--quick-forms", default=None,
+                    help="with --quick: comma-separated forms to time (fp64, mixed, mixed_ds; default all)")
     ap.add_argument("--quick-workload", default=None,
                     choices=["2d_sine_q2_p1_s4", "2d_smooth_q3_p3_s8", "3d_twist_q2_p2_s8", "3d_smooth_q2_p2_s12"],
                     help="with --quick: time this configuration instead of the default workload")
