@@ -20,8 +20,10 @@ Readings (the paper is garbled or silent here):
    volume: tensor GL with n_v = p + ceil(dim r / 2) points per axis (exact for the mass and
    streaming integrands with element-constant sigma).  Faces: n_f = p + r GL points per axis.
    2D faces are split at the real roots of Omega.n(s) in (0,1) (a polynomial of degree
-   r - 1 <= 2), so each piece's integrand is a polynomial and the rule is exact.  3D faces use
-   a composite K x K rule (K = face_subdiv) of n_f x n_f GL points per sub-square.
+   r - 1 <= 2), so each piece's integrand is a polynomial and the rule is exact.  3D faces are
+   split where the kink curve Omega.n = 0 crosses the face edges (outer coordinate) and at the
+   roots of Omega.n along every outer quadrature line (inner coordinate), on top of a K x K
+   composite rule (K = face_subdiv), n_f GL points per piece and axis (face_rule_3d).
  * A face shared by e and e' is owned by min(e, e'): its points and normal are computed
    from the owner's control points; the other side uses the negated normal at the same
    points, mapped to its own face coordinates by the orientation code.
@@ -95,6 +97,96 @@ def face_basis(gll, dim, t0, t1):
     return out
 
 
+BISECT_STEPS = 60     # fixed bisection count of the root isolation (interval width 2^-60)
+
+
+def poly_from_samples(vals):
+    """Monomial coefficients c[0..D] (list of arrays) of the degree-D polynomial through the
+    points (k/D, vals[..., k]), k = 0..D.  Newton divided differences, updated in place for
+    j = 1..D and k = D down to j: a_k = (a_k - a_{k-1}) / (x_k - x_{k-j}); the Newton form is then
+    expanded by nested multiplication for k = D-1 down to 0: c <- c (x - x_k) + a_k, i.e.
+    new_0 = a_k - x_k c_0, new_i = c_{i-1} - x_k c_i, new_m = c_{m-1} (m = current length)."""
+    D = vals.shape[-1] - 1
+    x = [float(k) / float(D) for k in range(D + 1)]
+    a = [vals[..., k].copy() for k in range(D + 1)]
+    for j in range(1, D + 1):
+        for k in range(D, j - 1, -1):
+            a[k] = (a[k] - a[k - 1]) / (x[k] - x[k - j])
+    c = [a[D]]
+    for k in range(D - 1, -1, -1):
+        m = len(c)
+        new = [a[k] - x[k] * c[0]]
+        for i in range(1, m):
+            new.append(c[i - 1] - x[k] * c[i])
+        new.append(c[m - 1])
+        c = new
+    return c
+
+
+def poly_eval(c, t):
+    """Horner: P(t) = (...(c_D t + c_{D-1}) t + ...) t + c_0."""
+    v = c[-1]
+    for i in range(len(c) - 2, -1, -1):
+        v = v * t + c[i]
+    return v
+
+
+def roots_01(c):
+    """Roots in the open interval (0, 1) where the polynomial changes sign, ascending, as a list
+    of D arrays with 1.0 in the unused slots (D = degree, elementwise over the arrays in c).
+
+    D = 1: -c0 / c1 (c1 != 0).  D = 2: the closed form of the 2D face split: c2 == 0: -c0/c1;
+    else disc = c1 c1 - (4 c2) c0 >= 0, qq = -0.5 (c1 + (c1 >= 0 ? sq : -sq)), roots qq/c2 and
+    c0/qq (qq != 0); min first.  D >= 3: the roots of the derivative (d_i = (i+1) c_{i+1}, this
+    function) cut [0, 1] into intervals on which P is monotone; an interval [lo, hi] with a strict
+    sign change (P(lo) < 0 < P(hi) or P(lo) > 0 > P(hi)) holds one root, found by BISECT_STEPS
+    bisections m = 0.5 (lo + hi) (lo <- m when P(m) > 0 equals P(lo) > 0, else hi <- m) and
+    returned as 0.5 (lo + hi).  Only sign changes split a face integrand: a double root is no kink.
+    """
+    D = len(c) - 1
+    shape = np.shape(c[0])
+    one = np.ones(shape)
+    if D == 1:
+        with np.errstate(divide="ignore", invalid="ignore"):
+            r = np.where(c[1] != 0.0, -c[0] / np.where(c[1] != 0.0, c[1], 1.0), 2.0)
+        return [np.where((r > 0.0) & (r < 1.0), r, 1.0)]
+    if D == 2:
+        c0, c1, c2 = c
+        with np.errstate(divide="ignore", invalid="ignore"):
+            lin = c2 == 0.0
+            c1nz = c1 != 0.0
+            r_lin = np.where(lin & c1nz, -c0 / np.where(c1nz, c1, 1.0), 2.0)
+            disc = c1 * c1 - (4.0 * c2) * c0
+            dok = (~lin) & (disc >= 0.0)
+            sq = np.sqrt(np.where(dok, disc, 0.0))
+            qq = -0.5 * (c1 + np.where(c1 >= 0.0, sq, -sq))
+            qnz = qq != 0.0
+            ra = np.where(dok, qq / np.where(lin, 1.0, c2), 2.0)
+            rb = np.where(dok & qnz, c0 / np.where(qnz, qq, 1.0), 2.0)
+        ra = np.where(lin, r_lin, ra)
+        rb = np.where(lin, 2.0, rb)
+        ra = np.where((ra > 0.0) & (ra < 1.0), ra, 1.0)
+        rb = np.where((rb > 0.0) & (rb < 1.0), rb, 1.0)
+        return [np.minimum(ra, rb), np.maximum(ra, rb)]
+    dc = [float(i + 1) * c[i + 1] for i in range(D)]
+    crit = roots_01(dc)
+    brk = [np.zeros(shape)] + crit + [one]
+    found = []
+    for k in range(D):
+        lo, hi = brk[k].copy(), brk[k + 1].copy()
+        flo, fhi = poly_eval(c, lo), poly_eval(c, hi)
+        change = ((flo < 0.0) & (fhi > 0.0)) | ((flo > 0.0) & (fhi < 0.0))
+        plo = flo > 0.0
+        for _ in range(BISECT_STEPS):
+            m = 0.5 * (lo + hi)
+            same = (poly_eval(c, m) > 0.0) == plo
+            lo = np.where(same, m, lo)
+            hi = np.where(same, hi, m)
+        found.append(np.where(change, 0.5 * (lo + hi), 1.0))
+    srt = np.sort(np.stack(found, axis=-1), axis=-1)
+    return [srt[..., k] for k in range(D)]
+
+
 def face_rule(ctrl, r, dim, f, omega, nf, K):
     """Per-direction face quadrature for local face f of the owner elements in ctrl.
 
@@ -106,8 +198,7 @@ def face_rule(ctrl, r, dim, f, omega, nf, K):
         else disc = c1 c1 - (4 c2) c0 >= 0, qq = -0.5 (c1 + (c1 >= 0 ? sq : -sq)), roots qq/c2
         and c0/qq (qq != 0).  Roots outside (0,1) are replaced by 1.0; rho1 = min, rho2 = max.
         Each piece [lo, hi] carries the n_f GL points s = lo + (hi - lo) t_i, w = (hi - lo) w_i.
-    3D: s0 = (u + t_i)/K, s1 = (v + t_j)/K, w = (w_i/K)(w_j/K), point order
-        ((v K + u) n_f + j) n_f + i; the same points for every direction.
+    3D: face_rule_3d (kink-aligned splitting in both face coordinates).
     """
     t, wt = gauss_legendre(nf)
     F = ctrl.shape[0]
@@ -154,21 +245,87 @@ def face_rule(ctrl, r, dim, f, omega, nf, K):
         nvec = face_normal(ctrl, r, f, s0, aligned=True)    # [F, D, P, 2]
         g = dot_omega(om, nvec)
         return s0, None, w, g
+    return face_rule_3d(ctrl, r, f, omega, nf, K)
+
+
+def _sorted_breaks(K, roots, shape):
+    """[0, 1/K, ..., 1] merged with the roots (1.0 where unused), ascending: list of arrays."""
+    base = [np.full(shape, float(k) / float(K)) for k in range(K + 1)]
+    srt = np.sort(np.stack(base + [np.broadcast_to(x, shape) for x in roots], axis=-1), axis=-1)
+    return srt
+
+
+def _pieces_used(brk):
+    """Number of leading pieces that can have nonzero length: breakpoints below 1.0 (the
+    pieces after them start at 1.0 and are empty)."""
+    return max(1, int((brk < 1.0).sum(axis=-1).max()))
+
+
+def face_rule_3d(ctrl, r, f, omega, nf, K):
+    """3D face quadrature aligned with the kink of max(+-Omega.n, 0) (paper Sec. 2, last
+    paragraph: the face integrands are only piecewise smooth where Omega.n changes sign; the
+    paper suggests Romberg integration, this reading splits at the kink instead).
+
+    g(s0, s1) = Omega . n(s0, s1) is a polynomial of degree D = 2r - 1 in each face coordinate
+    (n = T0 x T1 with T0, T1 the tangents of the Q_r face map).
+      outer (s1): breakpoints k/K (k = 0..K) merged with the roots in (0, 1) of the edge
+        polynomials g(0, s1) and g(1, s1) (roots_01 of the interpolant through s1 = k/D): where
+        the kink curve g = 0 crosses the face edges s0 = 0 and s0 = 1.  Piece [lo, hi] carries
+        s1 = lo + (hi - lo) t_j, w1 = (hi - lo) w_j (n_f GL points).
+      inner (s0), at every outer point: breakpoints k/K merged with the roots in (0, 1) of
+        g(., s1) (interpolant through s0 = k/D): s0 = lo + (hi - lo) t_i, w = w1 ((hi - lo) w_i).
+    Each inner piece integrates a polynomial exactly (n_f = p + r points); along s1 the inner
+    integral is smooth on each outer piece (its kinks are where the kink curve leaves the face),
+    so doubling K converges fast.  Without roots the rule is the K x K composite rule.
+    Point order: outer piece, outer point, inner piece, inner point.  Pieces that start at 1.0
+    are empty; they are dropped when no face/direction of the call uses them, and otherwise
+    carry points of weight 0 (whose terms are +-0 and change no sum).
+    Returns s0, s1, w, g of shape [F, Dd, P].
+    """
+    t, wt = gauss_legendre(nf)
+    F, Dd = ctrl.shape[0], omega.shape[0]
+    Dg = 2 * r - 1
+    xs = np.array([float(k) / float(Dg) for k in range(Dg + 1)])
+    om3 = [omega[:, k][None, :, None, None] for k in range(3)]
+    # edge polynomials g(0, s1), g(1, s1)
+    nE = face_normal(ctrl, r, f, np.array([0.0, 1.0])[:, None], xs[None, :])      # [F, 2, Dg+1, 3]
+    gE = dot_omega(om3, nE[:, None, :, :, :])                                       # [F, Dd, 2, Dg+1]
+    rE = roots_01(poly_from_samples(gE))                                             # Dg x [F, Dd, 2]
+    brk_o = _sorted_breaks(K, [x[..., 0] for x in rE] + [x[..., 1] for x in rE], (F, Dd))
+    n_o = _pieces_used(brk_o)
+    s1o, w1o = [], []
+    for v in range(n_o):
+        lo, hi = brk_o[..., v], brk_o[..., v + 1]
+        ln = hi - lo
+        for j in range(nf):
+            s1o.append(lo + ln * t[j])
+            w1o.append(ln * wt[j])
+    s1o = np.stack(s1o, axis=-1)                                                     # [F, Dd, NO]
+    w1o = np.stack(w1o, axis=-1)
+    NO = s1o.shape[-1]
+    # inner polynomial along each outer point's line
+    s0g = np.broadcast_to(xs, (F, Dd, NO, Dg + 1))
+    s1g = np.broadcast_to(s1o[..., None], (F, Dd, NO, Dg + 1))
+    nI = face_normal(ctrl, r, f, s0g, s1g, aligned=True)                            # [F, Dd, NO, Dg+1, 3]
+    gI = dot_omega([omega[:, k][None, :, None, None] for k in range(3)], nI)
+    rI = roots_01(poly_from_samples(gI))                                             # Dg x [F, Dd, NO]
+    brk_i = _sorted_breaks(K, rI, (F, Dd, NO))
+    n_i = _pieces_used(brk_i)
     s0l, s1l, wl = [], [], []
-    for v in range(K):
-        for u in range(K):
-            for j in range(nf):
-                for i in range(nf):
-                    s0l.append((u + t[i]) / K)
-                    s1l.append((v + t[j]) / K)
-                    wl.append((wt[i] / K) * (wt[j] / K))
-    s0 = np.array(s0l)
-    s1 = np.array(s1l)
-    nvec = face_normal(ctrl, r, f, s0, s1)                 # [F, P, 3]
-    g = dot_omega(om, nvec[:, None, :, :])                 # [F, D, P]
-    P = s0.shape[0]
-    return (np.broadcast_to(s0, (F, D, P)), np.broadcast_to(s1, (F, D, P)),
-            np.broadcast_to(np.array(wl), (F, D, P)), g)
+    for u in range(n_i):
+        lo, hi = brk_i[..., u], brk_i[..., u + 1]
+        ln = hi - lo
+        for i in range(nf):
+            s0l.append(lo + ln * t[i])
+            s1l.append(s1o)
+            wl.append(w1o * (ln * wt[i]))
+    P = NO * n_i * nf
+    s0 = np.stack(s0l, axis=-1).reshape(F, Dd, P)        # [F, Dd, NO, n_i nf] -> (outer, inner) order
+    s1 = np.stack(s1l, axis=-1).reshape(F, Dd, P)
+    w = np.stack(wl, axis=-1).reshape(F, Dd, P)
+    nvec = face_normal(ctrl, r, f, s0, s1, aligned=True)                             # [F, Dd, P, 3]
+    g = dot_omega([omega[:, k][None, :, None] for k in range(3)], nvec)
+    return s0, s1, w, g
 
 
 def coupling_block(a, phi_r, phi_u):
@@ -176,13 +333,13 @@ def coupling_block(a, phi_r, phi_u):
     a: [..., P]; phi_r, phi_u: lists over face nodes of [..., P].  Returns [..., Nf, Nf]."""
     nfn = len(phi_r)
     out = np.zeros(a.shape[:-1] + (nfn, len(phi_u)))
-    P = a.shape[-1]
+    zero = np.zeros(a.shape[:-1] + (1,))
     for i in range(nfn):
+        ar = a * phi_r[i]
         for j in range(len(phi_u)):
-            acc = np.zeros(a.shape[:-1])
-            for q in range(P):
-                acc = acc + (a[..., q] * phi_r[i][..., q]) * phi_u[j][..., q]
-            out[..., i, j] = acc
+            # np.add.accumulate adds strictly left to right: acc_q = acc_{q-1} + term_q, acc = 0.0
+            terms = np.concatenate([zero, ar * phi_u[j]], axis=-1)
+            out[..., i, j] = np.add.accumulate(terms, axis=-1)[..., -1]
     return out
 
 

@@ -75,8 +75,286 @@ __device__ void split_2d_cached(const double* nref, const double* om, double* br
   brk[3] = 1.0;
 }
 
+// ---- 3D faces: the kink of max(+-Omega.n, 0) follows the curve g(s0, s1) = Omega . n = 0, and g
+// is a polynomial of degree Dg = 2r - 1 in each face coordinate.  Outer coordinate s1: breakpoints
+// k/K merged with the roots of the edge polynomials g(0, s1) and g(1, s1) (where the kink curve
+// leaves the face); inner coordinate s0, on every outer quadrature line: breakpoints k/K merged
+// with the roots of g(., s1).  Every piece carries n_f Gauss-Legendre points.  Point order: outer
+// piece, outer point, inner piece, inner point; empty pieces (zero length) carry no points: their
+// terms would be +-0 and change no sum.
+constexpr int BISECT_STEPS = 60;
+constexpr int MAX_DG = 5;            // Q3 geometry: n = T0 x T1 has degree 5 per face coordinate
+
+// Monomial coefficients c[0..D] of the polynomial through (k/D, v_k): divided differences
+// (a_k -= a_{k-1}, / (x_k - x_{k-j}), k descending) then nested multiplication (k descending).
+__device__ inline void poly_from_samples(int D, const double* v, double* c) {
+  double x[MAX_DG + 1], a[MAX_DG + 1];
+  for (int k = 0; k <= D; ++k) {
+    x[k] = (double)k / (double)D;
+    a[k] = v[k];
+  }
+  for (int j = 1; j <= D; ++j)
+    for (int k = D; k >= j; --k) a[k] = (a[k] - a[k - 1]) / (x[k] - x[k - j]);
+  double cur[MAX_DG + 1], nxt[MAX_DG + 1];
+  cur[0] = a[D];
+  int m = 1;
+  for (int k = D - 1; k >= 0; --k) {
+    nxt[0] = a[k] - x[k] * cur[0];
+    for (int i = 1; i < m; ++i) nxt[i] = cur[i - 1] - x[k] * cur[i];
+    nxt[m] = cur[m - 1];
+    ++m;
+    for (int i = 0; i < m; ++i) cur[i] = nxt[i];
+  }
+  for (int i = 0; i <= D; ++i) c[i] = cur[i];
+}
+
+__device__ inline double poly_eval(int D, const double* c, double t) {
+  double v = c[D];
+  for (int i = D - 1; i >= 0; --i) v = v * t + c[i];
+  return v;
+}
+
+// Roots in (0, 1) of c0 + c1 t + c2 t^2 (the 2D split's closed form), ascending, 1.0 if absent.
+__device__ inline void quad_roots_01(double c0, double c1, double c2, double* out) {
+  double ra = 2.0, rb = 2.0;
+  if (c2 == 0.0) {
+    if (c1 != 0.0) ra = -c0 / c1;
+  } else {
+    const double disc = c1 * c1 - (4.0 * c2) * c0;
+    if (disc >= 0.0) {
+      const double sq = sqrt(disc);
+      const double qq = -0.5 * (c1 + (c1 >= 0.0 ? sq : -sq));
+      ra = qq / c2;
+      if (qq != 0.0) rb = c0 / qq;
+    }
+  }
+  ra = (ra > 0.0 && ra < 1.0) ? ra : 1.0;
+  rb = (rb > 0.0 && rb < 1.0) ? rb : 1.0;
+  out[0] = fmin(ra, rb);
+  out[1] = fmax(ra, rb);
+}
+
+// Sign-changing roots in (0, 1) of the degree-D polynomial c, ascending, D entries (1.0 where
+// unused).  Degree >= 3: the derivative's roots cut [0, 1] into monotone intervals; an interval
+// with a strict sign change holds one root, found by BISECT_STEPS bisections from its ends.
+__device__ inline void poly_roots_01(int D, const double* c, double* out) {
+  if (D == 1) {
+    const double r = c[1] != 0.0 ? -c[0] / c[1] : 2.0;
+    out[0] = (r > 0.0 && r < 1.0) ? r : 1.0;
+    return;
+  }
+  double d[MAX_DG - 1][MAX_DG + 1];          // derivative chain: d[k] has degree D - k
+  for (int i = 0; i <= D; ++i) d[0][i] = c[i];
+  for (int k = 1; k <= D - 2; ++k)
+    for (int i = 0; i <= D - k; ++i) d[k][i] = (double)(i + 1) * d[k - 1][i + 1];
+  double crit[MAX_DG];
+  quad_roots_01(d[D - 2][0], d[D - 2][1], d[D - 2][2], crit);
+  for (int level = D - 3; level >= 0; --level) {
+    const int deg = D - level;
+    const double* pc = d[level];
+    double brk[MAX_DG + 1];
+    brk[0] = 0.0;
+    for (int k = 0; k < deg - 1; ++k) brk[k + 1] = crit[k];
+    brk[deg] = 1.0;
+    double found[MAX_DG];
+    for (int k = 0; k < deg; ++k) {
+      double lo = brk[k], hi = brk[k + 1];
+      const double flo = poly_eval(deg, pc, lo), fhi = poly_eval(deg, pc, hi);
+      const bool change = (flo < 0.0 && fhi > 0.0) || (flo > 0.0 && fhi < 0.0);
+      found[k] = 1.0;
+      if (change) {
+        const bool plo = flo > 0.0;
+        for (int s = 0; s < BISECT_STEPS; ++s) {
+          const double m = 0.5 * (lo + hi);
+          if ((poly_eval(deg, pc, m) > 0.0) == plo) lo = m;
+          else hi = m;
+        }
+        found[k] = 0.5 * (lo + hi);
+      }
+    }
+    for (int a = 1; a < deg; ++a)           // ascending (insertion sort)
+      for (int b = a; b > 0 && found[b] < found[b - 1]; --b) {
+        const double t = found[b];
+        found[b] = found[b - 1];
+        found[b - 1] = t;
+      }
+    for (int k = 0; k < deg; ++k) crit[k] = found[k];
+  }
+  for (int k = 0; k < D; ++k) out[k] = crit[k];
+}
+
+// Breakpoints k/K (k = 0..K) merged with nr roots, ascending (insertion sort): K + 1 + nr values.
+__device__ inline void merge_breaks(int K, const double* roots, int nr, double* brk) {
+  int n = 0;
+  for (int k = 0; k <= K; ++k) brk[n++] = (double)k / (double)K;
+  for (int k = 0; k < nr; ++k) brk[n++] = roots[k];
+  for (int a = 1; a < n; ++a)
+    for (int b = a; b > 0 && brk[b] < brk[b - 1]; --b) {
+      const double t = brk[b];
+      brk[b] = brk[b - 1];
+      brk[b - 1] = t;
+    }
+}
+
 __device__ inline int face_npoints(const DevProblem& P) {
   return (P.dim == 2) ? 3 * P.nf : P.K * P.K * P.nf * P.nf;
+}
+
+// Per-warp shared-memory workspace of the 3D rule (doubles).
+constexpr int R3_CHUNK = 32;           // points staged per round
+struct R3Layout {
+  int Dg, nbo, nomax, nip, stride, n;
+  int o_roots, o_brk, o_s1, o_w1, o_ilo, o_iln, o_cnt, o_off, o_pts, o_acc;
+};
+__host__ __device__ inline R3Layout r3_layout(int r, int K, int nf, int Nf) {
+  R3Layout L;
+  L.Dg = 2 * r - 1;
+  L.nbo = K + 1 + 2 * L.Dg;
+  L.nomax = (K + 2 * L.Dg) * nf;
+  L.nip = K + L.Dg;
+  L.stride = 2 + 2 * Nf;
+  int o = 0;
+  L.o_roots = o; o += 2 * L.Dg;
+  L.o_brk = o;   o += L.nbo;
+  L.o_s1 = o;    o += L.nomax;
+  L.o_w1 = o;    o += L.nomax;
+  L.o_ilo = o;   o += L.nomax * L.nip;
+  L.o_iln = o;   o += L.nomax * L.nip;
+  L.o_cnt = o;   o += L.nomax + 1;         // number of points of outer point o (as a double), then NO
+  L.o_off = o;   o += L.nomax + 1;         // first point of outer point o
+  L.o_pts = o;   o += R3_CHUNK * L.stride;
+  L.o_acc = o;   o += 4 * Nf * Nf;
+  L.n = o;
+  return L;
+}
+
+// Roots of g along the edge s0 = side (as a polynomial in s1) or along the line s1 = const (as a
+// polynomial in s0), from the normals at the Dg + 1 equispaced samples.
+__device__ inline void line_roots(int Dg, const double* om, const double* nsamp, double* roots) {
+  double gv[MAX_DG + 1], c[MAX_DG + 1];
+  for (int k = 0; k <= Dg; ++k) gv[k] = dot_omega(3, om, nsamp + 3 * k);
+  poly_from_samples(Dg, gv, c);
+  poly_roots_01(Dg, c, roots);
+}
+
+// Blocks of one (3D face, direction) over the kink-aligned rule: block b = sum over the rule's
+// points, in order from 0.0, of (pt[aoff] pt[roff + i]) pt[uoff + j], spec[3 b .. 3 b + 2] =
+// (aoff, roff, uoff) on the point rows [a_o, a_n, phi_o[Nf], phi_n[Nf]] (a_o = max(-g, 0) w,
+// a_n = max(g, 0) w).  Results in ws[L.o_acc + b Nf^2 + i Nf + j]; nE (optional): the normals at
+// the edge samples (s0 = 0 and s0 = 1, s1 = k / Dg), [2][Dg + 1][3].
+__device__ void rule3_blocks(const DevProblem& P, const R3Layout& L, const double* ctrl, int f, int code,
+                             bool has_nbr, const double* om, const double* nE, double* ws, int lane, int nblk,
+                             const int* spec) {
+  const int K = P.K, nf = P.nf, Nf = P.Nf, np1 = P.p + 1, Dg = L.Dg, stride = L.stride;
+  const double* geo = tabp(P, P.off_geo);
+  const double* gll = tabp(P, P.off_gll);
+  const double* t = tabp(P, P.off_glf_t);
+  const double* wt = tabp(P, P.off_glf_w);
+  double* roots = ws + L.o_roots;
+  double* s1o = ws + L.o_s1;
+  double* w1o = ws + L.o_w1;
+  double* ilo = ws + L.o_ilo;
+  double* iln = ws + L.o_iln;
+  double* cnt = ws + L.o_cnt;
+  double* off = ws + L.o_off;
+  double* pts = ws + L.o_pts;
+  double* acc = ws + L.o_acc;
+  // edge roots (lanes 0 and 1), outer breakpoints and outer points (lane 0)
+  if (lane < 2) {
+    double ns[3 * (MAX_DG + 1)];
+    for (int k = 0; k <= Dg; ++k) {
+      if (nE) {
+        for (int c = 0; c < 3; ++c) ns[3 * k + c] = nE[(lane * (Dg + 1) + k) * 3 + c];
+      } else {
+        face_normal(3, P.r, geo, ctrl, f, (double)lane, (double)k / (double)Dg, ns + 3 * k);
+      }
+    }
+    line_roots(Dg, om, ns, roots + lane * Dg);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    double* brk = ws + L.o_brk;
+    merge_breaks(K, roots, 2 * Dg, brk);
+    int no = 0;
+    for (int v = 0; v + 1 < L.nbo; ++v) {
+      const double lo = brk[v], hi = brk[v + 1];
+      if (!(hi > lo)) continue;
+      const double ln = hi - lo;
+      for (int j = 0; j < nf; ++j) {
+        s1o[no] = lo + ln * t[j];
+        w1o[no] = ln * wt[j];
+        ++no;
+      }
+    }
+    cnt[L.nomax] = (double)no;
+  }
+  __syncwarp();
+  const int NO = (int)cnt[L.nomax];
+  // inner breakpoints along every outer line
+  for (int o = lane; o < NO; o += 32) {
+    double ns[3 * (MAX_DG + 1)], rr[MAX_DG], brk[4 + 1 + MAX_DG];
+    for (int k = 0; k <= Dg; ++k) face_normal(3, P.r, geo, ctrl, f, (double)k / (double)Dg, s1o[o], ns + 3 * k);
+    line_roots(Dg, om, ns, rr);
+    merge_breaks(K, rr, Dg, brk);
+    int c = 0;
+    for (int u = 0; u < K + Dg; ++u) {
+      const double lo = brk[u], hi = brk[u + 1];
+      if (!(hi > lo)) continue;
+      ilo[o * L.nip + c] = lo;
+      iln[o * L.nip + c] = hi - lo;
+      ++c;
+    }
+    cnt[o] = (double)(c * nf);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    double s = 0.0;
+    for (int o = 0; o < NO; ++o) {
+      off[o] = s;
+      s = s + cnt[o];
+    }
+    off[NO] = s;
+  }
+  for (int e = lane; e < nblk * Nf * Nf; e += 32) acc[e] = 0.0;
+  __syncwarp();
+  const int NP = (int)off[NO];
+  for (int c0 = 0; c0 < NP; c0 += R3_CHUNK) {
+    const int q = c0 + lane;
+    if (lane < R3_CHUNK && q < NP) {
+      int o = 0;
+      while ((int)off[o + 1] <= q) ++o;
+      const int loc = q - (int)off[o], u = loc / nf, i = loc % nf;
+      const double lo = ilo[o * L.nip + u], ln = iln[o * L.nip + u];
+      const double s0 = lo + ln * t[i], s1 = s1o[o];
+      const double w = w1o[o] * (ln * wt[i]);
+      double nv[3];
+      face_normal(3, P.r, geo, ctrl, f, s0, s1, nv);
+      const double g = dot_omega(3, om, nv);
+      const double mg = -g;
+      double* pt = pts + lane * stride;
+      pt[0] = (mg > 0.0 ? mg : 0.0) * w;
+      pt[1] = (g > 0.0 ? g : 0.0) * w;
+      for (int k = 0; k < Nf; ++k) pt[2 + k] = face_basis(3, gll, np1, k, s0, s1);
+      if (has_nbr) {
+        double t0, t1;
+        orient_map(3, code, s0, s1, t0, t1);
+        for (int k = 0; k < Nf; ++k) pt[2 + Nf + k] = face_basis(3, gll, np1, k, t0, t1);
+      }
+    }
+    __syncwarp();
+    const int nq = min(R3_CHUNK, NP - c0);
+    for (int e = lane; e < nblk * Nf * Nf; e += 32) {
+      const int b = e / (Nf * Nf), ij = e % (Nf * Nf), i = ij / Nf, j = ij % Nf;
+      const int aoff = spec[3 * b], roff = spec[3 * b + 1], uoff = spec[3 * b + 2];
+      double a = acc[e];
+      for (int qq = 0; qq < nq; ++qq) {
+        const double* pt = pts + qq * stride;
+        a = a + (pt[aoff] * pt[roff + i]) * pt[uoff + j];
+      }
+      acc[e] = a;
+    }
+    __syncwarp();
+  }
 }
 
 __device__ inline PointData face_point(const DevProblem& P, const double* brk, int q) {
@@ -92,11 +370,15 @@ __device__ inline PointData face_point(const DevProblem& P, const double* brk, i
     pd.s1 = 0.0;
     pd.w = ln * wt[i];
   } else {
+    // 3D rule without roots (the K x K composite rule) in the rule's point order: point
+    // ((v nf + j) K + u) nf + i, outer piece v, outer point j, inner piece u, inner point i
     const int K = P.K;
-    const int i = q % nf, j = (q / nf) % nf, u = (q / (nf * nf)) % K, v = q / (nf * nf * K);
-    pd.s0 = ((double)u + t[i]) / (double)K;
-    pd.s1 = ((double)v + t[j]) / (double)K;
-    pd.w = (wt[i] / (double)K) * (wt[j] / (double)K);
+    const int i = q % nf, u = (q / nf) % K, j = (q / (nf * K)) % nf, v = q / (nf * K * nf);
+    const double lo1 = (double)v / (double)K, hi1 = (double)(v + 1) / (double)K, ln1 = hi1 - lo1;
+    const double lo0 = (double)u / (double)K, hi0 = (double)(u + 1) / (double)K, ln0 = hi0 - lo0;
+    pd.s1 = lo1 + ln1 * t[j];
+    pd.s0 = lo0 + ln0 * t[i];
+    pd.w = (ln1 * wt[j]) * (ln0 * wt[i]);
   }
   return pd;
 }
@@ -315,6 +597,32 @@ cudaError_t launch_mass_lu(const DevProblem& P, double* lu, int32_t* perm, cudaS
   return cudaGetLastError();
 }
 
+// Edge weights and inflow modes of one (interior face, direction) from its two coupling blocks
+// fb = [owner <- neighbour][neighbour <- owner] and their max-entry norms mo, mn.
+__device__ void emit_weights(const DevProblem& P, int64_t fi, int d, int64_t owner, int64_t nbr, int f, int fn,
+                             int weighting, const double* mt_lu, const int32_t* mt_perm, const double* fb,
+                             double mo, double mn, double* z_o, double* z_n, uint32_t* facecode, int lane) {
+  const int Nf = P.Nf;
+  const bool eo = mo > 0.0, en = mn > 0.0;
+  double wo = 0.0, wv = 0.0;
+  if (weighting == SN_WEIGHT_UNITY) {
+    wo = eo ? 1.0 : 0.0;
+    wv = en ? 1.0 : 0.0;
+  } else if (weighting == SN_WEIGHT_FACE) {
+    wo = mo;
+    wv = mn;
+  } else {
+    wo = eo ? siginv_weight(P, fb, owner, f, mt_lu, mt_perm, lane) : 0.0;
+    wv = en ? siginv_weight(P, fb + Nf * Nf, nbr, fn, mt_lu, mt_perm, lane) : 0.0;
+  }
+  if (lane == 0) {
+    z_o[fi * P.M + d] = wo;
+    z_n[fi * P.M + d] = wv;
+    if (eo) atomicOr(&facecode[(int64_t)d * P.E + owner], (en ? MODE_MIXED : MODE_PURE) << (2 * f));
+    if (en) atomicOr(&facecode[(int64_t)d * P.E + nbr], (eo ? MODE_MIXED : MODE_PURE) << (2 * fn));
+  }
+}
+
 // ------------------------------------------------------------------ edge weights
 // One warp per interior face, all directions.  The unsplit rule's point data (normals, both
 // sides' basis values) are computed once per face; a direction whose 2D split has no root in
@@ -344,20 +652,72 @@ __global__ void weights_face_kernel(DevProblem P, const int32_t* __restrict__ if
   double* wn = cache + np * stride;                     // np x (1 + dim)
   double* scratch = wn + np * (1 + dim);                // np x stride (2D split directions)
   double* fb = scratch + (dim == 2 ? np * stride : 0);  // [2][Nf][Nf]
+  // 3D: normals at the edge samples [2][Dg+1][3] and along the composite rule's outer lines
+  // [K nf][Dg+1][3] (direction independent), and the rule's workspace
+  const R3Layout L = r3_layout(P.r, P.K, P.nf, Nf);
+  const int Dg = L.Dg, nlines = P.K * P.nf;
+  double* nE = fb + 2 * Nf * Nf;
+  double* nB = nE + (dim == 3 ? 2 * (Dg + 1) * 3 : 0);
+  double* r3 = nB + (dim == 3 ? nlines * (Dg + 1) * 3 : 0);
   copy_ctrl(P, owner, ctrl, lane);
+  const double* geo = tabp(P, P.off_geo);
   if (dim == 2 && lane < 3) {
-    const double* geo = tabp(P, P.off_geo);
     double nv[3];
     face_normal(2, P.r, geo, ctrl, f, lane == 0 ? 0.0 : (lane == 1 ? 0.5 : 1.0), 0.0, nv);
     nref[2 * lane] = nv[0];
     nref[2 * lane + 1] = nv[1];
   }
+  if (dim == 3) {
+    const double* t = tabp(P, P.off_glf_t);
+    for (int s = lane; s < 2 * (Dg + 1); s += 32)
+      face_normal(3, P.r, geo, ctrl, f, (double)(s / (Dg + 1)), (double)(s % (Dg + 1)) / (double)Dg, nE + 3 * s);
+    for (int s = lane; s < nlines * (Dg + 1); s += 32) {
+      const int ob = s / (Dg + 1), k = s % (Dg + 1), v = ob / P.nf, j = ob % P.nf;
+      const double lo = (double)v / (double)P.K, hi = (double)(v + 1) / (double)P.K;
+      face_normal(3, P.r, geo, ctrl, f, (double)k / (double)Dg, lo + (hi - lo) * t[j], nB + 3 * s);
+    }
+  }
   fill_cache(P, ctrl, f, code, cache, wn, lane);
+  const int spec3[6] = {0, 2, 2 + Nf, 1, 2 + Nf, 2};   // owner <- neighbour, neighbour <- owner
   for (int d = 0; d < P.M; ++d) {
     const double om[3] = {P.omega[d * 3 + 0], P.omega[d * 3 + 1], P.omega[d * 3 + 2]};
     double brk[4] = {0.0, 1.0, 1.0, 1.0};
-    if (dim == 2) split_2d_cached(nref, om, brk);
-    const bool unsplit = brk[1] == 1.0 && brk[2] == 1.0;
+    bool unsplit;
+    if (dim == 2) {
+      split_2d_cached(nref, om, brk);
+      unsplit = brk[1] == 1.0 && brk[2] == 1.0;
+    } else {
+      // no root on either edge and none along the composite rule's outer lines: the rule is the
+      // cached composite rule
+      bool root = false;
+      double rr[MAX_DG];
+      if (lane < 2) {
+        line_roots(Dg, om, nE + lane * (Dg + 1) * 3, rr);
+        for (int k = 0; k < Dg; ++k) root = root || rr[k] < 1.0;
+      }
+      for (int ob = lane; ob < nlines; ob += 32) {
+        line_roots(Dg, om, nB + ob * (Dg + 1) * 3, rr);
+        for (int k = 0; k < Dg; ++k) root = root || rr[k] < 1.0;
+      }
+      unsplit = !__any_sync(0xffffffffu, root);
+    }
+    if (dim == 3 && !unsplit) {
+      rule3_blocks(P, L, ctrl, f, code, true, om, nE, r3, lane, 2, spec3);
+      double mo = 0.0, mn = 0.0;
+      for (int t2 = lane; t2 < Nf * Nf; t2 += 32) {
+        const double bo = r3[L.o_acc + t2], bn = r3[L.o_acc + Nf * Nf + t2];
+        fb[t2] = bo;
+        fb[Nf * Nf + t2] = bn;
+        mo = fmax(mo, fabs(bo));
+        mn = fmax(mn, fabs(bn));
+      }
+      __syncwarp();
+      mo = warp_max(mo);
+      mn = warp_max(mn);
+      emit_weights(P, fi, d, owner, nbr, f, fn, weighting, mt_lu, mt_perm, fb, mo, mn, z_o, z_n, facecode, lane);
+      __syncwarp();
+      continue;
+    }
     const double* sp;
     int npe;
     if (unsplit) {
@@ -382,24 +742,7 @@ __global__ void weights_face_kernel(DevProblem P, const int32_t* __restrict__ if
     __syncwarp();
     mo = warp_max(mo);
     mn = warp_max(mn);
-    const bool eo = mo > 0.0, en = mn > 0.0;
-    double wo = 0.0, wv = 0.0;
-    if (weighting == SN_WEIGHT_UNITY) {
-      wo = eo ? 1.0 : 0.0;
-      wv = en ? 1.0 : 0.0;
-    } else if (weighting == SN_WEIGHT_FACE) {
-      wo = mo;
-      wv = mn;
-    } else {
-      wo = eo ? siginv_weight(P, fb, owner, f, mt_lu, mt_perm, lane) : 0.0;
-      wv = en ? siginv_weight(P, fb + Nf * Nf, nbr, fn, mt_lu, mt_perm, lane) : 0.0;
-    }
-    if (lane == 0) {
-      z_o[fi * P.M + d] = wo;
-      z_n[fi * P.M + d] = wv;
-      if (eo) atomicOr(&facecode[(int64_t)d * P.E + owner], (en ? MODE_MIXED : MODE_PURE) << (2 * f));
-      if (en) atomicOr(&facecode[(int64_t)d * P.E + nbr], (eo ? MODE_MIXED : MODE_PURE) << (2 * fn));
-    }
+    emit_weights(P, fi, d, owner, nbr, f, fn, weighting, mt_lu, mt_perm, fb, mo, mn, z_o, z_n, facecode, lane);
     __syncwarp();                        // fb and the point data are rewritten for the next direction
   }
 }
@@ -407,11 +750,19 @@ __global__ void weights_face_kernel(DevProblem P, const int32_t* __restrict__ if
 static int weights_face_shm_per_warp(const DevProblem& P) {
   const int np = (P.dim == 2) ? 3 * P.nf : P.K * P.K * P.nf * P.nf;
   const int stride = 2 + 2 * P.Nf;
-  return P.Nv * P.dim + 6 + np * stride + np * (1 + P.dim) + (P.dim == 2 ? np * stride : 0) + 2 * P.Nf * P.Nf;
+  int n = P.Nv * P.dim + 6 + np * stride + np * (1 + P.dim) + (P.dim == 2 ? np * stride : 0) + 2 * P.Nf * P.Nf;
+  if (P.dim == 3) {
+    const R3Layout L = r3_layout(P.r, P.K, P.nf, P.Nf);
+    n += 2 * (L.Dg + 1) * 3 + P.K * P.nf * (L.Dg + 1) * 3 + L.n;
+  }
+  return n;
 }
 
+// Per-warp workspace of the per-(face, direction) kernels: control points, then the 2D rule's
+// point rows or the 3D rule's workspace.
 static int weights_shm_per_warp(const DevProblem& P) {
-  const int np = (P.dim == 2) ? 3 * P.nf : P.K * P.K * P.nf * P.nf;
+  if (P.dim == 3) return P.Nv * P.dim + r3_layout(P.r, P.K, P.nf, P.Nf).n;
+  const int np = 3 * P.nf;
   return P.Nv * P.dim + np * (2 + 2 * P.Nf) + 2 * P.Nf * P.Nf;
 }
 
@@ -450,12 +801,22 @@ __global__ void bdr_modes_kernel(DevProblem P, const int32_t* __restrict__ bface
   const int stride = 2 + 2 * Nf;
   copy_ctrl(P, e, ctrl, lane);
   double om[3] = {P.omega[d * 3 + 0], P.omega[d * 3 + 1], P.omega[d * 3 + 2]};
-  fill_points(P, ctrl, f, 0, false, om, sp, lane);
   double mi = 0.0, mo = 0.0;
-  for (int t = lane; t < Nf * Nf; t += 32) {
-    const int i = t / Nf, j = t % Nf;
-    mi = fmax(mi, fabs(block_entry(sp, np, stride, 0, 2, 2, i, j)));
-    mo = fmax(mo, fabs(block_entry(sp, np, stride, 1, 2, 2, i, j)));
+  if (P.dim == 3) {
+    const R3Layout L = r3_layout(P.r, P.K, P.nf, Nf);
+    const int spec[6] = {0, 2, 2, 1, 2, 2};            // inflow block, outflow block
+    rule3_blocks(P, L, ctrl, f, 0, false, om, nullptr, sp, lane, 2, spec);
+    for (int t = lane; t < Nf * Nf; t += 32) {
+      mi = fmax(mi, fabs(sp[L.o_acc + t]));
+      mo = fmax(mo, fabs(sp[L.o_acc + Nf * Nf + t]));
+    }
+  } else {
+    fill_points(P, ctrl, f, 0, false, om, sp, lane);
+    for (int t = lane; t < Nf * Nf; t += 32) {
+      const int i = t / Nf, j = t % Nf;
+      mi = fmax(mi, fabs(block_entry(sp, np, stride, 0, 2, 2, i, j)));
+      mo = fmax(mo, fabs(block_entry(sp, np, stride, 1, 2, 2, i, j)));
+    }
   }
   mi = warp_max(mi);
   mo = warp_max(mo);
@@ -524,11 +885,21 @@ __global__ void mixed_blocks_kernel(DevProblem P, const int32_t* __restrict__ if
   const int stride = 2 + 2 * Nf;
   copy_ctrl(P, e0, ctrl, lane);
   double om[3] = {P.omega[d * 3 + 0], P.omega[d * 3 + 1], P.omega[d * 3 + 2]};
-  fill_points(P, ctrl, f0, code, e1 >= 0, om, sp, lane);
+  const double* B0 = nullptr;       // 3D: the two blocks from the rule's workspace
+  const double* B1 = nullptr;
+  if (P.dim == 3) {
+    const R3Layout L = r3_layout(P.r, P.K, P.nf, Nf);
+    const int spec[6] = {0, 2, 2, 1, 2 + Nf, 2 + Nf};  // owner's inflow block, neighbour's inflow block
+    rule3_blocks(P, L, ctrl, f0, code, e1 >= 0, om, nullptr, sp, lane, 2, spec);
+    B0 = sp + L.o_acc;
+    B1 = sp + L.o_acc + Nf * Nf;
+  } else {
+    fill_points(P, ctrl, f0, code, e1 >= 0, om, sp, lane);
+  }
   if (m0) {
     const int64_t slot = mixed_off[(int64_t)d * P.E + e0] + mixed_rank(c0, f0);
     for (int t = lane; t < Nf * Nf; t += 32) {
-      const double v = block_entry(sp, np, stride, 0, 2, 2, t / Nf, t % Nf);
+      const double v = B0 ? B0[t] : block_entry(sp, np, stride, 0, 2, 2, t / Nf, t % Nf);
       mixedB[slot * Nf * Nf + t] = v;
       mixedB32[slot * Nf * Nf + t] = (float)v;
       mixedB32lo[slot * Nf * Nf + t] = (float)(v - (double)(float)v);
@@ -537,7 +908,7 @@ __global__ void mixed_blocks_kernel(DevProblem P, const int32_t* __restrict__ if
   if (m1) {
     const int64_t slot = mixed_off[(int64_t)d * P.E + e1] + mixed_rank(c1, f1);
     for (int t = lane; t < Nf * Nf; t += 32) {
-      const double v = block_entry(sp, np, stride, 1, 2 + Nf, 2 + Nf, t / Nf, t % Nf);
+      const double v = B1 ? B1[t] : block_entry(sp, np, stride, 1, 2 + Nf, 2 + Nf, t / Nf, t % Nf);
       mixedB[slot * Nf * Nf + t] = v;
       mixedB32[slot * Nf * Nf + t] = (float)v;
       mixedB32lo[slot * Nf * Nf + t] = (float)(v - (double)(float)v);

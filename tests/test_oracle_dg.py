@@ -276,7 +276,9 @@ def test_pure_absorber_attenuation_converges_on_twisted_hexes(p):
 def test_reoriented_hexes_give_the_same_solution(p):
     """Renumbering every element's local nodes by a rotation of the reference cube (orientation
     codes with the swap bit) must not change the physical solution: a wrong neighbour face-node
-    map or orientation transform fails here."""
+    map or orientation transform fails here.  The kink-aligned face rule follows the owner's face
+    coordinates, so a renumbered face is integrated on other points: the two solutions agree to
+    the rule's accuracy (measured 9e-9 at p = 1, 5e-10 at p = 2), not to rounding."""
     base = si.make_config("3d_twist_q2_p2_s8", n=3, p=p, sn=2)
     rot = si.make_config("3d_twist_q2_p2_s8", n=3, p=p, sn=2, reorient_seed=11)
     assert np.any(rot.mesh.orient >= 4) and np.any(rot.mesh.orient & 3)
@@ -288,4 +290,4 @@ def test_reoriented_hexes_give_the_same_solution(p):
         D = Discretization(prob)
         R = Sweeper(D, build_graph(D, "face")).source_iterate(tol=1e-13)
         out.append(np.einsum("emn,en->e", D.M, R["phi"]))     # int_e phi, numbering-independent
-    assert np.allclose(out[0], out[1], rtol=1e-11, atol=0)
+    assert np.allclose(out[0], out[1], rtol=1e-7, atol=0)
