@@ -368,7 +368,8 @@ def run_gpu(args):
                          "phi_rel_l2_mixed_ds_vs_fp64": diffs["mixed_ds"]},
         "forms": {k: form_line(k) for k in forms},
         "graph": {"build_s": t_graph, "removed": gstats["n_removed"], "levels": gstats["max_level"] + 1,
-                  "max_scc": gstats["max_scc"], "mixed_faces": gstats["n_mixed_faces"]},
+                  "max_scc": gstats["max_scc"], "mixed_faces": gstats["n_mixed_faces"],
+                  "graph_ms": {k: gstats[k] for k in ("ms_geometry", "ms_weights", "ms_fas", "ms_levels")}},
         "peaks_file": pk_kind,
     }
     ctx.close()
@@ -449,7 +450,8 @@ def run_3d(g, torch, args):
     res = {"workload": "32^3 Q2 hexes twisted 60 deg about z, p=2, S8 (80 dirs), sigma_t=1, sigma_s=0.8, q=1",
            "updates_per_sweep": int(prob.mesh.n_elem * len(prob.w)), "graph_build_s": time.time() - t0,
            "removed_arcs": int(gs["n_removed"]), "max_scc": int(gs["max_scc"]), "levels": int(gs["max_level"] + 1),
-           "mixed_faces": int(gs["n_mixed_faces"])}
+           "mixed_faces": int(gs["n_mixed_faces"]), "n_scc": int(gs["n_scc"]),
+           "graph_ms": {k: gs[k] for k in ("ms_geometry", "ms_weights", "ms_fas", "ms_levels")}}
     ups = prob.mesh.n_elem * len(prob.w)
     E, N = prob.mesh.n_elem, 27
     for name, prec in (("mixed_ds", g.SN_PREC_MIXED_DS), ("fp64", g.SN_PREC_FP64)):

@@ -139,9 +139,11 @@ sn_status sn_set_materials(sn_ctx* ctx, const double* sigma_t, const double* sig
 /* Number of boundary faces (valid after sn_set_mesh). */
 int64_t sn_num_boundary_faces(const sn_ctx* ctx);
 
-/* Build the sweep graph [Sec. 3]: geometric factors, upwind arcs and weights on the device,
- * SCC + minimum feedback arc set on the host (exact for SCCs of at most exact_max <= 16
- * vertices, Eades-Lin-Smyth above), sweep levels and work lists on the device.
+/* Build the sweep graph [Sec. 3]: geometric factors, upwind arcs and weights, strongly connected
+ * components and a minimum-weight feedback arc set per component (exact for components of at most
+ * exact_max <= 16 vertices, Eades-Lin-Smyth above), sweep levels -- all on the device; the work
+ * lists are assembled on the host from the levels.  ms_fas in the stats is the wall time of the
+ * component and feedback-arc-set stage.
  * weighting: SN_WEIGHT_UNITY / _FACE / _SIGINVFACE.  stats may be NULL.
  * Errors: SN_ESTATE (missing inputs), SN_EMESH (det J <= 0 somewhere). */
 sn_status sn_build_graph(sn_ctx* ctx, int weighting, int exact_max, sn_graph_stats* stats);

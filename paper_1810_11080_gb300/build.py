@@ -43,12 +43,13 @@ def build(verbose=False, extra_nvcc=()):
     cu = {
         "geom.cu": [],
         "graph.cu": ["-fmad=false"],
+        "scc.cu": ["-fmad=false"],
         "sweep.cu": [],
         "noalloc.cu": [],
         "batch.cu": [],
         "mlp.cu": [],
     }
-    cpp = ["api.cpp", "batch_api.cpp", "predictor.cpp", "tables.cpp", "fas.cpp", "quadrature.cpp"]
+    cpp = ["api.cpp", "batch_api.cpp", "predictor.cpp", "tables.cpp", "quadrature.cpp"]
     jobs = []
     for src, flags in cu.items():
         obj = os.path.join(BUILD, src + ".o")

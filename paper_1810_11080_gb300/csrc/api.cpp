@@ -4,7 +4,6 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
-#include <thread>
 #include <cuda_runtime.h>
 #include "common.h"
 
@@ -484,99 +483,67 @@ sn_status sn_build_graph(sn_ctx* c, int weighting, int exact_max, sn_graph_stats
   }
   // edge weights and face modes
   const int64_t nI = (int64_t)c->h_iface.size() / 5, nB = (int64_t)c->h_bface.size() / 2;
-  double *d_zo = nullptr, *d_zn = nullptr, *d_lu = nullptr;
+  double *d_win = nullptr, *d_lu = nullptr;
   int32_t* d_perm = nullptr;
   SN_CUDA(c, dalloc(c->d_facecode, (size_t)M * E));
   SN_CUDA(c, cudaMemsetAsync(c->d_facecode, 0, (size_t)M * E * 4, s));
-  SN_CUDA(c, dalloc(d_zo, std::max<size_t>(1, nI * M)));
-  SN_CUDA(c, dalloc(d_zn, std::max<size_t>(1, nI * M)));
+  SN_CUDA(c, dalloc(d_win, (size_t)M * E * nfc));
   if (weighting == SN_WEIGHT_SIGINVFACE) {
     SN_CUDA(c, dalloc(d_lu, (size_t)E * c->N * c->N));
     SN_CUDA(c, dalloc(d_perm, (size_t)E * c->N));
     SN_CUDA(c, launch_mass_lu(P, d_lu, d_perm, s));
     c->launches++;
   }
-  SN_CUDA(c, launch_weights(P, c->d_iface, nI, weighting, d_lu, d_perm, d_zo, d_zn, c->d_facecode, s));
+  SN_CUDA(c, launch_weights(P, c->d_iface, nI, weighting, d_lu, d_perm, d_win, c->d_facecode, s));
   SN_CUDA(c, launch_bdr_modes(P, c->d_bface, nB, c->d_facecode, s));
   c->launches += 2;
   SN_CUDA(c, cudaEventRecord(ev[2], s));
-  std::vector<double> zo(nI * M), zn(nI * M);
-  std::vector<uint32_t> fc((size_t)M * E);
-  if (nI > 0) {
-    SN_CUDA(c, cudaMemcpyAsync(zo.data(), d_zo, zo.size() * 8, cudaMemcpyDeviceToHost, s));
-    SN_CUDA(c, cudaMemcpyAsync(zn.data(), d_zn, zn.size() * 8, cudaMemcpyDeviceToHost, s));
+  // components and feedback arc sets of every direction's graph (device); lag bits into facecode
+  SN_CUDA(c, cudaEventSynchronize(ev[2]));
+  auto t0 = std::chrono::steady_clock::now();
+  DeviceFasStats fs;
+  {
+    cudaError_t fe = device_fas(P, c->d_facecode, d_win, exact_max, &fs, s);
+    dfree(d_win);
+    dfree(d_lu);
+    dfree(d_perm);
+    if (fs.stuck) {
+      set_err(c, "graph components: a fixed-point iteration did not settle");
+      free_graph_state(c);
+      return SN_ESTATE;
+    }
+    SN_CUDA(c, fe);
   }
+  c->launches += fs.launches;
+  gs.ms_fas = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  gs.n_scc = fs.n_scc;
+  gs.max_scc = fs.max_scc;
+  std::vector<uint32_t> fc((size_t)M * E);
   SN_CUDA(c, cudaMemcpyAsync(fc.data(), c->d_facecode, fc.size() * 4, cudaMemcpyDeviceToHost, s));
   SN_CUDA(c, cudaStreamSynchronize(s));
-  dfree(d_zo);
-  dfree(d_zn);
-  dfree(d_lu);
-  dfree(d_perm);
-  // host: SCC + FAS per direction (independent directions in parallel threads)
-  auto t0 = std::chrono::steady_clock::now();
-  std::vector<std::vector<int32_t>> rem_dir(M);
-  std::vector<FasStats> fst(M);
-  std::vector<int64_t> narcs(M, 0);
-  const int* ifc = c->h_iface.data();
-  auto work = [&](int64_t d0, int64_t d1) {
-    for (int64_t d = d0; d < d1; ++d) {
-      std::vector<int32_t> src, dst, fidx, side;
-      std::vector<double> z;
-      for (int64_t i = 0; i < nI; ++i) {
-        const int32_t o = ifc[i * 5], f = ifc[i * 5 + 1], n = ifc[i * 5 + 2], fn = ifc[i * 5 + 3];
-        if (face_mode(fc[d * E + o], f) != MODE_NONE) {   // owner depends on neighbour
-          src.push_back(n);
-          dst.push_back(o);
-          z.push_back(zo[i * M + d]);
-          fidx.push_back((int32_t)i);
-          side.push_back(0);
-        }
-        if (face_mode(fc[d * E + n], fn) != MODE_NONE) {  // neighbour depends on owner
-          src.push_back(o);
-          dst.push_back(n);
-          z.push_back(zn[i * M + d]);
-          fidx.push_back((int32_t)i);
-          side.push_back(1);
-        }
-      }
-      narcs[d] = (int64_t)src.size();
-      std::vector<uint8_t> removed;
-      fst[d] = break_cycles(E, src, dst, z, exact_max, removed);
-      for (size_t k = 0; k < src.size(); ++k)
-        if (removed[k]) {
-          const int64_t i = fidx[k];
-          const int32_t e = dst[k];
-          const int f = side[k] == 0 ? ifc[i * 5 + 1] : ifc[i * 5 + 3];
-          rem_dir[d].push_back(e);
-          rem_dir[d].push_back(src[k]);
-          fc[d * E + e] |= 1u << (16 + f);
-        }
-    }
-  };
-  {
-    unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)M));
-    std::vector<std::thread> th;
-    int64_t chunk = (M + nt - 1) / nt;
-    for (unsigned t = 0; t < nt; ++t) {
-      int64_t a = t * chunk, b = std::min<int64_t>(M, a + chunk);
-      if (a < b) th.emplace_back(work, a, b);
-    }
-    for (auto& t : th) t.join();
-  }
-  gs.ms_fas = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  // arcs and removed (lagged) arcs from the face codes: (d, e, e') rows sorted ascending
   c->h_removed.clear();
-  for (int64_t d = 0; d < M; ++d) {
-    std::vector<std::pair<int32_t, int32_t>> rr;
-    for (size_t k = 0; k < rem_dir[d].size(); k += 2) rr.push_back({rem_dir[d][k], rem_dir[d][k + 1]});
-    std::sort(rr.begin(), rr.end());
-    for (auto& x : rr) c->h_removed.insert(c->h_removed.end(), {(int32_t)d, x.first, x.second});
-    gs.n_arcs += narcs[d];
-    gs.n_scc += fst[d].n_scc;
-    gs.max_scc = std::max(gs.max_scc, fst[d].max_scc);
-  }
+  for (int64_t d = 0; d < M; ++d)
+    for (int64_t e = 0; e < E; ++e) {
+      const uint32_t code = fc[d * E + e];
+      std::pair<int32_t, int32_t> rr[6];
+      int nr = 0;
+      for (int f = 0; f < nfc; ++f) {
+        const int64_t nb = c->h_nbr[e * nfc + f];
+        if (nb < 0 || face_mode(code, f) == MODE_NONE) continue;
+        gs.n_arcs++;
+        if (face_lagged(code, f)) rr[nr++] = {(int32_t)e, (int32_t)nb};
+      }
+      std::sort(rr, rr + nr);
+      for (int k = 0; k < nr; ++k) c->h_removed.insert(c->h_removed.end(), {(int32_t)d, rr[k].first, rr[k].second});
+    }
   c->n_removed = (int64_t)c->h_removed.size() / 3;
   gs.n_removed = c->n_removed;
-  SN_CUDA(c, cudaMemcpyAsync(c->d_facecode, fc.data(), fc.size() * 4, cudaMemcpyHostToDevice, s));
+  if (c->n_removed != fs.n_removed) {
+    set_err(c, "graph components: removed-arc count mismatch");
+    free_graph_state(c);
+    return SN_ESTATE;
+  }
   // levels (device) and work lists
   SN_CUDA(c, cudaEventRecord(ev[3], s));
   SN_CUDA(c, dalloc(c->d_levels, (size_t)M * E));

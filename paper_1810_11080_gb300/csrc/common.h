@@ -41,11 +41,17 @@ double lagrange(const double* nodes, int n, int j, double x);
 double lagrange_deriv(const double* nodes, int n, int j, double x);
 void build_tables(Tables& T, int dim, int p, int r);
 
-// Feedback arc set on one direction's graph (fas.cpp).  Arcs (src -> dst, weight) with
-// dst depending on src.  removed[i] set to 1 for lagged arcs.  Returns SCC stats.
-struct FasStats { int64_t n_scc = 0; int32_t max_scc = 0; };
-FasStats break_cycles(int64_t n, const std::vector<int32_t>& src, const std::vector<int32_t>& dst,
-                      const std::vector<double>& z, int exact_max, std::vector<uint8_t>& removed);
+// Components and feedback arc sets of every direction's graph on the device (scc.cu).
+struct DeviceFasStats {
+  int64_t n_scc = 0;        // components of at least two vertices, over all directions
+  int32_t max_scc = 0;
+  int64_t n_removed = 0;    // arcs marked lagged
+  int64_t launches = 0;
+  int stuck = 0;            // a fixed-point loop exceeded its bound
+};
+struct DevProblem;
+cudaError_t device_fas(const DevProblem& P, uint32_t* fc, const double* win, int exact_max, DeviceFasStats* stats,
+                       cudaStream_t s);
 
 // Device-side view of a problem passed to kernels by value.
 struct DevProblem {
@@ -127,8 +133,8 @@ cudaError_t launch_geometry(const DevProblem& P, double* elem, int* bad_flag, cu
 cudaError_t launch_elem_to_fp32(const DevProblem& P, float* elem32, float* elem32lo, cudaStream_t s);
 cudaError_t launch_mass_lu(const DevProblem& P, double* lu, int32_t* perm, cudaStream_t s);
 cudaError_t launch_weights(const DevProblem& P, const int32_t* iface, int64_t n_iface, int weighting,
-                           const double* mt_lu, const int32_t* mt_perm, double* z_o, double* z_n,
-                           uint32_t* facecode, cudaStream_t s);
+                           const double* mt_lu, const int32_t* mt_perm, double* win, uint32_t* facecode,
+                           cudaStream_t s);
 cudaError_t launch_bdr_modes(const DevProblem& P, const int32_t* bface, int64_t n_bface, uint32_t* facecode,
                              cudaStream_t s);
 cudaError_t launch_mixed_blocks(const DevProblem& P, const int32_t* iface, int64_t n_iface,

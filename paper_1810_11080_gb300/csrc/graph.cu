@@ -598,10 +598,11 @@ cudaError_t launch_mass_lu(const DevProblem& P, double* lu, int32_t* perm, cudaS
 }
 
 // Edge weights and inflow modes of one (interior face, direction) from its two coupling blocks
-// fb = [owner <- neighbour][neighbour <- owner] and their max-entry norms mo, mn.
+// fb = [owner <- neighbour][neighbour <- owner] and their max-entry norms mo, mn; the weight of an
+// arc is stored at the receiving element's face: win[d][e][f].
 __device__ void emit_weights(const DevProblem& P, int64_t fi, int d, int64_t owner, int64_t nbr, int f, int fn,
                              int weighting, const double* mt_lu, const int32_t* mt_perm, const double* fb,
-                             double mo, double mn, double* z_o, double* z_n, uint32_t* facecode, int lane) {
+                             double mo, double mn, double* win, uint32_t* facecode, int lane) {
   const int Nf = P.Nf;
   const bool eo = mo > 0.0, en = mn > 0.0;
   double wo = 0.0, wv = 0.0;
@@ -616,8 +617,9 @@ __device__ void emit_weights(const DevProblem& P, int64_t fi, int d, int64_t own
     wv = en ? siginv_weight(P, fb + Nf * Nf, nbr, fn, mt_lu, mt_perm, lane) : 0.0;
   }
   if (lane == 0) {
-    z_o[fi * P.M + d] = wo;
-    z_n[fi * P.M + d] = wv;
+    const int nfc = 2 * P.dim;
+    win[((int64_t)d * P.E + owner) * nfc + f] = wo;         // arc nbr -> owner, owner's face f
+    win[((int64_t)d * P.E + nbr) * nfc + fn] = wv;          // arc owner -> nbr, nbr's face fn
     if (eo) atomicOr(&facecode[(int64_t)d * P.E + owner], (en ? MODE_MIXED : MODE_PURE) << (2 * f));
     if (en) atomicOr(&facecode[(int64_t)d * P.E + nbr], (eo ? MODE_MIXED : MODE_PURE) << (2 * fn));
   }
@@ -633,8 +635,8 @@ __device__ void emit_weights(const DevProblem& P, int64_t fi, int d, int64_t own
 // points as fill_points does.  iface rows: owner, f, nbr, f_nbr, orient.
 __global__ void weights_face_kernel(DevProblem P, const int32_t* __restrict__ iface, int64_t n_iface,
                                     int weighting, const double* __restrict__ mt_lu,
-                                    const int32_t* __restrict__ mt_perm, double* __restrict__ z_o,
-                                    double* __restrict__ z_n, uint32_t* facecode, int shm_per_warp) {
+                                    const int32_t* __restrict__ mt_perm, double* __restrict__ win,
+                                    uint32_t* facecode, int shm_per_warp) {
   extern __shared__ double sh[];
   const int warp_in_block = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t fi = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_in_block;
@@ -714,7 +716,7 @@ __global__ void weights_face_kernel(DevProblem P, const int32_t* __restrict__ if
       __syncwarp();
       mo = warp_max(mo);
       mn = warp_max(mn);
-      emit_weights(P, fi, d, owner, nbr, f, fn, weighting, mt_lu, mt_perm, fb, mo, mn, z_o, z_n, facecode, lane);
+      emit_weights(P, fi, d, owner, nbr, f, fn, weighting, mt_lu, mt_perm, fb, mo, mn, win, facecode, lane);
       __syncwarp();
       continue;
     }
@@ -742,7 +744,7 @@ __global__ void weights_face_kernel(DevProblem P, const int32_t* __restrict__ if
     __syncwarp();
     mo = warp_max(mo);
     mn = warp_max(mn);
-    emit_weights(P, fi, d, owner, nbr, f, fn, weighting, mt_lu, mt_perm, fb, mo, mn, z_o, z_n, facecode, lane);
+    emit_weights(P, fi, d, owner, nbr, f, fn, weighting, mt_lu, mt_perm, fb, mo, mn, win, facecode, lane);
     __syncwarp();                        // fb and the point data are rewritten for the next direction
   }
 }
@@ -767,8 +769,8 @@ static int weights_shm_per_warp(const DevProblem& P) {
 }
 
 cudaError_t launch_weights(const DevProblem& P, const int32_t* iface, int64_t n_iface, int weighting,
-                           const double* mt_lu, const int32_t* mt_perm, double* z_o, double* z_n,
-                           uint32_t* facecode, cudaStream_t s) {
+                           const double* mt_lu, const int32_t* mt_perm, double* win, uint32_t* facecode,
+                           cudaStream_t s) {
   if (n_iface == 0) return cudaSuccess;
   const int spw = weights_face_shm_per_warp(P);
   int warps = 4;
@@ -776,8 +778,8 @@ cudaError_t launch_weights(const DevProblem& P, const int32_t* iface, int64_t n_
   const size_t shmem = (size_t)warps * spw * sizeof(double);
   cudaFuncSetAttribute(weights_face_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
   const int64_t blocks = (n_iface + warps - 1) / warps;
-  weights_face_kernel<<<(unsigned)blocks, warps * 32, shmem, s>>>(P, iface, n_iface, weighting, mt_lu, mt_perm, z_o,
-                                                                 z_n, facecode, spw);
+  weights_face_kernel<<<(unsigned)blocks, warps * 32, shmem, s>>>(P, iface, n_iface, weighting, mt_lu, mt_perm, win,
+                                                                 facecode, spw);
   return cudaGetLastError();
 }
 
