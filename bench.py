@@ -308,6 +308,19 @@ def run_gpu(args):
         res = ctx.sn_source_iterate(1e-8, 2000, prec, phi_out=phis[k])
         tts[k] = dict(seconds=time.perf_counter() - t0, iters=res["iters"], converged=res["converged"])
     diffs = {k: float(np.linalg.norm(phis[k] - phis["fp64"]) / np.linalg.norm(phis["fp64"])) for k in forms}
+    # the same solves with diffusion synthetic acceleration after every sweep
+    dsa = {}
+    for k in ("fp64", "mixed_ds"):
+        phi_k = np.zeros((E, N))
+        use_schedule(meas[k]["schedule"])
+        ctx.sn_set_dsa(True, args.dsa_rtol, 500)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ctx.sn_source_iterate(1e-8, 2000, forms[k], phi_out=phi_k)
+        dsa[k] = {"seconds": time.perf_counter() - t0, "iters": res["iters"], "converged": res["converged"],
+                  "last_cg_iters": ctx.sn_dsa_last_iters(),
+                  "phi_rel_l2_vs_plain_fp64": float(np.linalg.norm(phi_k - phis["fp64"]) / np.linalg.norm(phis["fp64"]))}
+        ctx.sn_set_dsa(False, args.dsa_rtol, 500)
 
     if rank != 0:
         return None
@@ -367,6 +380,9 @@ def run_gpu(args):
                          "fp64_iters": tts["fp64"]["iters"], "mixed_ds_iters": tts["mixed_ds"]["iters"],
                          "phi_rel_l2_mixed_ds_vs_fp64": diffs["mixed_ds"]},
         "forms": {k: form_line(k) for k in forms},
+        "dsa": {"cg_rtol": args.dsa_rtol, **dsa,
+                "speedup_fp64_dsa_vs_fp64": tts["fp64"]["seconds"] / dsa["fp64"]["seconds"],
+                "speedup_mixed_ds_dsa_vs_fp64": tts["fp64"]["seconds"] / dsa["mixed_ds"]["seconds"]},
         "graph": {"build_s": t_graph, "removed": gstats["n_removed"], "levels": gstats["max_level"] + 1,
                   "max_scc": gstats["max_scc"], "mixed_faces": gstats["n_mixed_faces"],
                   "graph_ms": {k: gstats[k] for k in ("ms_geometry", "ms_weights", "ms_fas", "ms_levels")}},
@@ -503,10 +519,15 @@ def run_learned(g, torch, args):
            "train_n": int(model.get("train_n", 0))}
     ref = np.zeros((E, N))
     runs = {}
-    for name, prec, use in (("plain_fp64", g.SN_PREC_FP64, False), ("learned_fp64", g.SN_PREC_FP64, True),
-                            ("plain_mixed_ds", g.SN_PREC_MIXED_DS, False),
-                            ("learned_mixed_ds", g.SN_PREC_MIXED_DS, True)):
+    for name, prec, use, acc in (("plain_fp64", g.SN_PREC_FP64, False, False),
+                                 ("learned_fp64", g.SN_PREC_FP64, True, False),
+                                 ("plain_mixed_ds", g.SN_PREC_MIXED_DS, False, False),
+                                 ("learned_mixed_ds", g.SN_PREC_MIXED_DS, True, False),
+                                 ("dsa_fp64", g.SN_PREC_FP64, False, True),
+                                 ("dsa_mixed_ds", g.SN_PREC_MIXED_DS, False, True),
+                                 ("learned_dsa_mixed_ds", g.SN_PREC_MIXED_DS, True, True)):
         phi = np.zeros((E, N))
+        ctx.sn_set_dsa(acc, args.dsa_rtol, 500)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if use:
@@ -524,6 +545,9 @@ def run_learned(g, torch, args):
     out.update(runs)
     out["speedup_learned_mixed_ds_vs_plain_fp64"] = runs["plain_fp64"]["seconds"] / runs["learned_mixed_ds"]["seconds"]
     out["speedup_learned_fp64_vs_plain_fp64"] = runs["plain_fp64"]["seconds"] / runs["learned_fp64"]["seconds"]
+    for k in ("dsa_fp64", "dsa_mixed_ds", "learned_dsa_mixed_ds"):
+        out[f"speedup_{k}_vs_plain_fp64"] = runs["plain_fp64"]["seconds"] / runs[k]["seconds"]
+    out["dsa_cg_rtol"] = args.dsa_rtol
     ctx.close()
     return out
 
@@ -690,6 +714,8 @@ def main():
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D twisted-mesh measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-predictor measurement")
     ap.add_argument("--no-small", action="store_true", help="skip the 16x16 p=1 S4 measurement")
+    ap.add_argument("--dsa-rtol", type=float, default=1e-4,
+                    help="relative residual of the conjugate-gradient DSA solve in the accelerated legs")
     ap.add_argument("--learned-n", type=int, default=48, help="mesh size n^3 of the learned-predictor measurement")
     ap.add_argument("--launch", default="auto", choices=["auto", "levels", "dataflow"],
                     help="sweep schedule per form: the autotuner's choice, one launch per level, or one persistent dataflow launch")

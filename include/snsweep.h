@@ -345,6 +345,31 @@ sn_status sn_moment_noalloc(int device, void* cuda_stream, int n_dir, int64_t n_
                             const double* w, const double* psi, const double* phi_prev,
                             double* phi_out, double* residual);
 
+/* ---- Diffusion synthetic acceleration (the paper names DSA as the follow-up for scattering-
+ * dominated problems [Sec. 4 opening, conclusions]; the operator is this library's reading).
+ * After each sweep, sn_si_step (and so sn_source_iterate and the learned iteration) replaces the
+ * scalar flux phi_half = sum_d w_d psi_d by phi_half + dphi, where dphi solves on the same DG space
+ *   a(dphi, v) = int sigma_s (phi_half - phi_prev) v,
+ *   a(u, v) = sum_K int_K (D grad u . grad v + sigma_a u v) + interior faces
+ *             int (kappa [[u]][[v]] - {{D grad u . n}}[[v]] - [[u]]{{D grad v . n}}) + boundary faces
+ *             int (kappa u v - (D grad u . n) v / 2 - u (D grad v . n) / 2),
+ * D = 1/(3 sigma_t), sigma_a = sigma_t - sigma_s, [[u]] = u_owner - u_other (owner = lower element id),
+ * kappa = max(c (D_o/h_o + D_t/h_t)/2, 1/4) inside, max(c D/h, 1/4) on the boundary, c = 2 p (p+1),
+ * h = element measure / face measure.  The system is solved by conjugate gradients preconditioned
+ * with the inverses of the diagonal blocks, to a relative residual of rtol (or max_iter
+ * iterations).  The correction vanishes at the fixed point, which is that of plain source
+ * iteration.  The operator is assembled at the first use after sn_build_graph and kept.
+ * sn_set_dsa: enable (1) or disable (0) the step; rtol in (0, 1); max_iter 1..100000. */
+sn_status sn_set_dsa(sn_ctx* ctx, int enable, double rtol, int max_iter);
+/* One DSA correction on its own: phi_out = phi_half + dphi (all [n_elem][N], host or device).  Uses
+ * the context's iteration buffers as scratch: call sn_si_begin before further sn_si_step calls.
+ * *cg_iters (may be NULL) receives the CG iterations.  Errors: SN_ESTATE (no graph), SN_EMESH (a
+ * singular diagonal block). */
+sn_status sn_dsa_correction(sn_ctx* ctx, const double* phi_half, const double* phi_prev, double* phi_out,
+                            int* cg_iters);
+/* CG iterations of the last DSA solve of this context. */
+int32_t sn_dsa_last_iters(const sn_ctx* ctx);
+
 /* Number of kernel launches this context has issued since creation (diagnostics). */
 int64_t sn_kernel_launches(const sn_ctx* ctx);
 

@@ -28,7 +28,8 @@ EXPORTED = ["sn_create", "sn_destroy", "sn_last_error", "sn_set_mesh", "sn_set_d
             "sn_batch_source_iterate", "sn_mlp_create", "sn_mlp_destroy", "sn_mlp_num_params", "sn_mlp_params",
             "sn_mlp_forward", "sn_mlp_grad", "sn_mlp_train", "sn_predictor_features", "sn_predictor_init_targets",
             "sn_predictor_corr_data", "sn_source_iterate_learned", "sn_predictor_initial_phi",
-            "sn_quadrature_level_symmetric", "sn_set_spin_limit"]
+            "sn_quadrature_level_symmetric", "sn_set_spin_limit", "sn_set_dsa", "sn_dsa_correction",
+            "sn_dsa_last_iters"]
 
 
 class sn_graph_stats(ctypes.Structure):
@@ -112,6 +113,9 @@ def load(path=LIB_PATH):
         "sn_moment_noalloc": (I, [I, P, I, I64, I, P, P, P, P, ctypes.POINTER(D)]),
         "sn_quadrature_level_symmetric": (I, [I, I, ctypes.POINTER(I), P, P]),
         "sn_set_spin_limit": (I, [P, I64]),
+        "sn_set_dsa": (I, [P, I, D, I]),
+        "sn_dsa_correction": (I, [P, P, P, P, ctypes.POINTER(I)]),
+        "sn_dsa_last_iters": (ctypes.c_int32, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -269,6 +273,20 @@ class Context:
 
     def sn_set_launch(self, mode, blocks_per_sm=0):
         return self._check(self._lib.sn_set_launch(self._c, int(mode), int(blocks_per_sm)))
+
+    def sn_set_dsa(self, enable=True, rtol=1e-4, max_iter=500):
+        en = int(enable) if not isinstance(enable, bool) else (1 if enable else 0)
+        return self._check(self._lib.sn_set_dsa(self._c, en, float(rtol), int(max_iter)))
+
+    def sn_dsa_correction(self, phi_half, phi_prev, phi_out):
+        it = ctypes.c_int()
+        self._check(self._lib.sn_dsa_correction(self._c, _ptr(phi_half, np.float64, "phi_half"),
+                                                _ptr(phi_prev, np.float64, "phi_prev"),
+                                                _ptr(phi_out, np.float64, "phi_out"), ctypes.byref(it)))
+        return it.value
+
+    def sn_dsa_last_iters(self):
+        return self._lib.sn_dsa_last_iters(self._c)
 
     def sn_set_spin_limit(self, polls):
         return self._check(self._lib.sn_set_spin_limit(self._c, int(polls)))

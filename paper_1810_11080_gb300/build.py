@@ -44,6 +44,7 @@ def build(verbose=False, extra_nvcc=()):
         "geom.cu": [],
         "graph.cu": ["-fmad=false"],
         "scc.cu": ["-fmad=false"],
+        "dsa.cu": [],
         "sweep.cu": [],
         "noalloc.cu": [],
         "batch.cu": [],

@@ -62,7 +62,15 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+void free_dsa(sn_ctx* c) {
+  sn::DsaState& D = c->dsa;
+  for (double** p : {&D.diag, &D.inv, &D.selfb, &D.offb, &D.vol, &D.b, &D.x, &D.r, &D.z, &D.p, &D.q, &D.sc}) dfree(*p);
+  dfree(D.bad);
+  D.ready = false;
+}
+
 void free_graph_state(sn_ctx* c) {
+  free_dsa(c);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   c->graphs.clear();
   dfree(c->d_facecode);
@@ -894,6 +902,75 @@ sn_status sn_moment(sn_ctx* c, const double* psi, const double* phi_prev, double
   return SN_OK;
 }
 
+namespace {
+// Allocates and assembles the DSA operator of the current graph and materials (once).
+sn_status dsa_prepare(sn_ctx* c) {
+  sn::DsaState& D = c->dsa;
+  if (D.ready) return SN_OK;
+  const size_t N = c->N, E = c->E, nfc = 2 * c->dim;
+  SN_CUDA(c, dalloc(D.diag, E * N * N));
+  SN_CUDA(c, dalloc(D.inv, E * N * N));
+  SN_CUDA(c, dalloc(D.selfb, E * nfc * N * N));
+  SN_CUDA(c, dalloc(D.offb, E * nfc * N * N));
+  SN_CUDA(c, dalloc(D.vol, E));
+  for (double** p : {&D.b, &D.x, &D.r, &D.z, &D.p, &D.q}) SN_CUDA(c, dalloc(*p, E * N));
+  SN_CUDA(c, dalloc(D.sc, 10));
+  SN_CUDA(c, dalloc(D.bad, 1));
+  SN_CUDA(c, cudaMemsetAsync(D.bad, 0, sizeof(int), c->stream));
+  DevProblem P = c->dev();
+  SN_CUDA(c, dsa_assemble(P, D, c->stream));
+  c->launches += 3;
+  int bad = 0;
+  SN_CUDA(c, cudaMemcpyAsync(&bad, D.bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  SN_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (bad) {
+    set_err(c, "DSA operator: a diagonal block is singular");
+    free_dsa(c);
+    return SN_EMESH;
+  }
+  D.ready = true;
+  return SN_OK;
+}
+}  // namespace
+
+sn_status sn_set_dsa(sn_ctx* c, int enable, double rtol, int max_iter) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, enable == 0 || enable == 1, SN_EINVAL, "enable must be 0 or 1");
+  SN_REQ(c, std::isfinite(rtol) && rtol > 0.0 && rtol < 1.0, SN_EINVAL, "rtol must be in (0, 1)");
+  SN_REQ(c, max_iter >= 1 && max_iter <= 100000, SN_EINVAL, "max_iter must be 1..100000");
+  c->dsa_on = enable == 1;
+  c->dsa_rtol = rtol;
+  c->dsa_max_iter = max_iter;
+  return SN_OK;
+}
+
+sn_status sn_dsa_correction(sn_ctx* c, const double* phi_half, const double* phi_prev, double* phi_out,
+                            int* cg_iters) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
+  SN_REQ(c, phi_half && phi_prev && phi_out, SN_EINVAL, "null array");
+  cudaSetDevice(c->device);
+  sn_status st = dsa_prepare(c);
+  if (st != SN_OK) return st;
+  const size_t nphi = (size_t)c->E * c->N;
+  // host or device inputs: staged into the context's scalar-flux buffers
+  SN_CUDA(c, cudaMemcpyAsync(c->d_phi2, phi_half, nphi * 8, cudaMemcpyDefault, c->stream));
+  SN_CUDA(c, cudaMemcpyAsync(c->d_phi, phi_prev, nphi * 8, cudaMemcpyDefault, c->stream));
+  SN_CUDA(c, cudaMemsetAsync(c->d_red, 0, 2 * sizeof(unsigned long long), c->stream));
+  DevProblem P = c->dev();
+  int it = 0;
+  SN_CUDA(c, dsa_apply(P, c->dsa, c->d_phi2, c->d_phi, c->d_phi2, c->d_src, c->d_srch, c->d_srcl, c->d_red,
+                       c->dsa_rtol, c->dsa_max_iter, &it, &c->launches, c->stream));
+  SN_CUDA(c, cudaMemcpyAsync(phi_out, c->d_phi2, nphi * 8, cudaMemcpyDefault, c->stream));
+  SN_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->dsa_last_iters = it;
+  c->si_ready = false;                 // the iteration buffers were used as scratch
+  if (cg_iters) *cg_iters = it;
+  return SN_OK;
+}
+
+int32_t sn_dsa_last_iters(const sn_ctx* c) { return c ? c->dsa_last_iters : 0; }
+
 sn_status sn_si_begin(sn_ctx* c, const double* phi0) {
   if (!c) return SN_EINVAL;
   SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
@@ -931,9 +1008,20 @@ sn_status sn_si_step(sn_ctx* c, int precision, double* residual, float* ms_sweep
   if (ms_sweep) SN_CUDA(c, cudaEventRecord(c->ev_b, s));
   SN_CUDA(c, cudaMemsetAsync(c->d_red, 0, 2 * sizeof(unsigned long long), s));
   DevProblem P = c->dev();
-  SN_CUDA(c, launch_moment(P, c->d_psi[cur ^ 1], c->d_phi, c->d_phi2, c->d_src, c->d_srch, c->d_srcl, c->d_red,
-                           s));
-  c->launches++;
+  if (c->dsa_on) {
+    // phi_half = sum_d w_d psi_d, then phi = phi_half + dphi with the residual and the source
+    if ((st = dsa_prepare(c)) != SN_OK) return st;
+    SN_CUDA(c, launch_moment(P, c->d_psi[cur ^ 1], c->d_phi, c->d_phi2, nullptr, nullptr, nullptr, nullptr, s));
+    c->launches++;
+    int it = 0;
+    SN_CUDA(c, dsa_apply(P, c->dsa, c->d_phi2, c->d_phi, c->d_phi2, c->d_src, c->d_srch, c->d_srcl, c->d_red,
+                         c->dsa_rtol, c->dsa_max_iter, &it, &c->launches, s));
+    c->dsa_last_iters = it;
+  } else {
+    SN_CUDA(c, launch_moment(P, c->d_psi[cur ^ 1], c->d_phi, c->d_phi2, c->d_src, c->d_srch, c->d_srcl, c->d_red,
+                             s));
+    c->launches++;
+  }
   unsigned long long red[3];
   SN_CUDA(c, cudaMemcpyAsync(red, c->d_red, sizeof(red), cudaMemcpyDeviceToHost, s));
   SN_CUDA(c, cudaStreamSynchronize(s));

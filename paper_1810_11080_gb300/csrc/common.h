@@ -53,6 +53,20 @@ struct DevProblem;
 cudaError_t device_fas(const DevProblem& P, uint32_t* fc, const double* win, int exact_max, DeviceFasStats* stats,
                        cudaStream_t s);
 
+// Diffusion synthetic acceleration (dsa.cu): the operator's blocks and the CG vectors.
+struct DsaState {
+  double *diag = nullptr, *inv = nullptr, *selfb = nullptr, *offb = nullptr, *vol = nullptr;   // operator
+  double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;   // CG
+  double* sc = nullptr;    // [0] b.b, then a ring of three (p.q, r.z, r.r) slots
+  int* bad = nullptr;      // a diagonal block was singular
+  bool ready = false;
+};
+struct DevProblem;
+cudaError_t dsa_assemble(const DevProblem& P, DsaState& D, cudaStream_t s);
+cudaError_t dsa_apply(const DevProblem& P, DsaState& D, const double* half, const double* prev, double* phi_new,
+                      double* src, float* src_h, float* src_l, unsigned long long* red, double rtol, int max_iter,
+                      int* cg_iters, int64_t* launches, cudaStream_t s);
+
 // Device-side view of a problem passed to kernels by value.
 struct DevProblem {
   int dim, r, p, N, Nf, nv, nf, K, Q, Nv, M;
@@ -218,6 +232,12 @@ struct sn_ctx {
   unsigned long long* d_red = nullptr;   // [0..1] residual maxima, [2] error word, [3] queue head
   int* d_flag = nullptr;
   int* d_done = nullptr;                 // [M][E] dataflow completion flags
+  // diffusion synthetic acceleration (sn_set_dsa)
+  sn::DsaState dsa;
+  bool dsa_on = false;
+  double dsa_rtol = 1e-4;
+  int dsa_max_iter = 500;
+  int dsa_last_iters = 0;
   int launch_mode = 0;                   // SN_LAUNCH_LEVELS / SN_LAUNCH_DATAFLOW
   long long spin_limit = 0;              // dataflow wait limit (0: the kernels' default)
   int blocks_per_sm = 0;                 // dataflow grid: 0 = occupancy limit

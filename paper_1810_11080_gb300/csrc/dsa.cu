@@ -302,5 +302,224 @@ __global__ void dsa_diag_kernel(int64_t E, int N, int nfc, const double* __restr
   for (int t = 0; t < N * N; ++t) inv[e * N * N + t] = V[t];
 }
 
+// ---------------------------------------------------------------- right-hand side and CG
+// b_e = sigma_s,e M_e (phi_half - phi_prev)_e; also x = 0 and bb = b . b.  Thread per (element, node).
+__global__ void dsa_rhs_kernel(DevProblem P, const double* __restrict__ half, const double* __restrict__ prev,
+                               double* __restrict__ b, double* __restrict__ x, double* sc) {
+  const int N = P.N;
+  const int64_t n = P.E * N;
+  double acc = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / N;
+    const int m = (int)(t % N);
+    const double* M = P.elem + e * P.blk + (int64_t)P.dim * N * N + (int64_t)m * N;
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) s += M[k] * (half[e * N + k] - prev[e * N + k]);
+    s *= P.sig_s[e];
+    b[t] = s;
+    x[t] = 0.0;
+    acc += s * s;
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) atomicAdd(sc + 0, acc);
+}
+
+// y_e = Minv_e v_e (block, column-major inverse): warp per element, lane = row.
+__device__ inline double block_apply(const double* __restrict__ blk, const double* __restrict__ v, int N, int i) {
+  double s = 0.0;
+  for (int j = 0; j < N; ++j) s += blk[j * N + i] * v[j];
+  return s;
+}
+
+// r = b; z = Minv r; p = z; rz = r . z into ring slot 2 (the "previous iteration").
+__global__ void dsa_cg_init_kernel(DevProblem P, const double* __restrict__ inv, const double* __restrict__ b,
+                                   double* __restrict__ r, double* __restrict__ z, double* __restrict__ pv, double* sc) {
+  const int N = P.N, lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  double acc = 0.0;
+  if (e < P.E) {
+    const double* be = b + e * N;
+    double zi = 0.0;
+    if (lane < N) {
+      r[e * N + lane] = be[lane];
+      zi = block_apply(inv + e * N * N, be, N, lane);
+      z[e * N + lane] = zi;
+      pv[e * N + lane] = zi;
+      acc = be[lane] * zi;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0 && acc != 0.0) atomicAdd(sc + 1 + 3 * 2 + 1, acc);
+}
+
+// Scalar ring: sc[1 + 3 s + 0] = p.q, [1] = r.z (new), [2] = r.r of iteration k with slot s = k % 3.
+// q = A p and p.q (warp per element, lane = row)
+__global__ void dsa_spmv_kernel(DevProblem P, const double* __restrict__ diag, const double* __restrict__ offb,
+                                const double* __restrict__ pv, double* __restrict__ q, double* sc, int slot) {
+  const int N = P.N, lane = threadIdx.x & 31, nfc = 2 * P.dim;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  double acc = 0.0;
+  if (e < P.E && lane < N) {
+    double s = block_apply(diag + e * N * N, pv + e * N, N, lane);
+    for (int f = 0; f < nfc; ++f) {
+      const int64_t nb = P.nbr[e * nfc + f];
+      if (nb >= 0) s += block_apply(offb + (e * nfc + f) * N * N, pv + nb * N, N, lane);
+    }
+    q[e * N + lane] = s;
+    acc = s * pv[e * N + lane];
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0 && acc != 0.0) atomicAdd(sc + 1 + 3 * slot + 0, acc);
+}
+
+// alpha = rz_prev / pq; x += alpha p; r -= alpha q; z = Minv r; rz_new, rr
+__global__ void dsa_update_kernel(DevProblem P, const double* __restrict__ inv, const double* __restrict__ pv,
+                                  const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r,
+                                  double* __restrict__ z, double* sc, int slot, int prev) {
+  const int N = P.N, lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const double pq = sc[1 + 3 * slot + 0], rz = sc[1 + 3 * prev + 1];
+  const double alpha = pq != 0.0 ? rz / pq : 0.0;
+  double arz = 0.0, arr = 0.0;
+  if (e < P.E) {
+    double ri = 0.0;
+    if (lane < N) {
+      const int64_t o = e * N + lane;
+      x[o] += alpha * pv[o];
+      ri = r[o] - alpha * q[o];
+      r[o] = ri;
+    }
+    __syncwarp();
+    if (lane < N) {
+      const double zi = block_apply(inv + e * N * N, r + e * N, N, lane);
+      z[e * N + lane] = zi;
+      arz = ri * zi;
+      arr = ri * ri;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    arz += __shfl_xor_sync(0xffffffffu, arz, off);
+    arr += __shfl_xor_sync(0xffffffffu, arr, off);
+  }
+  if (lane == 0 && (arz != 0.0 || arr != 0.0)) {
+    atomicAdd(sc + 1 + 3 * slot + 1, arz);
+    atomicAdd(sc + 1 + 3 * slot + 2, arr);
+  }
+}
+
+// beta = rz_new / rz_prev; p = z + beta p; clear the slot of the next iteration
+__global__ void dsa_pupdate_kernel(int64_t n, const double* __restrict__ z, double* __restrict__ pv, double* sc,
+                                   int slot, int prev, int next) {
+  const double rzn = sc[1 + 3 * slot + 1], rzp = sc[1 + 3 * prev + 1];
+  const double beta = rzp != 0.0 ? rzn / rzp : 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    pv[t] = z[t] + beta * pv[t];
+  if (blockIdx.x == 0 && threadIdx.x < 3) sc[1 + 3 * next + threadIdx.x] = 0.0;
+}
+
+// phi_new = phi_half + x; residual maxima |phi_new - phi_prev|, |phi_new|; source M (q + sigma_s
+// phi_new / (4 pi)) and its (hi, lo) split.  Block = whole elements: threads (element slot, node).
+__global__ void dsa_accept_kernel(DevProblem P, const double* __restrict__ half, const double* __restrict__ x,
+                                  const double* __restrict__ prev, double* __restrict__ phi_new, double* __restrict__ src,
+                                  float* __restrict__ src_h, float* __restrict__ src_l, unsigned long long* red) {
+  extern __shared__ double sphi[];
+  const int N = P.N;
+  const int epb = blockDim.x / N;
+  const int le = threadIdx.x / N, m = threadIdx.x % N;
+  const int64_t e = (int64_t)blockIdx.x * epb + le;
+  const bool ok = le < epb && e < P.E;
+  double phi = 0.0, diff = 0.0, mag = 0.0;
+  if (ok) {
+    phi = half[e * N + m] + x[e * N + m];
+    phi_new[e * N + m] = phi;
+    diff = fabs(phi - prev[e * N + m]);
+    mag = fabs(phi);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    diff = fmax(diff, __shfl_xor_sync(0xffffffffu, diff, off));
+    mag = fmax(mag, __shfl_xor_sync(0xffffffffu, mag, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(red + 0, (unsigned long long)__double_as_longlong(diff));
+    atomicMax(red + 1, (unsigned long long)__double_as_longlong(mag));
+  }
+  sphi[threadIdx.x] = phi;
+  __syncthreads();
+  if (ok && src != nullptr) {
+    const double* Mm = P.elem + e * P.blk + (int64_t)P.dim * N * N + (int64_t)m * N;
+    const double c = P.sig_s[e] * (1.0 / (4.0 * 3.14159265358979323846));
+    const double* qe = P.q + e * N;
+    double s = 0.0;
+    for (int n2 = 0; n2 < N; ++n2) s = fma(Mm[n2], fma(c, sphi[le * N + n2], qe[n2]), s);
+    src[e * N + m] = s;
+    if (src_h != nullptr) {
+      const float h = (float)s;
+      src_h[e * N + m] = h;
+      src_l[e * N + m] = (float)(s - (double)h);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t dsa_assemble(const DevProblem& P, DsaState& D, cudaStream_t s) {
+  const int N = P.N, nfc = 2 * P.dim;
+  const size_t shv = sizeof(double) * ((size_t)P.Q * 10);
+  dsa_volume_kernel<<<(unsigned)P.E, 128, shv, s>>>(P, D.diag, D.vol);
+  const int np = P.dim == 2 ? P.nf : P.K * P.K * P.nf * P.nf;
+  const int spw = np * (2 + 4 * N);
+  int warps = 4;
+  while (warps > 1 && (size_t)warps * spw * sizeof(double) > 96 * 1024) warps >>= 1;
+  const size_t shf = (size_t)warps * spw * sizeof(double);
+  cudaFuncSetAttribute(dsa_face_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf);
+  const int64_t items = P.E * nfc;
+  dsa_face_kernel<<<(unsigned)((items + warps - 1) / warps), warps * 32, shf, s>>>(P, D.vol, D.selfb, D.offb, spw);
+  dsa_diag_kernel<<<(unsigned)((P.E + 63) / 64), 64, 0, s>>>(P.E, N, nfc, D.selfb, D.diag, D.inv, D.bad);
+  return cudaGetLastError();
+}
+
+// One DSA correction: half = phi_half, prev = phi_prev; on return phi_new = half + dphi, the residual
+// maxima in red[0..1] and the source for the next sweep.  *cg_iters receives the iterations run.
+cudaError_t dsa_apply(const DevProblem& P, DsaState& D, const double* half, const double* prev, double* phi_new,
+                      double* src, float* src_h, float* src_l, unsigned long long* red, double rtol, int max_iter,
+                      int* cg_iters, int64_t* launches, cudaStream_t s) {
+  const int N = P.N;
+  const int64_t n = P.E * N;
+  const unsigned gw = (unsigned)((P.E + 3) / 4);          // warp per element, 4 per block
+  cudaError_t e = cudaMemsetAsync(D.sc, 0, 10 * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  dsa_rhs_kernel<<<1216, 256, 0, s>>>(P, half, prev, D.b, D.x, D.sc);
+  dsa_cg_init_kernel<<<gw, 128, 0, s>>>(P, D.inv, D.b, D.r, D.z, D.p, D.sc);
+  *launches += 2;
+  double bb = 0.0;
+  int it = 0;
+  e = cudaMemcpyAsync(&bb, D.sc, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  if (bb > 0.0) {
+    const double target = rtol * rtol * bb;
+    for (it = 0; it < max_iter;) {
+      for (int k = 0; k < 8 && it < max_iter; ++k, ++it) {
+        const int slot = it % 3, prevs = (it + 2) % 3, next = (it + 1) % 3;
+        dsa_spmv_kernel<<<gw, 128, 0, s>>>(P, D.diag, D.offb, D.p, D.q, D.sc, slot);
+        dsa_update_kernel<<<gw, 128, 0, s>>>(P, D.inv, D.p, D.q, D.x, D.r, D.z, D.sc, slot, prevs);
+        dsa_pupdate_kernel<<<1216, 256, 0, s>>>(n, D.z, D.p, D.sc, slot, prevs, next);
+        *launches += 3;
+      }
+      double rr = 0.0;
+      e = cudaMemcpyAsync(&rr, D.sc + 1 + 3 * ((it - 1) % 3) + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return e;
+      if (rr <= target) break;
+    }
+  }
+  *cg_iters = it;
+  const unsigned th = (unsigned)((256 / N) * N);
+  const int64_t epb = th / N;
+  dsa_accept_kernel<<<(unsigned)((P.E + epb - 1) / epb), th, th * sizeof(double), s>>>(P, half, D.x, prev, phi_new, src,
+                                                                                      src_h, src_l, red);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
 }  // namespace sn
