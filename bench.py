@@ -313,14 +313,14 @@ def run_gpu(args):
     for k in ("fp64", "mixed_ds"):
         phi_k = np.zeros((E, N))
         use_schedule(meas[k]["schedule"])
-        ctx.sn_set_dsa(True, args.dsa_rtol, 500)
+        ctx.sn_set_dsa(True, args.dsa_rtol, args.dsa_max_cg)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = ctx.sn_source_iterate(1e-8, 2000, forms[k], phi_out=phi_k)
         dsa[k] = {"seconds": time.perf_counter() - t0, "iters": res["iters"], "converged": res["converged"],
                   "last_cg_iters": ctx.sn_dsa_last_iters(),
                   "phi_rel_l2_vs_plain_fp64": float(np.linalg.norm(phi_k - phis["fp64"]) / np.linalg.norm(phis["fp64"]))}
-        ctx.sn_set_dsa(False, args.dsa_rtol, 500)
+        ctx.sn_set_dsa(False, args.dsa_rtol, args.dsa_max_cg)
 
     if rank != 0:
         return None
@@ -380,7 +380,7 @@ def run_gpu(args):
                          "fp64_iters": tts["fp64"]["iters"], "mixed_ds_iters": tts["mixed_ds"]["iters"],
                          "phi_rel_l2_mixed_ds_vs_fp64": diffs["mixed_ds"]},
         "forms": {k: form_line(k) for k in forms},
-        "dsa": {"cg_rtol": args.dsa_rtol, **dsa,
+        "dsa": {"cg_rtol": args.dsa_rtol, "cg_max_iter": args.dsa_max_cg, **dsa,
                 "speedup_fp64_dsa_vs_fp64": tts["fp64"]["seconds"] / dsa["fp64"]["seconds"],
                 "speedup_mixed_ds_dsa_vs_fp64": tts["fp64"]["seconds"] / dsa["mixed_ds"]["seconds"]},
         "graph": {"build_s": t_graph, "removed": gstats["n_removed"], "levels": gstats["max_level"] + 1,
@@ -397,6 +397,8 @@ def run_gpu(args):
         out["twisted_3d"] = run_3d(g, torch, args)
     if not args.no_learned:
         out["learned"] = run_learned(g, torch, args)
+    if not args.no_dsa_thick:
+        out["dsa_thick"] = run_dsa_thick(g, torch, args)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     return out
@@ -496,6 +498,40 @@ def run_3d(g, torch, args):
     return res
 
 
+def run_dsa_thick(g, torch, args):
+    """Where diffusion synthetic acceleration is the tool: the 2D Q3 p=3 S8 workload family on a
+    64 x 64 mesh with sigma_t ~ U[10, 100] per element (optically thick cells) and scattering ratio
+    0.995.  Time to a 1e-8 scalar-flux change, double-single sweeps, plain vs DSA."""
+    import sn_inputs as si
+    prob = si.make_config("2d_smooth_q3_p3_s8", n=64)
+    prob.sigma_t = 20.0 * prob.sigma_t
+    prob.sigma_s = 0.995 * prob.sigma_t
+    stream = torch.cuda.Stream()
+    ctx = g.setup_problem(prob, device=0, stream=stream.cuda_stream)
+    ctx.sn_build_graph("face", 10)
+    ctx.sn_autotune(g.SN_PREC_MIXED_DS)
+    E, N = prob.mesh.n_elem, 16
+    out = {"workload": "64x64 Q3 quads, smooth perturbation 0.1h, p=3, S8 (40 dirs), sigma_t~U[10,100], c=0.995, q=1",
+           "updates_per_sweep": int(E * len(prob.w))}
+    ref = None
+    for name, acc in (("plain_mixed_ds", False), ("dsa_mixed_ds", True)):
+        phi = np.zeros((E, N))
+        ctx.sn_set_dsa(acc, args.dsa_rtol, args.dsa_max_cg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = ctx.sn_source_iterate(1e-8, 20000, g.SN_PREC_MIXED_DS, phi_out=phi)
+        dt = time.perf_counter() - t0
+        if ref is None:
+            ref = phi.copy()
+        out[name] = {"seconds": dt, "iters": r["iters"], "converged": r["converged"],
+                     "phi_rel_l2_vs_plain": float(np.linalg.norm(phi - ref) / np.linalg.norm(ref))}
+        if acc:
+            out[name]["last_cg_iters"] = ctx.sn_dsa_last_iters()
+    out["speedup_dsa"] = out["plain_mixed_ds"]["seconds"] / out["dsa_mixed_ds"]["seconds"]
+    ctx.close()
+    return out
+
+
 def run_learned(g, torch, args):
     """3D learned-predictor workload family: n^3 Q2 hexes with seeded smooth perturbation 0.1h,
     p = 2, S12 (168 directions), sigma_t = exp(N(0,1)), c = 0.99, q = 1, the workload's own seeds
@@ -523,11 +559,10 @@ def run_learned(g, torch, args):
                                  ("learned_fp64", g.SN_PREC_FP64, True, False),
                                  ("plain_mixed_ds", g.SN_PREC_MIXED_DS, False, False),
                                  ("learned_mixed_ds", g.SN_PREC_MIXED_DS, True, False),
-                                 ("dsa_fp64", g.SN_PREC_FP64, False, True),
                                  ("dsa_mixed_ds", g.SN_PREC_MIXED_DS, False, True),
                                  ("learned_dsa_mixed_ds", g.SN_PREC_MIXED_DS, True, True)):
         phi = np.zeros((E, N))
-        ctx.sn_set_dsa(acc, args.dsa_rtol, 500)
+        ctx.sn_set_dsa(acc, args.dsa_rtol, args.dsa_max_cg)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if use:
@@ -545,9 +580,9 @@ def run_learned(g, torch, args):
     out.update(runs)
     out["speedup_learned_mixed_ds_vs_plain_fp64"] = runs["plain_fp64"]["seconds"] / runs["learned_mixed_ds"]["seconds"]
     out["speedup_learned_fp64_vs_plain_fp64"] = runs["plain_fp64"]["seconds"] / runs["learned_fp64"]["seconds"]
-    for k in ("dsa_fp64", "dsa_mixed_ds", "learned_dsa_mixed_ds"):
+    for k in ("dsa_mixed_ds", "learned_dsa_mixed_ds"):
         out[f"speedup_{k}_vs_plain_fp64"] = runs["plain_fp64"]["seconds"] / runs[k]["seconds"]
-    out["dsa_cg_rtol"] = args.dsa_rtol
+    out["dsa_cg"] = {"rtol": args.dsa_rtol, "max_iter": args.dsa_max_cg}
     ctx.close()
     return out
 
@@ -716,6 +751,8 @@ def main():
     ap.add_argument("--no-small", action="store_true", help="skip the 16x16 p=1 S4 measurement")
     ap.add_argument("--dsa-rtol", type=float, default=1e-4,
                     help="relative residual of the conjugate-gradient DSA solve in the accelerated legs")
+    ap.add_argument("--dsa-max-cg", type=int, default=100, help="CG iteration cap of one DSA solve")
+    ap.add_argument("--no-dsa-thick", action="store_true", help="skip the optically thick DSA measurement")
     ap.add_argument("--learned-n", type=int, default=48, help="mesh size n^3 of the learned-predictor measurement")
     ap.add_argument("--launch", default="auto", choices=["auto", "levels", "dataflow"],
                     help="sweep schedule per form: the autotuner's choice, one launch per level, or one persistent dataflow launch")

@@ -169,7 +169,7 @@ sn_status sn_set_launch(sn_ctx* ctx, int mode, int blocks_per_sm);
 sn_status sn_set_spin_limit(sn_ctx* ctx, int64_t polls);
 
 /* Autotuner (no counterpart in the paper): times three source iterations of every candidate
- * schedule -- per-level launches, or the dataflow launch with 1, 2, 4 or the maximum resident
+ * schedule -- per-level launches, or the dataflow launch with 1, 2, 3, 4 or the maximum resident
  * CTAs per SM -- keeps the fastest via sn_set_launch and resets the iteration state
  * (sn_si_begin(ctx, NULL)).  mode_out / blocks_per_sm_out may be NULL. */
 sn_status sn_autotune(sn_ctx* ctx, int precision, int* mode_out, int* blocks_per_sm_out);

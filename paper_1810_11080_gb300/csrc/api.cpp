@@ -680,8 +680,8 @@ sn_status sn_set_spin_limit(sn_ctx* c, int64_t polls) {
 sn_status sn_autotune(sn_ctx* c, int precision, int* mode_out, int* blocks_per_sm_out) {
   if (!c) return SN_EINVAL;
   SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
-  const int cand[5][2] = {{SN_LAUNCH_LEVELS, 0}, {SN_LAUNCH_DATAFLOW, 1}, {SN_LAUNCH_DATAFLOW, 2},
-                          {SN_LAUNCH_DATAFLOW, 4}, {SN_LAUNCH_DATAFLOW, 0}};
+  const int cand[6][2] = {{SN_LAUNCH_LEVELS, 0}, {SN_LAUNCH_DATAFLOW, 1}, {SN_LAUNCH_DATAFLOW, 2},
+                          {SN_LAUNCH_DATAFLOW, 3}, {SN_LAUNCH_DATAFLOW, 4}, {SN_LAUNCH_DATAFLOW, 0}};
   float best = 1e30f;
   int bm = SN_LAUNCH_LEVELS, bb = 0;
   for (auto& cd : cand) {

@@ -333,8 +333,8 @@ sn_status sn_batch_source_iterate(sn_batch* b, double tol, int max_iter, int pre
 // the fastest (SI state is reset afterwards).
 sn_status sn_batch_tune(sn_batch* b, int precision, int* mode_out, int* blocks_per_sm_out) {
   if (!b) return SN_EINVAL;
-  const int cand[5][2] = {{SN_LAUNCH_LEVELS, 0}, {SN_LAUNCH_DATAFLOW, 1}, {SN_LAUNCH_DATAFLOW, 2},
-                          {SN_LAUNCH_DATAFLOW, 4}, {SN_LAUNCH_DATAFLOW, 0}};
+  const int cand[6][2] = {{SN_LAUNCH_LEVELS, 0}, {SN_LAUNCH_DATAFLOW, 1}, {SN_LAUNCH_DATAFLOW, 2},
+                          {SN_LAUNCH_DATAFLOW, 3}, {SN_LAUNCH_DATAFLOW, 4}, {SN_LAUNCH_DATAFLOW, 0}};
   float best = 1e30f;
   int bm = SN_LAUNCH_DATAFLOW, bb = 0;
   for (auto& cd : cand) {

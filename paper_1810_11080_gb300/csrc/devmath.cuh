@@ -95,6 +95,16 @@ __device__ inline void face_normal(int dim, int r, const double* geo, const doub
   tb[0] = (axis + 1) % dim;
   tb[1] = (axis + 2) % dim;
   const int ntan = dim - 1;
+  // 1D geometry basis values and derivatives on the face's own axes (each factor evaluated once;
+  // the products below use the same values as evaluating it per control point)
+  double lv[3][MAX_R + 1], ld[3][MAX_R + 1];
+  for (int k = 0; k < dim; ++k) {
+    if (k == axis) continue;
+    for (int a = 0; a < n1; ++a) {
+      lv[k][a] = dlagrange(geo, n1, a, xi[k]);
+      ld[k][a] = dlagrange_deriv(geo, n1, a, xi[k]);
+    }
+  }
   double T[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
   for (int m = 0; m < Nv; ++m) {
     int mi[3];
@@ -108,8 +118,8 @@ __device__ inline void face_normal(int dim, int r, const double* geo, const doub
       for (int k = 0; k < dim; ++k) {
         double fac;
         if (k == axis) fac = 1.0;
-        else if (k == b) fac = dlagrange_deriv(geo, n1, mi[k], xi[k]);
-        else fac = dlagrange(geo, n1, mi[k], xi[k]);
+        else if (k == b) fac = ld[k][mi[k]];
+        else fac = lv[k][mi[k]];
         dv = dv * fac;
       }
       for (int c = 0; c < dim; ++c) T[t][c] = T[t][c] + ctrl[m * dim + c] * dv;
@@ -146,6 +156,19 @@ __device__ inline double dot_omega(int dim, const double* om, const double* v) {
 __device__ inline double face_basis(int dim, const double* gll, int np1, int fn, double t0, double t1) {
   if (dim == 2) return dlagrange(gll, np1, fn, t0);
   return dlagrange(gll, np1, fn % np1, t0) * dlagrange(gll, np1, fn / np1, t1);
+}
+
+// All face-node basis values at once (out[fn], fn = i + np1 j): the same products as face_basis,
+// each 1D factor evaluated once.
+__device__ inline void face_basis_all(int dim, const double* gll, int np1, double t0, double t1, double* out) {
+  double l0[MAX_P + 1], l1[MAX_P + 1];
+  for (int a = 0; a < np1; ++a) l0[a] = dlagrange(gll, np1, a, t0);
+  if (dim == 2) {
+    for (int a = 0; a < np1; ++a) out[a] = l0[a];
+    return;
+  }
+  for (int a = 0; a < np1; ++a) l1[a] = dlagrange(gll, np1, a, t1);
+  for (int fn = 0; fn < np1 * np1; ++fn) out[fn] = l0[fn % np1] * l1[fn / np1];
 }
 
 }  // namespace sn

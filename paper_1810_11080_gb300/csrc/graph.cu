@@ -334,11 +334,11 @@ __device__ void rule3_blocks(const DevProblem& P, const R3Layout& L, const doubl
       double* pt = pts + lane * stride;
       pt[0] = (mg > 0.0 ? mg : 0.0) * w;
       pt[1] = (g > 0.0 ? g : 0.0) * w;
-      for (int k = 0; k < Nf; ++k) pt[2 + k] = face_basis(3, gll, np1, k, s0, s1);
+      face_basis_all(3, gll, np1, s0, s1, pt + 2);
       if (has_nbr) {
         double t0, t1;
         orient_map(3, code, s0, s1, t0, t1);
-        for (int k = 0; k < Nf; ++k) pt[2 + Nf + k] = face_basis(3, gll, np1, k, t0, t1);
+        face_basis_all(3, gll, np1, t0, t1, pt + 2 + Nf);
       }
     }
     __syncwarp();
@@ -402,11 +402,11 @@ __device__ void fill_points_brk(const DevProblem& P, const double* ctrl, int f, 
     double* o = sp + q * stride;
     o[0] = (mg > 0.0 ? mg : 0.0) * pd.w;
     o[1] = (g > 0.0 ? g : 0.0) * pd.w;
-    for (int i = 0; i < Nf; ++i) o[2 + i] = face_basis(P.dim, gll, np1, i, pd.s0, pd.s1);
+    face_basis_all(P.dim, gll, np1, pd.s0, pd.s1, o + 2);
     if (has_nbr) {
       double t0, t1;
       orient_map(P.dim, code, pd.s0, pd.s1, t0, t1);
-      for (int i = 0; i < Nf; ++i) o[2 + Nf + i] = face_basis(P.dim, gll, np1, i, t0, t1);
+      face_basis_all(P.dim, gll, np1, t0, t1, o + 2 + Nf);
     }
   }
   __syncwarp();
@@ -439,10 +439,10 @@ __device__ void fill_cache(const DevProblem& P, const double* ctrl, int f, int c
     w[0] = pd.w;
     for (int c = 0; c < dim; ++c) w[1 + c] = nv[c];
     double* o = sp + q * stride;
-    for (int i = 0; i < Nf; ++i) o[2 + i] = face_basis(dim, gll, np1, i, pd.s0, pd.s1);
+    face_basis_all(dim, gll, np1, pd.s0, pd.s1, o + 2);
     double t0, t1;
     orient_map(dim, code, pd.s0, pd.s1, t0, t1);
-    for (int i = 0; i < Nf; ++i) o[2 + Nf + i] = face_basis(dim, gll, np1, i, t0, t1);
+    face_basis_all(dim, gll, np1, t0, t1, o + 2 + Nf);
   }
   __syncwarp();
 }
@@ -825,9 +825,94 @@ __global__ void bdr_modes_kernel(DevProblem P, const int32_t* __restrict__ bface
   if (lane == 0 && mi > 0.0) atomicOr(&facecode[(int64_t)d * P.E + e], (mo > 0.0 ? MODE_MIXED : MODE_PURE) << (2 * f));
 }
 
+// 3D boundary faces: one warp per face, all directions.  The mode needs only whether the rule has
+// points with g < 0 (inflow) and with g > 0 (outflow): the block B = sum max(-/+g, 0) w phi phi has a
+// nonzero diagonal entry exactly then (the basis is a partition of unity).  Directions without roots
+// on the edges and on the composite rule's outer lines use the cached composite points' normals;
+// the others build the split rule's blocks.
+__global__ void bdr_modes3_kernel(DevProblem P, const int32_t* __restrict__ bface, int64_t n_bface,
+                                  uint32_t* facecode, int shm_per_warp) {
+  extern __shared__ double sh[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t bi = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (bi >= n_bface) return;
+  const int64_t e = bface[bi * 2];
+  const int f = bface[bi * 2 + 1];
+  const R3Layout L = r3_layout(P.r, P.K, P.nf, P.Nf);
+  const int Dg = L.Dg, nlines = P.K * P.nf, np = P.K * P.K * P.nf * P.nf, Nf = P.Nf;
+  double* ctrl = sh + (size_t)wib * shm_per_warp;
+  double* nbase = ctrl + P.Nv * 3;               // [np][3]
+  double* nE = nbase + np * 3;                   // [2][Dg+1][3]
+  double* nB = nE + 2 * (Dg + 1) * 3;            // [nlines][Dg+1][3]
+  double* r3 = nB + nlines * (Dg + 1) * 3;
+  copy_ctrl(P, e, ctrl, lane);
+  const double* geo = tabp(P, P.off_geo);
+  const double* t = tabp(P, P.off_glf_t);
+  const double brk0[4] = {0.0, 1.0, 1.0, 1.0};
+  for (int q = lane; q < np; q += 32) {
+    const PointData pd = face_point(P, brk0, q);
+    face_normal(3, P.r, geo, ctrl, f, pd.s0, pd.s1, nbase + 3 * q);
+  }
+  for (int k = lane; k < 2 * (Dg + 1); k += 32)
+    face_normal(3, P.r, geo, ctrl, f, (double)(k / (Dg + 1)), (double)(k % (Dg + 1)) / (double)Dg, nE + 3 * k);
+  for (int k = lane; k < nlines * (Dg + 1); k += 32) {
+    const int ob = k / (Dg + 1), kk = k % (Dg + 1), v = ob / P.nf, j = ob % P.nf;
+    const double lo = (double)v / (double)P.K, hi = (double)(v + 1) / (double)P.K;
+    face_normal(3, P.r, geo, ctrl, f, (double)kk / (double)Dg, lo + (hi - lo) * t[j], nB + 3 * k);
+  }
+  __syncwarp();
+  const int spec[6] = {0, 2, 2, 1, 2, 2};
+  for (int d = 0; d < P.M; ++d) {
+    const double om[3] = {P.omega[d * 3 + 0], P.omega[d * 3 + 1], P.omega[d * 3 + 2]};
+    bool root = false;
+    double rr[MAX_DG];
+    if (lane < 2) {
+      line_roots(Dg, om, nE + lane * (Dg + 1) * 3, rr);
+      for (int k = 0; k < Dg; ++k) root = root || rr[k] < 1.0;
+    }
+    for (int ob = lane; ob < nlines; ob += 32) {
+      line_roots(Dg, om, nB + ob * (Dg + 1) * 3, rr);
+      for (int k = 0; k < Dg; ++k) root = root || rr[k] < 1.0;
+    }
+    bool in = false, out = false;
+    if (!__any_sync(0xffffffffu, root)) {
+      for (int q = lane; q < np; q += 32) {
+        const double g = dot_omega(3, om, nbase + 3 * q);
+        in = in || (g < 0.0);
+        out = out || (g > 0.0);
+      }
+      in = __any_sync(0xffffffffu, in);
+      out = __any_sync(0xffffffffu, out);
+    } else {
+      rule3_blocks(P, L, ctrl, f, 0, false, om, nE, r3, lane, 2, spec);
+      double mi = 0.0, mo = 0.0;
+      for (int t2 = lane; t2 < Nf * Nf; t2 += 32) {
+        mi = fmax(mi, fabs(r3[L.o_acc + t2]));
+        mo = fmax(mo, fabs(r3[L.o_acc + Nf * Nf + t2]));
+      }
+      in = warp_max(mi) > 0.0;
+      out = warp_max(mo) > 0.0;
+      __syncwarp();
+    }
+    if (lane == 0 && in) atomicOr(&facecode[(int64_t)d * P.E + e], (out ? MODE_MIXED : MODE_PURE) << (2 * f));
+  }
+}
+
 cudaError_t launch_bdr_modes(const DevProblem& P, const int32_t* bface, int64_t n_bface, uint32_t* facecode,
                              cudaStream_t s) {
   if (n_bface == 0) return cudaSuccess;
+  if (P.dim == 3) {
+    const R3Layout L = r3_layout(P.r, P.K, P.nf, P.Nf);
+    const int np = P.K * P.K * P.nf * P.nf;
+    const int spw = P.Nv * 3 + np * 3 + 2 * (L.Dg + 1) * 3 + P.K * P.nf * (L.Dg + 1) * 3 + L.n;
+    int warps = 4;
+    while (warps > 1 && (size_t)warps * spw * sizeof(double) > 96 * 1024) warps >>= 1;
+    const size_t shmem = (size_t)warps * spw * sizeof(double);
+    cudaFuncSetAttribute(bdr_modes3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+    bdr_modes3_kernel<<<(unsigned)((n_bface + warps - 1) / warps), warps * 32, shmem, s>>>(P, bface, n_bface, facecode,
+                                                                                          spw);
+    return cudaGetLastError();
+  }
   const int spw = weights_shm_per_warp(P);
   int warps = 4;
   while (warps > 1 && (size_t)warps * spw * sizeof(double) > 96 * 1024) warps >>= 1;
