@@ -649,6 +649,17 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
     nbv[f] = valid ? Pb.nbr[e * 2 * DIM + f] : -1;
     fov[f] = valid ? (Pb.nbr_face[e * 2 * DIM + f] | (Pb.orient[e * 2 * DIM + f] << 8)) : 0;
   });
+  // Dataflow schedule with the whole matrix formed before the wait (2D): the inverse depends only
+  // on the element and the direction, so it is computed while the upwind pairs are still running
+  // and only the right-hand side, the two inverse applications and the residual follow the wait.
+  // (On per-level launches only one level runs ahead, and a longer pre-wait half bounds the level.)
+  constexpr bool GJ_PRE = DF && S::FACES_PRE;
+  int plk[N], myk;
+  float v[N];
+  if constexpr (GJ_PRE) {
+    static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = ah[decltype(jconst)::value]; });
+    gj32<N, W>(a, v, lane, row, plk, myk);
+  }
   if constexpr (DF) {
     wait_upwind<DIM>(Pb, sa, code, e, d, valid);
   } else {
@@ -730,10 +741,10 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
       if (mode == MODE_MIXED) ++mrank;
     });
   }
-  static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = ah[decltype(jconst)::value]; });
-  int plk[N], myk;
-  float v[N];
-  gj32<N, W>(a, v, lane, row, plk, myk);
+  if constexpr (!GJ_PRE) {
+    static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = ah[decltype(jconst)::value]; });
+    gj32<N, W>(a, v, lane, row, plk, myk);
+  }
   const float xhat = gj_apply<N, W>(v, rbh, plk);        // on the pivot lane of step myk
   // r = b - A xhat in double-single, four independent accumulation chains
   float rh[4] = {rbh, 0.0f, 0.0f, 0.0f}, rl[4] = {rbl, 0.0f, 0.0f, 0.0f};
