@@ -58,7 +58,7 @@ typedef enum {
 } sn_status;
 
 enum { SN_WEIGHT_UNITY = 0, SN_WEIGHT_FACE = 1, SN_WEIGHT_SIGINVFACE = 2 };
-enum { SN_PREC_FP64 = 0, SN_PREC_MIXED = 1, SN_PREC_MIXED_DS = 2 };
+enum { SN_PREC_FP64 = 0, SN_PREC_MIXED = 1, SN_PREC_MIXED_DS = 2, SN_PREC_FP64_INV = 3 };
 enum { SN_LAUNCH_LEVELS = 0, SN_LAUNCH_DATAFLOW = 1 };
 
 typedef struct {
@@ -174,6 +174,18 @@ sn_status sn_set_spin_limit(sn_ctx* ctx, int64_t polls);
  * (sn_si_begin(ctx, NULL)).  mode_out / blocks_per_sm_out may be NULL. */
 sn_status sn_autotune(sn_ctx* ctx, int precision, int* mode_out, int* blocks_per_sm_out);
 
+/* Stored local inverses of the SN_PREC_FP64_INV form (no counterpart in the paper, which
+ * factors during the sweep): the left-hand side of eq. 21 for direction d and element e,
+ * G + F_e + M_t, is the same in every source iteration, so its inverse is formed once, by
+ * Gauss-Jordan elimination with partial pivoting in FP64, for all (direction, element) pairs in
+ * one launch, and kept in a device buffer of n_dir * n_elem * N * N doubles owned by the context.
+ * sn_prepare_inverse (re)forms them now; *ms (may be NULL) receives the device time of that
+ * work.  Valid after sn_build_graph; new materials or a new graph make the stored inverses
+ * stale, and the next sweep of the form forms them again.  sn_release_inverse frees the buffer.
+ * Errors: SN_ESTATE (no graph), SN_ENOMEM (the buffer does not fit in device memory). */
+sn_status sn_prepare_inverse(sn_ctx* ctx, float* ms);
+sn_status sn_release_inverse(sn_ctx* ctx);
+
 /* Copy the graph out (valid after sn_build_graph).
  *   *n_removed receives the number of removed arcs; if removed != NULL and cap >= that number,
  *   removed [k][3] receives (direction, e, e') rows sorted ascending: e depends on e' and the
@@ -193,7 +205,10 @@ sn_status sn_get_graph(sn_ctx* ctx, int64_t* n_removed, int32_t* removed, int64_
  *   one refinement step whose residual is formed in FP64.  SN_PREC_MIXED_DS: as SN_PREC_MIXED
  *   but the matrix row and the residual are formed in double-single arithmetic (pairs of FP32
  *   values with error-free products and sums, ~2^-48 relative) on the FP32 pipe; only the
- *   right-hand side and the final sum are FP64.
+ *   right-hand side and the final sum are FP64.  SN_PREC_FP64_INV: FP64; the inverse of every
+ *   (direction, element) matrix G + F_e + M_t, which does not change between iterations, is
+ *   formed once (sn_prepare_inverse, or on the first sweep of this form) and kept in device
+ *   memory (n_dir * n_elem * N * N doubles); a sweep assembles the right-hand side and applies it.
  * Synchronises the stream before returning when any pointer is a host pointer. */
 sn_status sn_sweep(sn_ctx* ctx, const double* phi_in, const double* psi_old, double* psi_new,
                    int precision);
@@ -252,7 +267,9 @@ sn_status sn_batch_tune(sn_batch* batch, int precision, int* mode_out, int* bloc
  * problem. */
 sn_status sn_batch_si_begin(sn_batch* batch, const double* const* phi0);
 /* One source iteration of every problem; residuals [n_problems] (may be NULL) receive each
- * problem's relative scalar-flux change; *ms_sweep (may be NULL) the device time of the step. */
+ * problem's relative scalar-flux change; *ms_sweep (may be NULL) the device time of the step.
+ * With SN_PREC_FP64_INV the first step forms every member's stored inverses that are missing
+ * (sn_prepare_inverse) before it sweeps. */
 sn_status sn_batch_si_step(sn_batch* batch, int precision, double* residuals, float* ms_sweep);
 /* Steps until every problem's relative change is below tol; iters [n] receives the first
  * iteration at which each problem reached it (-1 if never), residuals [n] the last change.

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libsnsweep.so")
 
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENOTCONVERGED, SN_EMESH, SN_ESTATE = range(8)
 SN_WEIGHT_UNITY, SN_WEIGHT_FACE, SN_WEIGHT_SIGINVFACE = 0, 1, 2
-SN_PREC_FP64, SN_PREC_MIXED, SN_PREC_MIXED_DS = 0, 1, 2
+SN_PREC_FP64, SN_PREC_MIXED, SN_PREC_MIXED_DS, SN_PREC_FP64_INV = 0, 1, 2, 3
 SN_LAUNCH_LEVELS, SN_LAUNCH_DATAFLOW = 0, 1
 WEIGHTING = {"unity": 0, "face": 1, "siginvface": 2}
 
@@ -29,7 +29,7 @@ EXPORTED = ["sn_create", "sn_destroy", "sn_last_error", "sn_set_mesh", "sn_set_d
             "sn_mlp_forward", "sn_mlp_grad", "sn_mlp_train", "sn_predictor_features", "sn_predictor_init_targets",
             "sn_predictor_corr_data", "sn_source_iterate_learned", "sn_predictor_initial_phi",
             "sn_quadrature_level_symmetric", "sn_set_spin_limit", "sn_set_dsa", "sn_dsa_correction",
-            "sn_dsa_last_iters"]
+            "sn_dsa_last_iters", "sn_prepare_inverse", "sn_release_inverse"]
 
 
 class sn_graph_stats(ctypes.Structure):
@@ -116,6 +116,8 @@ def load(path=LIB_PATH):
         "sn_set_dsa": (I, [P, I, D, I]),
         "sn_dsa_correction": (I, [P, P, P, P, ctypes.POINTER(I)]),
         "sn_dsa_last_iters": (ctypes.c_int32, [P]),
+        "sn_prepare_inverse": (I, [P, ctypes.POINTER(ctypes.c_float)]),
+        "sn_release_inverse": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -287,6 +289,15 @@ class Context:
 
     def sn_dsa_last_iters(self):
         return self._lib.sn_dsa_last_iters(self._c)
+
+    def sn_prepare_inverse(self):
+        """Forms the stored local inverses of the SN_PREC_FP64_INV form; returns device ms."""
+        ms = ctypes.c_float()
+        self._check(self._lib.sn_prepare_inverse(self._c, ctypes.byref(ms)))
+        return ms.value
+
+    def sn_release_inverse(self):
+        return self._check(self._lib.sn_release_inverse(self._c))
 
     def sn_set_spin_limit(self, polls):
         return self._check(self._lib.sn_set_spin_limit(self._c, int(polls)))

@@ -46,6 +46,7 @@ def build(verbose=False, extra_nvcc=()):
         "scc.cu": ["-fmad=false"],
         "dsa.cu": [],
         "sweep.cu": [],
+        "sweep_inv.cu": [],
         "noalloc.cu": [],
         "batch.cu": [],
         "mlp.cu": [],

@@ -71,6 +71,8 @@ void free_dsa(sn_ctx* c) {
 
 void free_graph_state(sn_ctx* c) {
   free_dsa(c);
+  dfree(c->d_inv);
+  c->inv_ready = false;
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   c->graphs.clear();
   dfree(c->d_facecode);
@@ -727,6 +729,40 @@ sn_status sn_get_graph(sn_ctx* c, int64_t* n_removed, int32_t* removed, int64_t 
 
 namespace {
 
+// Stored inverses of the SN_PREC_FP64_INV form: allocated once, formed for every pair.
+sn_status form_inverse(sn_ctx* c, float* ms) {
+  const size_t n = (size_t)c->M * c->E * c->N * c->N;
+  if (!c->d_inv) {
+    if (dalloc(c->d_inv, n) != cudaSuccess) {
+      cudaGetLastError();
+      c->d_inv = nullptr;
+      set_err(c, "stored inverses: " + std::to_string(n * 8) + " bytes do not fit in device memory");
+      return SN_ENOMEM;
+    }
+  }
+  c->inv_ready = false;
+  if (ms && !c->ev_a) {
+    SN_CUDA(c, cudaEventCreate(&c->ev_a));
+    SN_CUDA(c, cudaEventCreate(&c->ev_b));
+  }
+  DevProblem P = c->dev();
+  SweepArgs sa{c->d_facecode, c->d_mixed_off, c->d_mixedB, c->d_mixedB32, c->d_mixedB32lo, c->d_src,
+               nullptr, nullptr, nullptr, nullptr, nullptr,
+               nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, c->d_inv};
+  if (ms) SN_CUDA(c, cudaEventRecord(c->ev_a, c->stream));
+  SN_CUDA(c, launch_invert(P, sa, c->stream));
+  c->launches++;
+  if (ms) {
+    SN_CUDA(c, cudaEventRecord(c->ev_b, c->stream));
+    SN_CUDA(c, cudaEventSynchronize(c->ev_b));
+    SN_CUDA(c, cudaEventElapsedTime(ms, c->ev_a, c->ev_b));
+  } else {
+    SN_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  c->inv_ready = true;
+  return SN_OK;
+}
+
 // One sweep: either one launch per level, or one persistent dataflow launch (completion flags
 // and queue head cleared first).  Replayed from a captured CUDA graph when the stream allows
 // capture (not the legacy default stream).
@@ -736,9 +772,13 @@ sn_status run_levels(sn_ctx* c, int prec, const double* psi_old, double* psi_new
   const int64_t total = c->level_off.back();
   int* err = reinterpret_cast<int*>(c->d_red + 2);
   unsigned long long* head = c->d_red + 3;
+  if (prec == SN_PREC_FP64_INV && !c->inv_ready) {      // outside any capture: it synchronises
+    sn_status st = form_inverse(c, nullptr);
+    if (st != SN_OK) return st;
+  }
   SweepArgs sa{c->d_facecode, c->d_mixed_off, c->d_mixedB, c->d_mixedB32, c->d_mixedB32lo, c->d_src,
                psi_old, psi_new, c->d_done, err, c->d_pairs,
-               c->d_srch, c->d_srcl, nullptr, nullptr, nullptr, nullptr, c->spin_limit};
+               c->d_srch, c->d_srcl, nullptr, nullptr, nullptr, nullptr, c->spin_limit, c->d_inv};
   // (hi, lo) splits of the two iterates: the context's own buffers, or scratch for caller buffers
   bool convert_old = false;
   const size_t npsi = (size_t)c->M * c->E * c->N;
@@ -844,12 +884,28 @@ const double* stage_in(sn_ctx* c, const double* p, size_t n, int slot, sn_status
 
 }  // namespace
 
+sn_status sn_prepare_inverse(sn_ctx* c, float* ms) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
+  cudaSetDevice(c->device);
+  return form_inverse(c, ms);
+}
+
+sn_status sn_release_inverse(sn_ctx* c) {
+  if (!c) return SN_EINVAL;
+  cudaSetDevice(c->device);
+  SN_CUDA(c, cudaStreamSynchronize(c->stream));
+  dfree(c->d_inv);
+  c->inv_ready = false;
+  return SN_OK;
+}
+
 sn_status sn_sweep(sn_ctx* c, const double* phi_in, const double* psi_old, double* psi_new, int precision) {
   if (!c) return SN_EINVAL;
   SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
   SN_REQ(c, phi_in && psi_old && psi_new, SN_EINVAL, "null array");
   SN_REQ(c, (const void*)psi_old != (const void*)psi_new, SN_EINVAL, "psi_new must not alias psi_old");
-  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_MIXED_DS, SN_EINVAL, "unknown precision");
+  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_FP64_INV, SN_EINVAL, "unknown precision");
   cudaSetDevice(c->device);
   const size_t npsi = (size_t)c->M * c->E * c->N, nphi = (size_t)c->E * c->N;
   sn_status st;
@@ -994,7 +1050,7 @@ sn_status sn_si_begin(sn_ctx* c, const double* phi0) {
 sn_status sn_si_step(sn_ctx* c, int precision, double* residual, float* ms_sweep) {
   if (!c) return SN_EINVAL;
   SN_REQ(c, c->graph_ready && c->si_ready, SN_ESTATE, "sn_si_begin first");
-  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_MIXED_DS, SN_EINVAL, "unknown precision");
+  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_FP64_INV, SN_EINVAL, "unknown precision");
   cudaSetDevice(c->device);
   cudaStream_t s = c->stream;
   if (ms_sweep && !c->ev_a) {
@@ -1055,7 +1111,7 @@ sn_status sn_source_iterate(sn_ctx* c, double tol, int max_iter, int precision, 
   if (!c) return SN_EINVAL;
   SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
   SN_REQ(c, max_iter >= 1 && tol > 0.0, SN_EINVAL, "max_iter >= 1 and tol > 0 required");
-  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_MIXED_DS, SN_EINVAL, "unknown precision");
+  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_FP64_INV, SN_EINVAL, "unknown precision");
   auto t0 = std::chrono::steady_clock::now();
   sn_status st = sn_si_begin(c, phi0);
   if (st != SN_OK) return st;

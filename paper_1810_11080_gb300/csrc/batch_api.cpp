@@ -41,6 +41,8 @@ struct sn_batch {
   std::vector<unsigned long long> h_red;
   std::map<int, cudaGraphExec_t> graphs;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<SweepArgs> h_args[2];     // host copies of the argument tables
+  bool inv_linked = false;              // d_args carry every problem's stored inverses
 };
 
 namespace {
@@ -157,6 +159,7 @@ sn_status sn_batch_create(sn_batch** out, int n_problems, sn_ctx* const* problem
     args1[k].psi_old_l = c->d_psil[1];
     args1[k].psi_new_h = c->d_psih[0];
     args1[k].psi_new_l = c->d_psil[0];
+    args0[k].inv = args1[k].inv = nullptr;
     m0[k] = MomentArgs{c->d_psi[1], b->phiA[k], b->phiB[k], c->d_src, c->d_srch, c->d_srcl};
     m1[k] = MomentArgs{c->d_psi[0], b->phiB[k], b->phiA[k], c->d_src, c->d_srch, c->d_srcl};
   }
@@ -186,6 +189,8 @@ sn_status sn_batch_create(sn_batch** out, int n_problems, sn_ctx* const* problem
     return fail(SN_ENOMEM);
   if (cudaEventCreate(&b->ev[0]) != cudaSuccess || cudaEventCreate(&b->ev[1]) != cudaSuccess) return fail(SN_ECUDA);
   b->h_red.assign(2 * (size_t)n + 2, 0);
+  b->h_args[0] = args0;
+  b->h_args[1] = args1;
   *out = b;
   return SN_OK;
 }
@@ -252,8 +257,31 @@ sn_status sn_batch_si_begin(sn_batch* b, const double* const* phi0) {
 sn_status sn_batch_si_step(sn_batch* b, int precision, double* residuals, float* ms_sweep) {
   if (!b) return SN_EINVAL;
   SB_REQ(b, b->ready, SN_ESTATE, "sn_batch_si_begin first");
-  SB_REQ(b, precision >= SN_PREC_FP64 && precision <= SN_PREC_MIXED_DS, SN_EINVAL, "unknown precision");
+  SB_REQ(b, precision >= SN_PREC_FP64 && precision <= SN_PREC_FP64_INV, SN_EINVAL, "unknown precision");
   SB_CUDA(b, cudaSetDevice(b->device));
+  if (precision == SN_PREC_FP64_INV) {
+    // every problem's stored inverses formed (once), and their addresses in the argument tables
+    bool moved = !b->inv_linked;
+    for (int k = 0; k < b->n; ++k) {
+      sn_ctx* c = b->ctx[k];
+      if (!c->inv_ready) {
+        sn_status st = sn_prepare_inverse(c, nullptr);
+        if (st != SN_OK) {
+          b->err = std::string("problem ") + std::to_string(k) + ": " + c->err;
+          return st;
+        }
+      }
+      if (b->h_args[0][k].inv != c->d_inv) moved = true;
+      b->h_args[0][k].inv = b->h_args[1][k].inv = c->d_inv;
+    }
+    if (moved) {
+      SB_CUDA(b, cudaStreamSynchronize(b->stream));
+      for (int q = 0; q < 2; ++q)
+        SB_CUDA(b, cudaMemcpy(b->d_args[q], b->h_args[q].data(), b->h_args[q].size() * sizeof(SweepArgs),
+                              cudaMemcpyHostToDevice));
+      b->inv_linked = true;
+    }
+  }
   const int key = precision * 16 + b->launch_mode * 2 + b->parity;
   if (ms_sweep) SB_CUDA(b, cudaEventRecord(b->ev[0], b->stream));
   if (b->stream == nullptr) {

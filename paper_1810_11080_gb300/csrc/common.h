@@ -115,6 +115,7 @@ struct SweepArgs {
   float* psi_new_h;
   float* psi_new_l;
   long long spin_limit;       // dataflow schedule: polls of one upwind flag before giving up (<= 0: SPIN_LIMIT)
+  double* inv;                // [M][E][N][N] stored local inverses (SN_PREC_FP64_INV) or null
 };
 
 // Per-problem pointers of the fused moment / source kernel in a batch.
@@ -167,6 +168,8 @@ cudaError_t launch_sweep_level(const DevProblem& P, int precision, const int32_t
                                const SweepArgs& sa, cudaStream_t s);
 cudaError_t launch_sweep_flow(const DevProblem& P, int precision, const int32_t* pairs, int64_t count,
                               const SweepArgs& sa, unsigned long long* head, int blocks_per_sm, cudaStream_t s);
+// Forms sa.inv for every (direction, element) pair (sweep_inv.cu).
+cudaError_t launch_invert(const DevProblem& P, const SweepArgs& sa, cudaStream_t s);
 
 }  // namespace sn
 
@@ -238,6 +241,9 @@ struct sn_ctx {
   double dsa_rtol = 1e-4;
   int dsa_max_iter = 500;
   int dsa_last_iters = 0;
+  // stored local inverses (SN_PREC_FP64_INV)
+  double* d_inv = nullptr;
+  bool inv_ready = false;
   int launch_mode = 0;                   // SN_LAUNCH_LEVELS / SN_LAUNCH_DATAFLOW
   long long spin_limit = 0;              // dataflow wait limit (0: the kernels' default)
   int blocks_per_sm = 0;                 // dataflow grid: 0 = occupancy limit

@@ -26,7 +26,7 @@ def _status(fn, *a, **k):
     return g.SN_OK
 
 
-@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("prec", [0, 2, 3])
 def test_dataflow_wait_limit_gives_timeout_then_recovers(prec):
     prob = si.make_config("2d_smooth_q3_p3_s8", n=24)
     ctx, _ = gpu_ctx(prob, "face")
@@ -108,6 +108,9 @@ def test_invalid_inputs():
     assert _status(ctx.sn_set_discretization, 4, 2) == g.SN_EINVAL
     assert _status(ctx.sn_build_graph, 3, 10) == g.SN_EINVAL
     assert _status(ctx.sn_set_launch, 7, 0) == g.SN_EINVAL
+    ctx.sn_build_graph("face", 10)
+    z = np.zeros((len(prob.w), prob.mesh.n_elem, 4))
+    assert _status(ctx.sn_sweep, np.zeros((prob.mesh.n_elem, 4)), z, z.copy(), 4) == g.SN_EINVAL
 
 
 def test_calls_out_of_order():
@@ -120,6 +123,7 @@ def test_calls_out_of_order():
     assert _status(ctx.sn_sweep, np.zeros((E, N)), z, z.copy(), 0) == g.SN_ESTATE   # before the graph
     assert _status(ctx.sn_si_begin, None) == g.SN_ESTATE
     assert _status(ctx.sn_autotune, 0) == g.SN_ESTATE
+    assert _status(ctx.sn_prepare_inverse) == g.SN_ESTATE
     ctx.sn_build_graph("face", 10)
     assert _status(ctx.sn_si_step, 0) == g.SN_ESTATE                            # before sn_si_begin
     ctx.sn_si_begin(None)

@@ -50,19 +50,23 @@ def test_graph_bit_exact(case, weighting):
     assert stats["max_level"] == int(G["levels"].max())
 
 
+# prec 0: FP64 factorisation during the sweep; prec 3: FP64 with stored local inverses
+@pytest.mark.parametrize("prec", [0, 3])
 @pytest.mark.parametrize("case", list(CASES))
-def test_fp64_sweep_parity(case):
+def test_fp64_sweep_parity(case, prec):
     prob = CASES[case]()
     disc, G = oracle_graph(prob, "face")
     ctx, _ = gpu_ctx(prob, "face")
     phi, psi_old = random_state(prob, seed=1)
     ref = Sweeper(disc, G).sweep(phi, psi_old)
     out = np.zeros_like(psi_old)
-    ctx.sn_sweep(phi, psi_old, out, 0)
+    ctx.sn_sweep(phi, psi_old, out, prec)
+    print(f"{case} prec={prec}: rel L2 {rel_l2(out, ref):.3e}")
     assert rel_l2(out, ref) <= FP64_TOL, rel_l2(out, ref)
 
 
-def test_fp64_sweep_parity_with_direction_sources_and_inflow():
+@pytest.mark.parametrize("prec", [0, 3])
+def test_fp64_sweep_parity_with_direction_sources_and_inflow(prec):
     prob = si.make_config("2d_sine_q2_p1_s4", n=6, p=3)
     prob, _f, _fac = annulus_mms(prob)
     disc, G = oracle_graph(prob, "face")
@@ -70,8 +74,34 @@ def test_fp64_sweep_parity_with_direction_sources_and_inflow():
     phi, psi_old = random_state(prob, seed=2)
     ref = Sweeper(disc, G).sweep(phi, psi_old)
     out = np.zeros_like(psi_old)
-    ctx.sn_sweep(phi, psi_old, out, 0)
+    ctx.sn_sweep(phi, psi_old, out, prec)
     assert rel_l2(out, ref) <= FP64_TOL
+
+
+def test_stored_inverses_follow_new_materials():
+    """New cross sections invalidate the stored inverses: the next sweep forms them again, and
+    a released buffer is formed again on demand."""
+    prob = si.make_config("2d_smooth_q3_p3_s8", n=6)
+    disc, G = oracle_graph(prob, "face")
+    ctx, _ = gpu_ctx(prob, "face")
+    phi, psi_old = random_state(prob, seed=4)
+    out = np.zeros_like(psi_old)
+    ms = ctx.sn_prepare_inverse()
+    assert ms > 0.0
+    ctx.sn_sweep(phi, psi_old, out, 3)
+    assert rel_l2(out, Sweeper(disc, G).sweep(phi, psi_old)) <= FP64_TOL
+    prob.sigma_t = prob.sigma_t * 1.7
+    prob.sigma_s = prob.sigma_s * 1.3
+    disc2, G2 = oracle_graph(prob, "face")
+    ctx.sn_set_materials(prob.sigma_t, prob.sigma_s, prob.q, prob.q_dir, prob.psi_inc)
+    ctx.sn_build_graph("face", 10)
+    ctx.sn_sweep(phi, psi_old, out, 3)
+    ref2 = Sweeper(disc2, G2).sweep(phi, psi_old)
+    assert rel_l2(out, ref2) <= FP64_TOL
+    ctx.sn_release_inverse()
+    out2 = np.zeros_like(psi_old)
+    ctx.sn_sweep(phi, psi_old, out2, 3)
+    assert np.array_equal(out2, out)
 
 
 @pytest.mark.parametrize("prec", [1, 2])
@@ -189,7 +219,7 @@ def test_mixed_source_iteration_reaches_same_tolerance(case, prec):
     assert rel_l2(phi, ref["phi"]) <= 1e-6          # 1e-8 residual: the iteration error dominates
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("case", ["2d_sine_16", "2d_smooth_10_p3_s8", "3d_twist_4_p2_s8", "2d_reoriented_6_p2",
                                   "3d_twist_3_p1_s4_reoriented", "2d_sine_8_p2_strong"])
 def test_dataflow_schedule_matches_level_schedule(case, prec):
@@ -208,7 +238,7 @@ def test_dataflow_schedule_matches_level_schedule(case, prec):
         assert np.array_equal(out, ref), (bps, rel_l2(out, ref))
 
 
-@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("prec", [0, 2, 3])
 def test_dataflow_source_iteration(prec):
     import paper_1810_11080_gb300 as g
     prob = CASES["3d_twist_4_p2_s8"]()
@@ -256,7 +286,7 @@ def bench_3d():
 
 
 @pytest.mark.parametrize("launch", ["levels", "dataflow"])
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("shape", ["bench_2d", "bench_3d"])
 def test_benchmark_size_sweep_parity(shape, prec, launch, request):
     import paper_1810_11080_gb300 as g
@@ -266,9 +296,9 @@ def test_benchmark_size_sweep_parity(shape, prec, launch, request):
     ctx.sn_sweep(phi, psi_old, out, prec)
     assert np.all(np.isfinite(out))
     o, r = out[dirs], ref[dirs]
-    if prec == 0:
+    if prec in (0, 3):
         err = rel_l2(o, r)
-        print(f"{shape} fp64 {launch}: rel L2 {err:.3e}")
+        print(f"{shape} fp64 (prec={prec}) {launch}: rel L2 {err:.3e}")
         assert err <= FP64_TOL, err
     else:
         check_mixed(o, r, f"{shape} prec={prec} {launch}")
