@@ -45,12 +45,14 @@ def peaks():
 # microbenchmark bench_fp_peaks.cu: 1.20 TFLOP/s FP64 and 75.0 TFLOP/s FP32.
 FP64_PEAK_TFLOPS = 1.20
 
-DTYPES = {"fp64": "f64", "mixed": "f32+f64", "mixed_ds": "f32+f32x2+f64", "fp64_inv": "f64"}
+DTYPES = {"fp64": "f64", "mixed": "f32+f64", "mixed_ds": "f32+f32x2+f64", "fp64_inv": "f64", "ds_inv": "f32x2+f64"}
 PRECISION_DESC = {
     "fp64": "FP64 assembly, LU and solve",
     "mixed": "FP32 assembly and LU, one refinement with an FP64 residual",
     "mixed_ds": "FP32 LU, one refinement; row and residual in double-single (FP32 pairs), FP64 right-hand side",
     "fp64_inv": "FP64; local inverses formed once per problem (Gauss-Jordan, partial pivoting), applied each sweep",
+    "ds_inv": "local inverses formed once per problem in FP64, stored as FP32 (hi, lo) pairs and applied in "
+              "double-single arithmetic each sweep",
 }
 
 
@@ -270,7 +272,7 @@ def run_gpu(args):
                           sched["blocks_per_sm"])
 
     forms = {"fp64": g.SN_PREC_FP64, "mixed": g.SN_PREC_MIXED, "mixed_ds": g.SN_PREC_MIXED_DS,
-             "fp64_inv": g.SN_PREC_FP64_INV}
+             "fp64_inv": g.SN_PREC_FP64_INV, "ds_inv": g.SN_PREC_DS_INV}
     if args.quick and args.quick_forms:
         forms = {k: forms[k] for k in args.quick_forms.split(",")}
     meas = {k: timed_steps(v) for k, v in forms.items()}
@@ -310,11 +312,11 @@ def run_gpu(args):
     # ---- time to a 1e-8 relative scalar-flux change, full solves from phi = 0
     tts = {}
     phis = {}
-    inv_ms = ctx.sn_prepare_inverse() if "fp64_inv" in forms else None
+    inv_ms = {k: ctx.sn_prepare_inverse(forms[k]) for k in ("fp64_inv", "ds_inv") if k in forms}
     for k, prec in forms.items():
         phis[k] = np.zeros((E, N))
         use_schedule(meas[k]["schedule"])
-        if prec == g.SN_PREC_FP64_INV:
+        if prec in (g.SN_PREC_FP64_INV, g.SN_PREC_DS_INV):
             ctx.sn_release_inverse()         # formed again inside the timed solve
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -323,7 +325,7 @@ def run_gpu(args):
     diffs = {k: float(np.linalg.norm(phis[k] - phis["fp64"]) / np.linalg.norm(phis["fp64"])) for k in forms}
     # the same solves with diffusion synthetic acceleration after every sweep
     dsa = {}
-    for k in ("fp64", "mixed_ds", "fp64_inv"):
+    for k in ("fp64", "mixed_ds", "ds_inv"):
         phi_k = np.zeros((E, N))
         use_schedule(meas[k]["schedule"])
         ctx.sn_set_dsa(True, args.dsa_rtol, args.dsa_max_cg)
@@ -342,11 +344,11 @@ def run_gpu(args):
     work = alg_work(dim, prob.p)
 
     def roofline(kind, m):
-        pcode = {"fp64": 0, "mixed": 1, "mixed_ds": 2, "fp64_inv": 3}[kind]
+        pcode = {"fp64": 0, "mixed": 1, "mixed_ds": 2, "fp64_inv": 3, "ds_inv": 4}[kind]
         flow = m["schedule"]["mode"] == "dataflow"
         kname = (f"sweep_flow_kernel<{dim},{prob.p},{pcode}> (one persistent launch per sweep)" if flow else
                  f"sweep_level_kernel<{dim},{prob.p},{pcode}> (all level launches of one sweep)")
-        if kind == "fp64_inv":
+        if kind in ("fp64_inv", "ds_inv"):
             sweep_s = m["sweep_ms_per_step"] / 1e3
             ib = inv_alg_bytes(dim, prob.p)
             ach = ib * updates / sweep_s / 1e9
@@ -401,20 +403,23 @@ def run_gpu(args):
         "mixed_ds": form_line("mixed_ds"),
         "time_to_1e-8": {"fp64_s": tts["fp64"]["seconds"], "mixed_ds_s": tts["mixed_ds"]["seconds"],
                          "mixed_s": tts["mixed"]["seconds"], "fp64_inv_s": tts["fp64_inv"]["seconds"],
+                         "ds_inv_s": tts["ds_inv"]["seconds"],
                          "speedup_mixed_ds_vs_fp64": tts["fp64"]["seconds"] / tts["mixed_ds"]["seconds"],
                          "speedup_fp64_inv_vs_fp64": tts["fp64"]["seconds"] / tts["fp64_inv"]["seconds"],
+                         "speedup_ds_inv_vs_fp64": tts["fp64"]["seconds"] / tts["ds_inv"]["seconds"],
                          "fp64_iters": tts["fp64"]["iters"], "mixed_ds_iters": tts["mixed_ds"]["iters"],
-                         "fp64_inv_iters": tts["fp64_inv"]["iters"],
+                         "fp64_inv_iters": tts["fp64_inv"]["iters"], "ds_inv_iters": tts["ds_inv"]["iters"],
                          "phi_rel_l2_mixed_ds_vs_fp64": diffs["mixed_ds"],
                          "phi_rel_l2_fp64_inv_vs_fp64": diffs["fp64_inv"],
-                         "fp64_inv_includes": "allocation and formation of the stored inverses"},
-        "fp64_inv": {**form_line("fp64_inv"), "inverse_ms": inv_ms,
-                     "inverse_bytes": int(M) * int(E) * N * N * 8},
+                         "phi_rel_l2_ds_inv_vs_fp64": diffs["ds_inv"],
+                         "stored_inverse_forms_include": "allocation and formation of the stored inverses"},
+        "stored_inverses": {"inverse_ms": inv_ms, "inverse_bytes": int(M) * int(E) * N * N * 8,
+                            "fp64_inv": form_line("fp64_inv"), "ds_inv": form_line("ds_inv")},
         "forms": {k: form_line(k) for k in forms},
         "dsa": {"cg_rtol": args.dsa_rtol, "cg_max_iter": args.dsa_max_cg, **dsa,
                 "speedup_fp64_dsa_vs_fp64": tts["fp64"]["seconds"] / dsa["fp64"]["seconds"],
                 "speedup_mixed_ds_dsa_vs_fp64": tts["fp64"]["seconds"] / dsa["mixed_ds"]["seconds"],
-                "speedup_fp64_inv_dsa_vs_fp64": tts["fp64"]["seconds"] / dsa["fp64_inv"]["seconds"]},
+                "speedup_ds_inv_dsa_vs_fp64": tts["fp64"]["seconds"] / dsa["ds_inv"]["seconds"]},
         "graph": {"build_s": t_graph, "removed": gstats["n_removed"], "levels": gstats["max_level"] + 1,
                   "max_scc": gstats["max_scc"], "mixed_faces": gstats["n_mixed_faces"],
                   "graph_ms": {k: gstats[k] for k in ("ms_geometry", "ms_weights", "ms_fas", "ms_levels")}},
@@ -451,7 +456,7 @@ def run_small(g, torch, args):
     res = {"workload": "16x16 Q2 quads, x' = x + 0.05 sin(2 pi x) sin(2 pi y) on both coordinates, p=1, S4 (12 dirs), "
                        "sigma_t=1, sigma_s=0.5, q=1", "updates_per_sweep": ups, "levels": levels}
     for name, prec in (("fp64", g.SN_PREC_FP64), ("mixed_ds", g.SN_PREC_MIXED_DS),
-                       ("fp64_inv", g.SN_PREC_FP64_INV)):
+                       ("fp64_inv", g.SN_PREC_FP64_INV), ("ds_inv", g.SN_PREC_DS_INV)):
         mode, bps = ctx.sn_autotune(prec)
         for _ in range(args.warmup):
             ctx.sn_si_step(prec)
@@ -461,7 +466,7 @@ def run_small(g, torch, args):
             _, ms = ctx.sn_si_step(prec, time_sweep=True)
             tot += ms
         phi = np.zeros((E, N))
-        if prec == g.SN_PREC_FP64_INV:
+        if prec in (g.SN_PREC_FP64_INV, g.SN_PREC_DS_INV):
             ctx.sn_release_inverse()         # formed again inside the timed solve
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -509,7 +514,8 @@ def run_3d(g, torch, args):
     ups = prob.mesh.n_elem * len(prob.w)
     E, N = prob.mesh.n_elem, 27
     pk, pk_kind = peaks()
-    for name, prec in (("mixed_ds", g.SN_PREC_MIXED_DS), ("fp64", g.SN_PREC_FP64), ("fp64_inv", g.SN_PREC_FP64_INV)):
+    for name, prec in (("mixed_ds", g.SN_PREC_MIXED_DS), ("fp64", g.SN_PREC_FP64), ("fp64_inv", g.SN_PREC_FP64_INV),
+                       ("ds_inv", g.SN_PREC_DS_INV)):
         mode, bps = ctx.sn_autotune(prec)
         for _ in range(args.warmup):
             ctx.sn_si_step(prec)
@@ -520,15 +526,16 @@ def run_3d(g, torch, args):
             tot += ms
         phi = np.zeros((E, N))
         inv_ms = None
-        if prec == g.SN_PREC_FP64_INV:
-            inv_ms = ctx.sn_prepare_inverse()
+        stored = prec in (g.SN_PREC_FP64_INV, g.SN_PREC_DS_INV)
+        if stored:
+            inv_ms = ctx.sn_prepare_inverse(prec)
             ctx.sn_release_inverse()         # formed again inside the timed solve
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         r = ctx.sn_source_iterate(1e-8, 3000, prec, phi_out=phi)
         rate = ups * steps / (tot / 1e3)
         work = alg_work(3, prob.p)
-        if prec == g.SN_PREC_FP64_INV:
+        if stored:
             ib = inv_alg_bytes(3, prob.p)
             roof = {"bound": "hbm", "achieved_gbs": rate * ib / 1e9, "peak_gbs": pk["hbm_gbs"],
                     "frac": rate * ib / 1e9 / pk["hbm_gbs"], "alg_bytes_per_update": ib}
@@ -611,6 +618,8 @@ def run_learned(g, torch, args):
                                  ("learned_fp64", g.SN_PREC_FP64, True, False),
                                  ("plain_fp64_inv", g.SN_PREC_FP64_INV, False, False),
                                  ("learned_fp64_inv", g.SN_PREC_FP64_INV, True, False),
+                                 ("plain_ds_inv", g.SN_PREC_DS_INV, False, False),
+                                 ("learned_ds_inv", g.SN_PREC_DS_INV, True, False),
                                  ("plain_mixed_ds", g.SN_PREC_MIXED_DS, False, False),
                                  ("learned_mixed_ds", g.SN_PREC_MIXED_DS, True, False),
                                  ("dsa_mixed_ds", g.SN_PREC_MIXED_DS, False, True),
@@ -635,7 +644,8 @@ def run_learned(g, torch, args):
     out.update(runs)
     out["speedup_learned_mixed_ds_vs_plain_fp64"] = runs["plain_fp64"]["seconds"] / runs["learned_mixed_ds"]["seconds"]
     out["speedup_learned_fp64_vs_plain_fp64"] = runs["plain_fp64"]["seconds"] / runs["learned_fp64"]["seconds"]
-    for k in ("dsa_mixed_ds", "learned_dsa_mixed_ds", "plain_fp64_inv", "learned_fp64_inv"):
+    for k in ("dsa_mixed_ds", "learned_dsa_mixed_ds", "plain_fp64_inv", "learned_fp64_inv", "plain_ds_inv",
+              "learned_ds_inv"):
         out[f"speedup_{k}_vs_plain_fp64"] = runs["plain_fp64"]["seconds"] / runs[k]["seconds"]
     out["dsa_cg"] = {"rtol": args.dsa_rtol, "max_iter": args.dsa_max_cg}
     ctx.sn_release_inverse()
@@ -658,7 +668,8 @@ def run_batch(g, torch, args):
     ups = b.sn_batch_updates_per_sweep()
     res = {"workload": "256 uneven 2D problems, n~U{8..64}, p~U{1,2,3}, r~U{2,3}, S4-S8, seed 31",
            "updates_per_sweep": int(ups), "elements": int(sum(p.mesh.n_elem for p in probs))}
-    for name, prec in (("mixed_ds", g.SN_PREC_MIXED_DS), ("fp64", g.SN_PREC_FP64), ("fp64_inv", g.SN_PREC_FP64_INV)):
+    for name, prec in (("mixed_ds", g.SN_PREC_MIXED_DS), ("fp64", g.SN_PREC_FP64), ("fp64_inv", g.SN_PREC_FP64_INV),
+                       ("ds_inv", g.SN_PREC_DS_INV)):
         mode, bps = b.sn_batch_tune(prec)
         b.sn_batch_si_begin()
         for _ in range(args.warmup):
@@ -672,7 +683,7 @@ def run_batch(g, torch, args):
         ev1.record(stream)
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
-        if prec == g.SN_PREC_FP64_INV:
+        if prec in (g.SN_PREC_FP64_INV, g.SN_PREC_DS_INV):
             for c in ctxs:
                 c.sn_release_inverse()       # formed again inside the timed solve
         torch.cuda.synchronize()
@@ -816,7 +827,7 @@ def main():
     ap.add_argument("--learned-n", type=int, default=48, help="mesh size n^3 of the learned-predictor measurement")
     ap.add_argument("--launch", default="auto", choices=["auto", "levels", "dataflow"],
                     help="sweep schedule per form: the autotuner's choice, one launch per level, or one persistent dataflow launch")
-    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed", "mixed_ds", "fp64_inv"],
+    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed", "mixed_ds", "fp64_inv", "ds_inv"],
                     help="form reported as the headline value (all three are measured; default: the paper's FP64)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no e2e, time-to-tolerance or CPU legs): for profiler launch lists")

@@ -58,7 +58,7 @@ typedef enum {
 } sn_status;
 
 enum { SN_WEIGHT_UNITY = 0, SN_WEIGHT_FACE = 1, SN_WEIGHT_SIGINVFACE = 2 };
-enum { SN_PREC_FP64 = 0, SN_PREC_MIXED = 1, SN_PREC_MIXED_DS = 2, SN_PREC_FP64_INV = 3 };
+enum { SN_PREC_FP64 = 0, SN_PREC_MIXED = 1, SN_PREC_MIXED_DS = 2, SN_PREC_FP64_INV = 3, SN_PREC_DS_INV = 4 };
 enum { SN_LAUNCH_LEVELS = 0, SN_LAUNCH_DATAFLOW = 1 };
 
 typedef struct {
@@ -174,16 +174,21 @@ sn_status sn_set_spin_limit(sn_ctx* ctx, int64_t polls);
  * (sn_si_begin(ctx, NULL)).  mode_out / blocks_per_sm_out may be NULL. */
 sn_status sn_autotune(sn_ctx* ctx, int precision, int* mode_out, int* blocks_per_sm_out);
 
-/* Stored local inverses of the SN_PREC_FP64_INV form (no counterpart in the paper, which
- * factors during the sweep): the left-hand side of eq. 21 for direction d and element e,
- * G + F_e + M_t, is the same in every source iteration, so its inverse is formed once, by
- * Gauss-Jordan elimination with partial pivoting in FP64, for all (direction, element) pairs in
- * one launch, and kept in a device buffer of n_dir * n_elem * N * N doubles owned by the context.
- * sn_prepare_inverse (re)forms them now; *ms (may be NULL) receives the device time of that
- * work.  Valid after sn_build_graph; new materials or a new graph make the stored inverses
- * stale, and the next sweep of the form forms them again.  sn_release_inverse frees the buffer.
- * Errors: SN_ESTATE (no graph), SN_ENOMEM (the buffer does not fit in device memory). */
-sn_status sn_prepare_inverse(sn_ctx* ctx, float* ms);
+/* Stored local inverses of the stored-inverse forms (no counterpart in the paper, which factors
+ * during the sweep): the left-hand side of eq. 21 for direction d and element e, G + F_e + M_t,
+ * is the same in every source iteration, so its inverse is formed once, by Gauss-Jordan
+ * elimination with partial pivoting in FP64, for all (direction, element) pairs in one launch,
+ * together with the pair's inflow face blocks (the coupling matrices of its upwind traces), and
+ * kept in context-owned device buffers: n_dir * n_elem * N * N entries for the inverses and
+ * Nf * Nf per inflow face for the blocks, 8 bytes each.  precision SN_PREC_FP64_INV stores them
+ * as doubles, SN_PREC_DS_INV as (hi, lo) FP32 pairs of the same FP64 values.
+ * sn_prepare_inverse (re)forms them now in the layout of `precision`; *ms (may be NULL) receives
+ * the device time of that launch.  Otherwise the first sweep of a stored-inverse form forms them
+ * (and a sweep of the other stored-inverse form forms them again).  Valid after sn_build_graph;
+ * new materials or a new graph drop them.  sn_release_inverse frees the buffers.
+ * Errors: SN_ESTATE (no graph), SN_EINVAL (precision not a stored-inverse form), SN_ENOMEM (the
+ * buffers do not fit in device memory). */
+sn_status sn_prepare_inverse(sn_ctx* ctx, int precision, float* ms);
 sn_status sn_release_inverse(sn_ctx* ctx);
 
 /* Copy the graph out (valid after sn_build_graph).
@@ -206,9 +211,11 @@ sn_status sn_get_graph(sn_ctx* ctx, int64_t* n_removed, int32_t* removed, int64_
  *   but the matrix row and the residual are formed in double-single arithmetic (pairs of FP32
  *   values with error-free products and sums, ~2^-48 relative) on the FP32 pipe; only the
  *   right-hand side and the final sum are FP64.  SN_PREC_FP64_INV: FP64; the inverse of every
- *   (direction, element) matrix G + F_e + M_t, which does not change between iterations, is
- *   formed once (sn_prepare_inverse, or on the first sweep of this form) and kept in device
- *   memory (n_dir * n_elem * N * N doubles); a sweep assembles the right-hand side and applies it.
+ *   (direction, element) matrix G + F_e + M_t, which does not change between iterations, and
+ *   its inflow face blocks are formed once (see sn_prepare_inverse) and kept in device memory;
+ *   a sweep forms the right-hand side and applies the inverse.  SN_PREC_DS_INV: the same stored
+ *   FP64 values kept as (hi, lo) FP32 pairs, right-hand side and application in double-single
+ *   arithmetic on the FP32 pipe.
  * Synchronises the stream before returning when any pointer is a host pointer. */
 sn_status sn_sweep(sn_ctx* ctx, const double* phi_in, const double* psi_old, double* psi_new,
                    int precision);

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libsnsweep.so")
 
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENOTCONVERGED, SN_EMESH, SN_ESTATE = range(8)
 SN_WEIGHT_UNITY, SN_WEIGHT_FACE, SN_WEIGHT_SIGINVFACE = 0, 1, 2
-SN_PREC_FP64, SN_PREC_MIXED, SN_PREC_MIXED_DS, SN_PREC_FP64_INV = 0, 1, 2, 3
+SN_PREC_FP64, SN_PREC_MIXED, SN_PREC_MIXED_DS, SN_PREC_FP64_INV, SN_PREC_DS_INV = 0, 1, 2, 3, 4
 SN_LAUNCH_LEVELS, SN_LAUNCH_DATAFLOW = 0, 1
 WEIGHTING = {"unity": 0, "face": 1, "siginvface": 2}
 
@@ -116,7 +116,7 @@ def load(path=LIB_PATH):
         "sn_set_dsa": (I, [P, I, D, I]),
         "sn_dsa_correction": (I, [P, P, P, P, ctypes.POINTER(I)]),
         "sn_dsa_last_iters": (ctypes.c_int32, [P]),
-        "sn_prepare_inverse": (I, [P, ctypes.POINTER(ctypes.c_float)]),
+        "sn_prepare_inverse": (I, [P, I, ctypes.POINTER(ctypes.c_float)]),
         "sn_release_inverse": (I, [P]),
     }
     for name, (res, args) in sig.items():
@@ -290,10 +290,10 @@ class Context:
     def sn_dsa_last_iters(self):
         return self._lib.sn_dsa_last_iters(self._c)
 
-    def sn_prepare_inverse(self):
-        """Forms the stored local inverses of the SN_PREC_FP64_INV form; returns device ms."""
+    def sn_prepare_inverse(self, precision=SN_PREC_FP64_INV):
+        """Forms the stored local inverses and face blocks of a stored-inverse form; returns device ms."""
         ms = ctypes.c_float()
-        self._check(self._lib.sn_prepare_inverse(self._c, ctypes.byref(ms)))
+        self._check(self._lib.sn_prepare_inverse(self._c, int(precision), ctypes.byref(ms)))
         return ms.value
 
     def sn_release_inverse(self):

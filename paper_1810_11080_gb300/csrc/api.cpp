@@ -69,10 +69,16 @@ void free_dsa(sn_ctx* c) {
   D.ready = false;
 }
 
+void free_inverse(sn_ctx* c) {
+  dfree(c->d_inv);
+  dfree(c->d_fblk);
+  dfree(c->d_fidx);
+  c->inv_form = -1;
+}
+
 void free_graph_state(sn_ctx* c) {
   free_dsa(c);
-  dfree(c->d_inv);
-  c->inv_ready = false;
+  free_inverse(c);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   c->graphs.clear();
   dfree(c->d_facecode);
@@ -729,10 +735,41 @@ sn_status sn_get_graph(sn_ctx* c, int64_t* n_removed, int32_t* removed, int64_t 
 
 namespace {
 
-// Stored inverses of the SN_PREC_FP64_INV form: allocated once, formed for every pair.
-sn_status form_inverse(sn_ctx* c, float* ms) {
-  const size_t n = (size_t)c->M * c->E * c->N * c->N;
+// Stored inverses and inflow face blocks of the stored-inverse forms: the block index of every
+// pair (its inflow faces counted in pair order) is set up on the host from the face codes, the
+// buffers are allocated once per graph, and one launch forms every record in the layout of
+// `prec` (doubles, or (hi, lo) FP32 pairs of the same values).
+sn_status form_inverse(sn_ctx* c, int prec, float* ms) {
+  const size_t npair = (size_t)c->M * c->E;
+  const size_t nblk = (size_t)c->Nf * c->Nf;
+  c->inv_form = -1;
+  if (!c->d_fidx) {
+    std::vector<uint32_t> code(npair);
+    SN_CUDA(c, cudaMemcpyAsync(code.data(), c->d_facecode, npair * 4, cudaMemcpyDeviceToHost, c->stream));
+    SN_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::vector<int32_t> fidx(npair);
+    int64_t tot = 0;
+    for (size_t q = 0; q < npair; ++q) {
+      fidx[q] = (int32_t)tot;
+      for (int f = 0; f < 2 * c->dim; ++f) tot += face_mode(code[q], f) != MODE_NONE;
+      if (tot > INT32_MAX) {
+        set_err(c, "stored inverses: more than 2^31 inflow face blocks");
+        return SN_EINVAL;
+      }
+    }
+    const size_t nfb = std::max<size_t>(1, (size_t)tot) * nblk;
+    if (dalloc(c->d_fblk, nfb) != cudaSuccess || dalloc(c->d_fidx, npair) != cudaSuccess) {
+      cudaGetLastError();
+      dfree(c->d_fblk);
+      dfree(c->d_fidx);
+      set_err(c, "stored inverses: " + std::to_string(nfb * 8) + " bytes of face blocks do not fit in device memory");
+      return SN_ENOMEM;
+    }
+    SN_CUDA(c, cudaMemcpyAsync(c->d_fidx, fidx.data(), npair * 4, cudaMemcpyHostToDevice, c->stream));
+    SN_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
   if (!c->d_inv) {
+    const size_t n = npair * c->N * c->N;
     if (dalloc(c->d_inv, n) != cudaSuccess) {
       cudaGetLastError();
       c->d_inv = nullptr;
@@ -740,7 +777,6 @@ sn_status form_inverse(sn_ctx* c, float* ms) {
       return SN_ENOMEM;
     }
   }
-  c->inv_ready = false;
   if (ms && !c->ev_a) {
     SN_CUDA(c, cudaEventCreate(&c->ev_a));
     SN_CUDA(c, cudaEventCreate(&c->ev_b));
@@ -748,9 +784,9 @@ sn_status form_inverse(sn_ctx* c, float* ms) {
   DevProblem P = c->dev();
   SweepArgs sa{c->d_facecode, c->d_mixed_off, c->d_mixedB, c->d_mixedB32, c->d_mixedB32lo, c->d_src,
                nullptr, nullptr, nullptr, nullptr, nullptr,
-               nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, c->d_inv};
+               nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, c->d_inv, c->d_fblk, c->d_fidx};
   if (ms) SN_CUDA(c, cudaEventRecord(c->ev_a, c->stream));
-  SN_CUDA(c, launch_invert(P, sa, c->stream));
+  SN_CUDA(c, launch_invert(P, prec, sa, c->stream));
   c->launches++;
   if (ms) {
     SN_CUDA(c, cudaEventRecord(c->ev_b, c->stream));
@@ -759,7 +795,7 @@ sn_status form_inverse(sn_ctx* c, float* ms) {
   } else {
     SN_CUDA(c, cudaStreamSynchronize(c->stream));
   }
-  c->inv_ready = true;
+  c->inv_form = prec;
   return SN_OK;
 }
 
@@ -772,13 +808,15 @@ sn_status run_levels(sn_ctx* c, int prec, const double* psi_old, double* psi_new
   const int64_t total = c->level_off.back();
   int* err = reinterpret_cast<int*>(c->d_red + 2);
   unsigned long long* head = c->d_red + 3;
-  if (prec == SN_PREC_FP64_INV && !c->inv_ready) {      // outside any capture: it synchronises
-    sn_status st = form_inverse(c, nullptr);
+  const bool stored = prec == SN_PREC_FP64_INV || prec == SN_PREC_DS_INV;
+  if (stored && c->inv_form != prec) {     // outside any capture: it synchronises
+    sn_status st = form_inverse(c, prec, nullptr);
     if (st != SN_OK) return st;
   }
   SweepArgs sa{c->d_facecode, c->d_mixed_off, c->d_mixedB, c->d_mixedB32, c->d_mixedB32lo, c->d_src,
                psi_old, psi_new, c->d_done, err, c->d_pairs,
-               c->d_srch, c->d_srcl, nullptr, nullptr, nullptr, nullptr, c->spin_limit, c->d_inv};
+               c->d_srch, c->d_srcl, nullptr, nullptr, nullptr, nullptr, c->spin_limit,
+               c->d_inv, c->d_fblk, c->d_fidx};
   // (hi, lo) splits of the two iterates: the context's own buffers, or scratch for caller buffers
   bool convert_old = false;
   const size_t npsi = (size_t)c->M * c->E * c->N;
@@ -792,7 +830,7 @@ sn_status run_levels(sn_ctx* c, int prec, const double* psi_old, double* psi_new
       sa.psi_new_l = c->d_psil[k];
     }
   }
-  if (prec == SN_PREC_MIXED_DS) {
+  if (prec == SN_PREC_MIXED_DS || prec == SN_PREC_DS_INV) {
     for (int k = 0; k < 2; ++k)
       if (!c->d_scr_h[k] && (k == 0 ? !sa.psi_old_h : !sa.psi_new_h)) {
         SN_CUDA(c, dalloc(c->d_scr_h[k], npsi));
@@ -884,19 +922,20 @@ const double* stage_in(sn_ctx* c, const double* p, size_t n, int slot, sn_status
 
 }  // namespace
 
-sn_status sn_prepare_inverse(sn_ctx* c, float* ms) {
+sn_status sn_prepare_inverse(sn_ctx* c, int precision, float* ms) {
   if (!c) return SN_EINVAL;
   SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
+  SN_REQ(c, precision == SN_PREC_FP64_INV || precision == SN_PREC_DS_INV, SN_EINVAL,
+         "precision must be SN_PREC_FP64_INV or SN_PREC_DS_INV");
   cudaSetDevice(c->device);
-  return form_inverse(c, ms);
+  return form_inverse(c, precision, ms);
 }
 
 sn_status sn_release_inverse(sn_ctx* c) {
   if (!c) return SN_EINVAL;
   cudaSetDevice(c->device);
   SN_CUDA(c, cudaStreamSynchronize(c->stream));
-  dfree(c->d_inv);
-  c->inv_ready = false;
+  free_inverse(c);
   return SN_OK;
 }
 
@@ -905,7 +944,7 @@ sn_status sn_sweep(sn_ctx* c, const double* phi_in, const double* psi_old, doubl
   SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
   SN_REQ(c, phi_in && psi_old && psi_new, SN_EINVAL, "null array");
   SN_REQ(c, (const void*)psi_old != (const void*)psi_new, SN_EINVAL, "psi_new must not alias psi_old");
-  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_FP64_INV, SN_EINVAL, "unknown precision");
+  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_DS_INV, SN_EINVAL, "unknown precision");
   cudaSetDevice(c->device);
   const size_t npsi = (size_t)c->M * c->E * c->N, nphi = (size_t)c->E * c->N;
   sn_status st;
@@ -1050,7 +1089,7 @@ sn_status sn_si_begin(sn_ctx* c, const double* phi0) {
 sn_status sn_si_step(sn_ctx* c, int precision, double* residual, float* ms_sweep) {
   if (!c) return SN_EINVAL;
   SN_REQ(c, c->graph_ready && c->si_ready, SN_ESTATE, "sn_si_begin first");
-  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_FP64_INV, SN_EINVAL, "unknown precision");
+  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_DS_INV, SN_EINVAL, "unknown precision");
   cudaSetDevice(c->device);
   cudaStream_t s = c->stream;
   if (ms_sweep && !c->ev_a) {
@@ -1111,7 +1150,7 @@ sn_status sn_source_iterate(sn_ctx* c, double tol, int max_iter, int precision, 
   if (!c) return SN_EINVAL;
   SN_REQ(c, c->graph_ready, SN_ESTATE, "sn_build_graph first");
   SN_REQ(c, max_iter >= 1 && tol > 0.0, SN_EINVAL, "max_iter >= 1 and tol > 0 required");
-  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_FP64_INV, SN_EINVAL, "unknown precision");
+  SN_REQ(c, precision >= SN_PREC_FP64 && precision <= SN_PREC_DS_INV, SN_EINVAL, "unknown precision");
   auto t0 = std::chrono::steady_clock::now();
   sn_status st = sn_si_begin(c, phi0);
   if (st != SN_OK) return st;

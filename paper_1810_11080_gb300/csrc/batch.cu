@@ -89,6 +89,8 @@ cudaError_t launch_batch_sweep(int dim, int precision, bool dataflow, const DevP
   SN_BATCH_CASE(3, 2)
   SN_BATCH_CASE(2, 3)
   SN_BATCH_CASE(3, 3)
+  SN_BATCH_CASE(2, 4)
+  SN_BATCH_CASE(3, 4)
 #undef SN_BATCH_CASE
   return cudaErrorInvalidValue;
 }

@@ -160,6 +160,8 @@ sn_status sn_batch_create(sn_batch** out, int n_problems, sn_ctx* const* problem
     args1[k].psi_new_h = c->d_psih[0];
     args1[k].psi_new_l = c->d_psil[0];
     args0[k].inv = args1[k].inv = nullptr;
+    args0[k].fblk = args1[k].fblk = nullptr;
+    args0[k].fidx = args1[k].fidx = nullptr;
     m0[k] = MomentArgs{c->d_psi[1], b->phiA[k], b->phiB[k], c->d_src, c->d_srch, c->d_srcl};
     m1[k] = MomentArgs{c->d_psi[0], b->phiB[k], b->phiA[k], c->d_src, c->d_srch, c->d_srcl};
   }
@@ -257,22 +259,26 @@ sn_status sn_batch_si_begin(sn_batch* b, const double* const* phi0) {
 sn_status sn_batch_si_step(sn_batch* b, int precision, double* residuals, float* ms_sweep) {
   if (!b) return SN_EINVAL;
   SB_REQ(b, b->ready, SN_ESTATE, "sn_batch_si_begin first");
-  SB_REQ(b, precision >= SN_PREC_FP64 && precision <= SN_PREC_FP64_INV, SN_EINVAL, "unknown precision");
+  SB_REQ(b, precision >= SN_PREC_FP64 && precision <= SN_PREC_DS_INV, SN_EINVAL, "unknown precision");
   SB_CUDA(b, cudaSetDevice(b->device));
-  if (precision == SN_PREC_FP64_INV) {
+  if (precision == SN_PREC_FP64_INV || precision == SN_PREC_DS_INV) {
     // every problem's stored inverses formed (once), and their addresses in the argument tables
     bool moved = !b->inv_linked;
     for (int k = 0; k < b->n; ++k) {
       sn_ctx* c = b->ctx[k];
-      if (!c->inv_ready) {
-        sn_status st = sn_prepare_inverse(c, nullptr);
+      if (c->inv_form != precision) {
+        sn_status st = sn_prepare_inverse(c, precision, nullptr);
         if (st != SN_OK) {
           b->err = std::string("problem ") + std::to_string(k) + ": " + c->err;
           return st;
         }
       }
-      if (b->h_args[0][k].inv != c->d_inv) moved = true;
-      b->h_args[0][k].inv = b->h_args[1][k].inv = c->d_inv;
+      if (b->h_args[0][k].inv != c->d_inv || b->h_args[0][k].fblk != c->d_fblk) moved = true;
+      for (int q = 0; q < 2; ++q) {
+        b->h_args[q][k].inv = c->d_inv;
+        b->h_args[q][k].fblk = c->d_fblk;
+        b->h_args[q][k].fidx = c->d_fidx;
+      }
     }
     if (moved) {
       SB_CUDA(b, cudaStreamSynchronize(b->stream));

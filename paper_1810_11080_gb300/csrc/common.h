@@ -115,7 +115,12 @@ struct SweepArgs {
   float* psi_new_h;
   float* psi_new_l;
   long long spin_limit;       // dataflow schedule: polls of one upwind flag before giving up (<= 0: SPIN_LIMIT)
-  double* inv;                // [M][E][N][N] stored local inverses (SN_PREC_FP64_INV) or null
+  // stored-inverse forms: per pair q = d E + e, inv + q N^2 holds the inverse column-major and
+  // fblk + (fidx[q] + r) Nf^2 the block of its r-th inflow face (row-major); doubles for
+  // SN_PREC_FP64_INV, (hi, lo) FP32 pairs for SN_PREC_DS_INV
+  double* inv;
+  double* fblk;
+  const int32_t* fidx;
 };
 
 // Per-problem pointers of the fused moment / source kernel in a batch.
@@ -168,8 +173,9 @@ cudaError_t launch_sweep_level(const DevProblem& P, int precision, const int32_t
                                const SweepArgs& sa, cudaStream_t s);
 cudaError_t launch_sweep_flow(const DevProblem& P, int precision, const int32_t* pairs, int64_t count,
                               const SweepArgs& sa, unsigned long long* head, int blocks_per_sm, cudaStream_t s);
-// Forms sa.inv for every (direction, element) pair (sweep_inv.cu).
-cudaError_t launch_invert(const DevProblem& P, const SweepArgs& sa, cudaStream_t s);
+// Forms sa.inv and sa.fblk for every (direction, element) pair in the layout of `precision`
+// (SN_PREC_FP64_INV or SN_PREC_DS_INV) (sweep_inv.cu).
+cudaError_t launch_invert(const DevProblem& P, int precision, const SweepArgs& sa, cudaStream_t s);
 
 }  // namespace sn
 
@@ -241,9 +247,11 @@ struct sn_ctx {
   double dsa_rtol = 1e-4;
   int dsa_max_iter = 500;
   int dsa_last_iters = 0;
-  // stored local inverses (SN_PREC_FP64_INV)
+  // stored local inverses and inflow face blocks (SN_PREC_FP64_INV, SN_PREC_DS_INV)
   double* d_inv = nullptr;
-  bool inv_ready = false;
+  double* d_fblk = nullptr;
+  int32_t* d_fidx = nullptr;
+  int inv_form = -1;               // the form the stored records are written for (-1: none)
   int launch_mode = 0;                   // SN_LAUNCH_LEVELS / SN_LAUNCH_DATAFLOW
   long long spin_limit = 0;              // dataflow wait limit (0: the kernels' default)
   int blocks_per_sm = 0;                 // dataflow grid: 0 = occupancy limit

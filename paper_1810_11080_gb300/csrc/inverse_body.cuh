@@ -1,0 +1,349 @@
+// Stored-inverse forms of the (element, direction) solve.  The matrix A = G + F_e + M_t of a
+// pair (the left-hand side of eq. 21: sigma_t, Omega, the element's factors and its inflow
+// faces) is the same in every source iteration, so it is inverted once per problem
+// (invert_pair) and a sweep only forms the right-hand side and applies the inverse:
+//   psi_e = Ainv (src_e + sum_{inflow faces f} B_f trace_f).
+// Stored per pair q = d E + e: Ainv column-major at inv + q N^2 (entry (i, j) at j N + i, so the
+// lanes of a segment read each column as one contiguous run), and the block B_f of its r-th
+// inflow face, row-major, at fblk + (fidx[q] + r) Nf^2 (r counts the inflow faces in face order).
+// SN_PREC_FP64_INV keeps doubles and applies them in FP64; SN_PREC_DS_INV keeps (hi, lo) FP32
+// pairs of the same FP64 values and applies them in double-single arithmetic on the FP32 pipe.
+#pragma once
+
+namespace sn {
+
+// Inverse and inflow blocks of one pair, formed in FP64 by Gauss-Jordan elimination with partial
+// pivoting (row-per-lane; see gj32 for the bookkeeping of V in pivot-step order).  A is assembled
+// as in body64.  DSOUT: store (hi, lo) FP32 pairs instead of doubles.
+template <int DIM, int P_, bool DSOUT>
+__device__ __forceinline__ void invert_pair(const DevProblem& Pb, const SweepArgs& sa, int64_t q, bool valid,
+                                            int lane) {
+  using S = Shape<DIM, P_>;
+  constexpr int N = S::N, NF = S::NF, W = S::W;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int i = lane % W;
+  const int64_t E = Pb.E;
+  const int d = valid ? (int)(q / E) : 0;
+  const int64_t e = valid ? q % E : 0;
+  const bool row = valid && (i < N);
+  const double om0 = Pb.omega[d * 3 + 0], om1 = Pb.omega[d * 3 + 1], om2 = Pb.omega[d * 3 + 2];
+  const double* blk = Pb.elem + e * Pb.blk;
+  auto put = [&](int64_t idx, double x, double* base) {
+    if constexpr (DSOUT) {
+      float2 v;
+      ds_split(x, v.x, v.y);
+      reinterpret_cast<float2*>(base)[idx] = v;
+    } else {
+      base[idx] = x;
+    }
+  };
+  double a[N];
+  if (row) {
+    const double st = Pb.sig_t[e];
+    static_for<0, N>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      double v = om0 * __ldg(blk + j * N + i);
+      v = fma(om1, __ldg(blk + N * N + j * N + i), v);
+      if (DIM == 3) v = fma(om2, __ldg(blk + 2 * N * N + j * N + i), v);
+      a[j] = fma(st, __ldg(blk + DIM * N * N + j * N + i), v);
+    });
+  } else {
+    static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = 0.0; });
+  }
+  const uint32_t code = valid ? sa.facecode[q] : 0u;
+  const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[q] : 0;
+  const int64_t bidx = valid ? sa.fidx[q] : 0;
+  int mrank = 0, rank = 0;
+  static_for<0, 2 * DIM>([&](auto fconst) {
+    constexpr int f = decltype(fconst)::value;
+    const uint32_t mode = face_mode(code, f);
+    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+    if (mode != MODE_NONE && fi >= 0) {
+      double Brow[NF];
+      brow64<DIM, P_>(blk, sa, mode, f, fi, mbase + mrank, om0, om1, om2, Brow);
+      const int64_t o = (bidx + rank) * (NF * NF) + fi * NF;
+      static_for<0, NF>([&](auto jconst) {
+        constexpr int fj = decltype(jconst)::value;
+        a[fvi<DIM, P_>(f, fj)] += Brow[fj];
+        put(o + fj, Brow[fj], sa.fblk);
+      });
+    }
+    if (mode == MODE_MIXED) ++mrank;
+    if (mode != MODE_NONE) ++rank;
+  });
+  double v[N];
+  int plk[N];
+  bool used = !row;
+  double myinv = 0.0;
+  int myk = -1;
+  static_for<0, N>([&](auto jconst) { v[decltype(jconst)::value] = 0.0; });
+  static_for<0, N>([&](auto kconst) {
+    constexpr int k = decltype(kconst)::value;
+    const unsigned hw = (unsigned)((unsigned long long)__double_as_longlong(a[k]) >> 32);
+    const unsigned key = used ? 0u : ((hw & 0x7fffffe0u) | (unsigned)(31 - lane));
+    const int pl = seg_argmax_key<W>(key, lane);
+    plk[k] = pl;
+    const double inv = nr_rcp(__shfl_sync(FULL, a[k], pl, W));
+    const bool me = (lane == pl);
+    if (me) {
+      used = true;
+      myk = k;
+      myinv = inv;
+      v[k] = 1.0;
+    }
+    const double l = me ? 0.0 : a[k] * inv;
+    static_for<k + 1, N>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      a[j] = fma(-l, __shfl_sync(FULL, a[j], pl, W), a[j]);
+    });
+    static_for<0, k + 1>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      v[j] = fma(-l, __shfl_sync(FULL, v[j], pl, W), v[j]);
+    });
+  });
+  // the lane of step k holds row k of the inverse: Ainv[k][row of plk[m]] = v[m] / pivot
+  if (row && myk >= 0) {
+    const int64_t o = q * (N * N) + myk;
+    static_for<0, N>([&](auto mconst) {
+      constexpr int m = decltype(mconst)::value;
+      put(o + (plk[m] % W) * N, v[m] * myinv, sa.inv);
+    });
+  }
+}
+
+// ------------------------------------------------------------------ FP64 application
+template <int DIM, int P_, bool DF>
+__device__ __forceinline__ void bodyinv(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid, int lane) {
+  using S = Shape<DIM, P_>;
+  constexpr int N = S::N, NF = S::NF, W = S::W;
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr bool BPRE = DIM == 2;      // inflow block rows held in registers across the wait (2D)
+  const int i = lane % W;
+  const int M = Pb.M;
+  const int64_t E = Pb.E;
+  const int64_t e = pr / M;
+  const int d = pr % M;
+  const int64_t q = (int64_t)d * E + e;
+  const bool row = valid && (i < N);
+  double ainv[N];
+  double b = 0.0;
+  if (row) {
+    const double* ai = sa.inv + q * (N * N) + i;
+    static_for<0, N>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      ainv[j] = __ldcs(ai + j * N);      // read once per sweep: streamed past the caches
+    });
+    if (Pb.q_dir != nullptr) {
+      const double* blk = Pb.elem + e * Pb.blk;
+      const double* qd = Pb.q_dir + q * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) b = fma(__ldg(blk + DIM * N * N + i * N + j), qd[j], b);
+    }
+  } else {
+    static_for<0, N>([&](auto jconst) { ainv[decltype(jconst)::value] = 0.0; });
+  }
+  const uint32_t code = valid ? sa.facecode[q] : 0u;
+  const int64_t bidx = valid ? sa.fidx[q] : 0;
+  // 2D: a node lies on at most one face per axis; that face's block row goes to slot axis.
+  double Bax[BPRE ? DIM : 1][NF];
+  if constexpr (BPRE) {
+    int rank = 0;
+    static_for<0, 2 * DIM>([&](auto fconst) {
+      constexpr int f = decltype(fconst)::value;
+      const uint32_t mode = face_mode(code, f);
+      const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+      if (mode != MODE_NONE && fi >= 0) {
+        const double* br = sa.fblk + (bidx + rank) * (NF * NF) + fi * NF;
+        static_for<0, NF>([&](auto jconst) { Bax[f >> 1][decltype(jconst)::value] = __ldcs(br + decltype(jconst)::value); });
+      }
+      if (mode != MODE_NONE) ++rank;
+    });
+  }
+  if constexpr (DF) wait_upwind<DIM>(Pb, sa, code, e, d, valid);
+  else {
+    pdl_wait();                          // sources and upwind traces come from earlier launches
+    pdl_launch_dependents();
+  }
+  if (row) b += sa.src[e * N + i];
+  int rank = 0;
+  static_for<0, 2 * DIM>([&](auto fconst) {
+    constexpr int f = decltype(fconst)::value;
+    const uint32_t mode = face_mode(code, f);
+    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+    if (mode != MODE_NONE && fi >= 0) {
+      if constexpr (BPRE) {
+        face_rhs<DIM, P_, DF>(Pb, sa, code, f, e, d, Bax[f >> 1], b);
+      } else {
+        double Brow[NF];
+        const double* br = sa.fblk + (bidx + rank) * (NF * NF) + fi * NF;
+        static_for<0, NF>([&](auto jconst) { Brow[decltype(jconst)::value] = __ldcs(br + decltype(jconst)::value); });
+        face_rhs<DIM, P_, DF>(Pb, sa, code, f, e, d, Brow, b);
+      }
+    }
+    if (mode != MODE_NONE) ++rank;
+  });
+  // psi_i = sum_j Ainv[i][j] b_j, b_j from lane j of the segment; two accumulation chains
+  double x0 = 0.0, x1 = 0.0;
+  static_for<0, N>([&](auto jconst) {
+    constexpr int j = decltype(jconst)::value;
+    const double bj = __shfl_sync(FULL, b, j, W);
+    if (j & 1) x1 = fma(ainv[j], bj, x1);
+    else x0 = fma(ainv[j], bj, x0);
+  });
+  if (row) {
+    const double x = x0 + x1;
+    const int64_t o = q * N + i;
+    sa.psi_new[o] = x;
+    if (sa.psi_new_h != nullptr) {
+      const float h = (float)x;
+      sa.psi_new_h[o] = h;
+      sa.psi_new_l[o] = (float)(x - (double)h);
+    }
+  }
+  publish<DF, W>(Pb, sa, e, d, valid, i);
+}
+
+// ------------------------------------------------------------------ double-single application
+// The right-hand side is accumulated and the inverse applied in double-single arithmetic
+// (error-free FP32 products and sums, ~2^-48 relative), from the (hi, lo) splits of the stored
+// FP64 inverse and blocks, of the source and of the upwind traces; no FP64 instruction on the
+// solve path except the final psi = hi + lo.
+template <int DIM, int P_, bool DF>
+__device__ __forceinline__ void bodydsinv(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid,
+                                          int lane) {
+  using S = Shape<DIM, P_>;
+  constexpr int N = S::N, NF = S::NF, W = S::W, NP1 = S::NP1;
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr bool BPRE = DIM == 2;
+  const int i = lane % W;
+  const int M = Pb.M;
+  const int64_t E = Pb.E;
+  const int64_t e = pr / M;
+  const int d = pr % M;
+  const int64_t q = (int64_t)d * E + e;
+  const bool row = valid && (i < N);
+  const float2* inv2 = reinterpret_cast<const float2*>(sa.inv);
+  const float2* fb2 = reinterpret_cast<const float2*>(sa.fblk);
+  float2 A[N];
+  float rbh = 0.0f, rbl = 0.0f;
+  if (row) {
+    const float2* ai = inv2 + q * (N * N) + i;
+    static_for<0, N>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      A[j] = __ldcs(ai + j * N);
+    });
+    if (Pb.q_dir != nullptr) {           // direction-dependent source (tests): FP64, then split
+      const double* blk = Pb.elem + e * Pb.blk;
+      const double* qd = Pb.q_dir + q * N;
+      double qb = 0.0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) qb = fma(__ldg(blk + DIM * N * N + i * N + j), qd[j], qb);
+      ds_split(qb, rbh, rbl);
+    }
+  } else {
+    static_for<0, N>([&](auto jconst) { A[decltype(jconst)::value] = make_float2(0.0f, 0.0f); });
+  }
+  const uint32_t code = valid ? sa.facecode[q] : 0u;
+  const int64_t bidx = valid ? sa.fidx[q] : 0;
+  int64_t nbv[2 * DIM];
+  int fov[2 * DIM];
+  static_for<0, 2 * DIM>([&](auto fconst) {
+    constexpr int f = decltype(fconst)::value;
+    nbv[f] = valid ? Pb.nbr[e * 2 * DIM + f] : -1;
+    fov[f] = valid ? (Pb.nbr_face[e * 2 * DIM + f] | (Pb.orient[e * 2 * DIM + f] << 8)) : 0;
+  });
+  float2 Bax[BPRE ? DIM : 1][NF];
+  if constexpr (BPRE) {
+    int rank = 0;
+    static_for<0, 2 * DIM>([&](auto fconst) {
+      constexpr int f = decltype(fconst)::value;
+      const uint32_t mode = face_mode(code, f);
+      const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+      if (mode != MODE_NONE && fi >= 0) {
+        const float2* br = fb2 + (bidx + rank) * (NF * NF) + fi * NF;
+        static_for<0, NF>([&](auto jconst) { Bax[f >> 1][decltype(jconst)::value] = __ldcs(br + decltype(jconst)::value); });
+      }
+      if (mode != MODE_NONE) ++rank;
+    });
+  }
+  if constexpr (DF) {
+    wait_upwind<DIM>(Pb, sa, code, e, d, valid);
+  } else {
+    pdl_wait();                          // sources and upwind traces come from earlier launches
+    pdl_launch_dependents();
+  }
+  if (row) ds_add(rbh, rbl, sa.src_h[e * N + i], sa.src_l[e * N + i]);
+  float sh2 = 0.0f, sl2 = 0.0f;          // second accumulation chain for the face terms
+  int rank = 0;
+  static_for<0, 2 * DIM>([&](auto fconst) {
+    constexpr int f = decltype(fconst)::value;
+    const uint32_t mode = face_mode(code, f);
+    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+    const int64_t nb = nbv[f];
+    if (mode != MODE_NONE && fi >= 0 && (nb >= 0 || Pb.psi_inc != nullptr)) {
+      float2 B[NF];
+      if constexpr (BPRE) {
+        static_for<0, NF>([&](auto jconst) { B[decltype(jconst)::value] = Bax[f >> 1][decltype(jconst)::value]; });
+      } else {
+        const float2* br = fb2 + (bidx + rank) * (NF * NF) + fi * NF;
+        static_for<0, NF>([&](auto jconst) { B[decltype(jconst)::value] = __ldcs(br + decltype(jconst)::value); });
+      }
+      if (nb >= 0) {                     // upwind neighbour's (hi, lo) split of the trace
+        const bool lag = face_lagged(code, f);
+        int c0, ci, cj;
+        trace_affine<DIM, P_>(fov[f] & 0xff, fov[f] >> 8, c0, ci, cj);
+        const int64_t base = ((int64_t)d * E + nb) * N + c0;
+        const float* ph_ = (lag ? sa.psi_old_h : sa.psi_new_h) + base;
+        const float* pl_ = (lag ? sa.psi_old_l : sa.psi_new_l) + base;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) {
+          const int o = ci * (fj % NP1) + cj * (fj / NP1);
+          float th, tl, qh, ql;
+          if (!lag && DF) {
+            th = __ldcg(ph_ + o);
+            tl = __ldcg(pl_ + o);
+          } else {
+            th = __ldg(ph_ + o);
+            tl = __ldg(pl_ + o);
+          }
+          ds_mul(B[fj].x, B[fj].y, th, tl, qh, ql);
+          if (fj & 1) ds_add(sh2, sl2, qh, ql);
+          else ds_add(rbh, rbl, qh, ql);
+        }
+      } else {                           // incident flux on the domain boundary
+        const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * 2 * DIM + f]) * NF;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) {
+          float th, tl, qh, ql;
+          ds_split(__ldg(pin + fj), th, tl);
+          ds_mul(B[fj].x, B[fj].y, th, tl, qh, ql);
+          ds_add(rbh, rbl, qh, ql);
+        }
+      }
+    }
+    if (mode != MODE_NONE) ++rank;
+  });
+  ds_add(rbh, rbl, sh2, sl2);
+  // psi_i = sum_j Ainv[i][j] b_j in double-single, four independent chains
+  float xh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, xl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  static_for<0, N>([&](auto jconst) {
+    constexpr int j = decltype(jconst)::value;
+    const float bjh = __shfl_sync(FULL, rbh, j, W);
+    const float bjl = __shfl_sync(FULL, rbl, j, W);
+    float ph, pl;
+    ds_mul(A[j].x, A[j].y, bjh, bjl, ph, pl);
+    ds_add(xh[j & 3], xl[j & 3], ph, pl);
+  });
+  ds_add(xh[0], xl[0], xh[1], xl[1]);
+  ds_add(xh[2], xl[2], xh[3], xl[3]);
+  ds_add(xh[0], xl[0], xh[2], xl[2]);
+  if (row) {
+    const int64_t o = q * N + i;
+    sa.psi_new_h[o] = xh[0];
+    sa.psi_new_l[o] = xl[0];
+    sa.psi_new[o] = (double)xh[0] + (double)xl[0];
+  }
+  publish<DF, W>(Pb, sa, e, d, valid, i);
+}
+
+}  // namespace sn

@@ -22,25 +22,34 @@
 
 namespace sn {
 
-#define SN_DISPATCH(FN, ...)                                                                        \
-  do {                                                                                              \
-    if (precision == SN_PREC_FP64_INV) return FN##_inv(__VA_ARGS__);                                \
-    if (P.dim == 2 && P.p == 1) { if (precision == 0) return FN<2, 1, 0>(__VA_ARGS__); if (precision == 1) return FN<2, 1, 1>(__VA_ARGS__); return FN<2, 1, 2>(__VA_ARGS__); } \
-    if (P.dim == 2 && P.p == 2) { if (precision == 0) return FN<2, 2, 0>(__VA_ARGS__); if (precision == 1) return FN<2, 2, 1>(__VA_ARGS__); return FN<2, 2, 2>(__VA_ARGS__); } \
-    if (P.dim == 2 && P.p == 3) { if (precision == 0) return FN<2, 3, 0>(__VA_ARGS__); if (precision == 1) return FN<2, 3, 1>(__VA_ARGS__); return FN<2, 3, 2>(__VA_ARGS__); } \
-    if (P.dim == 3 && P.p == 1) { if (precision == 0) return FN<3, 1, 0>(__VA_ARGS__); if (precision == 1) return FN<3, 1, 1>(__VA_ARGS__); return FN<3, 1, 2>(__VA_ARGS__); } \
-    if (P.dim == 3 && P.p == 2) { if (precision == 0) return FN<3, 2, 0>(__VA_ARGS__); if (precision == 1) return FN<3, 2, 1>(__VA_ARGS__); return FN<3, 2, 2>(__VA_ARGS__); } \
-    return cudaErrorInvalidValue;                                                                   \
+// Template instance of the form and the problem's (dim, p); the stored-inverse forms live in
+// sweep_inv.cu.
+#define SN_CASE(FN, D, PP, ...)                                                                    \
+  if (P.dim == D && P.p == PP) {                                                                   \
+    if (precision == SN_PREC_FP64) return FN<D, PP, SN_PREC_FP64>(P, __VA_ARGS__);                 \
+    if (precision == SN_PREC_MIXED) return FN<D, PP, SN_PREC_MIXED>(P, __VA_ARGS__);               \
+    return FN<D, PP, SN_PREC_MIXED_DS>(P, __VA_ARGS__);                                            \
+  }
+#define SN_DISPATCH(FN, ...)                                                                       \
+  do {                                                                                             \
+    if (precision == SN_PREC_FP64_INV || precision == SN_PREC_DS_INV)                              \
+      return FN##_inv(P, precision, __VA_ARGS__);                                                  \
+    SN_CASE(FN, 2, 1, __VA_ARGS__)                                                                 \
+    SN_CASE(FN, 2, 2, __VA_ARGS__)                                                                 \
+    SN_CASE(FN, 2, 3, __VA_ARGS__)                                                                 \
+    SN_CASE(FN, 3, 1, __VA_ARGS__)                                                                 \
+    SN_CASE(FN, 3, 2, __VA_ARGS__)                                                                 \
+    return cudaErrorInvalidValue;                                                                  \
   } while (0)
 
 cudaError_t launch_sweep_level(const DevProblem& P, int precision, const int32_t* pairs, int64_t count,
                                const SweepArgs& sa, cudaStream_t s) {
-  SN_DISPATCH(launch_level_t, P, sa, pairs, count, s);
+  SN_DISPATCH(launch_level_t, sa, pairs, count, s);
 }
 
 cudaError_t launch_sweep_flow(const DevProblem& P, int precision, const int32_t* pairs, int64_t count,
                               const SweepArgs& sa, unsigned long long* head, int blocks_per_sm, cudaStream_t s) {
-  SN_DISPATCH(launch_flow_t, P, sa, pairs, count, head, blocks_per_sm, s);
+  SN_DISPATCH(launch_flow_t, sa, pairs, count, head, blocks_per_sm, s);
 }
 
 // ------------------------------------------------------------------ moment and source

@@ -53,6 +53,7 @@ struct Shape {
 template <int DIM, int P_, int PREC>
 constexpr int sweep_minb() {
   if (PREC == SN_PREC_FP64_INV) return DIM == 2 ? 5 : 3;
+  if (PREC == SN_PREC_DS_INV) return DIM == 2 ? 5 : 4;
   if (DIM == 3 && P_ == 2) return PREC == SN_PREC_MIXED_DS ? 4 : (PREC == SN_PREC_FP64 ? 3 : 2);
   if (PREC == SN_PREC_FP64) return DIM == 2 ? 6 : 5;
   return PREC == SN_PREC_MIXED ? 4 : 5;
@@ -422,191 +423,6 @@ __device__ __forceinline__ void body64(const DevProblem& Pb, const SweepArgs& sa
   publish<DF, W>(Pb, sa, e, d, valid, i);
 }
 
-// ------------------------------------------------------------------ FP64 form, stored inverses
-// The local matrix A of (e, d) does not change between source iterations (sigma_t, Omega, the
-// element's factors and its inflow faces are fixed once the graph is built), so its inverse is
-// formed once per problem (invert_kernel) and a sweep only assembles b and applies it:
-// psi_i = sum_j Ainv[i][j] b_j.  Ainv of pair (d, e) is stored column-major, entry (i, j) at
-// ((d E + e) N + j) N + i, so the lanes of a segment read each column as one contiguous run.
-// The row of Ainv and (2D) the inflow block rows are loaded before the wait for upwind data.
-template <int DIM, int P_, bool DF>
-__device__ __forceinline__ void bodyinv(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid, int lane) {
-  using S = Shape<DIM, P_>;
-  constexpr int N = S::N, NF = S::NF, W = S::W;
-  constexpr unsigned FULL = 0xffffffffu;
-  constexpr bool BPRE = DIM == 2;      // inflow block rows kept in registers across the wait (2D)
-  const int i = lane % W;
-  const int M = Pb.M;
-  const int64_t E = Pb.E;
-  const int64_t e = pr / M;
-  const int d = pr % M;
-  const bool row = valid && (i < N);
-  const double om0 = Pb.omega[d * 3 + 0], om1 = Pb.omega[d * 3 + 1], om2 = Pb.omega[d * 3 + 2];
-  const double* blk = Pb.elem + e * Pb.blk;
-  double ainv[N];
-  double b = 0.0;
-  if (row) {
-    const double* ai = sa.inv + ((int64_t)d * E + e) * (N * N) + i;
-    static_for<0, N>([&](auto jconst) {
-      constexpr int j = decltype(jconst)::value;
-      ainv[j] = __ldcs(ai + j * N);      // read once per sweep: streamed past the caches
-    });
-    if (Pb.q_dir != nullptr) {
-      const double* qd = Pb.q_dir + ((int64_t)d * E + e) * N;
-#pragma unroll
-      for (int j = 0; j < N; ++j) b = fma(__ldg(blk + DIM * N * N + i * N + j), qd[j], b);
-    }
-  } else {
-    static_for<0, N>([&](auto jconst) { ainv[decltype(jconst)::value] = 0.0; });
-  }
-  const uint32_t code = valid ? sa.facecode[(int64_t)d * E + e] : 0u;
-  const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[(int64_t)d * E + e] : 0;
-  // 2D: a node lies on at most one face per axis; that face's block row goes to slot axis.
-  double Bax[BPRE ? DIM : 1][NF];
-  if constexpr (BPRE) {
-    int mrank = 0;
-    static_for<0, 2 * DIM>([&](auto fconst) {
-      constexpr int f = decltype(fconst)::value;
-      const uint32_t mode = face_mode(code, f);
-      const int fi = row ? on_face<DIM, P_>(f, i) : -1;
-      if (mode != MODE_NONE && fi >= 0) {
-        double Brow[NF];
-        brow64<DIM, P_>(blk, sa, mode, f, fi, mbase + mrank, om0, om1, om2, Brow);
-        static_for<0, NF>([&](auto jconst) { Bax[f >> 1][decltype(jconst)::value] = Brow[decltype(jconst)::value]; });
-      }
-      if (mode == MODE_MIXED) ++mrank;
-    });
-  }
-  if constexpr (DF) wait_upwind<DIM>(Pb, sa, code, e, d, valid);
-  else {
-    pdl_wait();                          // sources and upwind traces come from earlier launches
-    pdl_launch_dependents();
-  }
-  if (row) b += sa.src[e * N + i];
-  int mrank = 0;
-  static_for<0, 2 * DIM>([&](auto fconst) {
-    constexpr int f = decltype(fconst)::value;
-    const uint32_t mode = face_mode(code, f);
-    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
-    if (mode != MODE_NONE && fi >= 0) {
-      if constexpr (BPRE) {
-        face_rhs<DIM, P_, DF>(Pb, sa, code, f, e, d, Bax[f >> 1], b);
-      } else {
-        double Brow[NF];
-        brow64<DIM, P_>(blk, sa, mode, f, fi, mbase + mrank, om0, om1, om2, Brow);
-        face_rhs<DIM, P_, DF>(Pb, sa, code, f, e, d, Brow, b);
-      }
-    }
-    if (mode == MODE_MIXED) ++mrank;
-  });
-  // psi_i = sum_j Ainv[i][j] b_j, b_j from lane j of the segment; two accumulation chains
-  double x0 = 0.0, x1 = 0.0;
-  static_for<0, N>([&](auto jconst) {
-    constexpr int j = decltype(jconst)::value;
-    const double bj = __shfl_sync(FULL, b, j, W);
-    if (j & 1) x1 = fma(ainv[j], bj, x1);
-    else x0 = fma(ainv[j], bj, x0);
-  });
-  if (row) {
-    const double x = x0 + x1;
-    const int64_t o = ((int64_t)d * E + e) * N + i;
-    sa.psi_new[o] = x;
-    if (sa.psi_new_h != nullptr) {
-      const float h = (float)x;
-      sa.psi_new_h[o] = h;
-      sa.psi_new_l[o] = (float)(x - (double)h);
-    }
-  }
-  publish<DF, W>(Pb, sa, e, d, valid, i);
-}
-
-// Inverse of the local matrix of one (e, d) pair by Gauss-Jordan elimination with partial
-// pivoting in FP64 (row-per-lane, as gj32), stored in the layout bodyinv reads.  The matrix is
-// assembled exactly as in body64.
-template <int DIM, int P_>
-__device__ __forceinline__ void invert_pair(const DevProblem& Pb, const SweepArgs& sa, int64_t q, bool valid,
-                                            int lane) {
-  using S = Shape<DIM, P_>;
-  constexpr int N = S::N, NF = S::NF, W = S::W;
-  constexpr unsigned FULL = 0xffffffffu;
-  const int i = lane % W;
-  const int64_t E = Pb.E;
-  const int d = valid ? (int)(q / E) : 0;
-  const int64_t e = valid ? q % E : 0;
-  const bool row = valid && (i < N);
-  const double om0 = Pb.omega[d * 3 + 0], om1 = Pb.omega[d * 3 + 1], om2 = Pb.omega[d * 3 + 2];
-  const double* blk = Pb.elem + e * Pb.blk;
-  double a[N];
-  if (row) {
-    const double st = Pb.sig_t[e];
-    static_for<0, N>([&](auto jconst) {
-      constexpr int j = decltype(jconst)::value;
-      double v = om0 * __ldg(blk + j * N + i);
-      v = fma(om1, __ldg(blk + N * N + j * N + i), v);
-      if (DIM == 3) v = fma(om2, __ldg(blk + 2 * N * N + j * N + i), v);
-      a[j] = fma(st, __ldg(blk + DIM * N * N + j * N + i), v);
-    });
-  } else {
-    static_for<0, N>([&](auto jconst) { a[decltype(jconst)::value] = 0.0; });
-  }
-  const uint32_t code = valid ? sa.facecode[(int64_t)d * E + e] : 0u;
-  const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[(int64_t)d * E + e] : 0;
-  int mrank = 0;
-  static_for<0, 2 * DIM>([&](auto fconst) {
-    constexpr int f = decltype(fconst)::value;
-    const uint32_t mode = face_mode(code, f);
-    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
-    if (mode != MODE_NONE && fi >= 0) {
-      double Brow[NF];
-      brow64<DIM, P_>(blk, sa, mode, f, fi, mbase + mrank, om0, om1, om2, Brow);
-      static_for<0, NF>([&](auto jconst) {
-        constexpr int fj = decltype(jconst)::value;
-        a[fvi<DIM, P_>(f, fj)] += Brow[fj];
-      });
-    }
-    if (mode == MODE_MIXED) ++mrank;
-  });
-  // Gauss-Jordan on [A | I]: see gj32 for the bookkeeping (V in pivot-step order)
-  double v[N];
-  int plk[N];
-  bool used = !row;
-  double myinv = 0.0;
-  int myk = -1;
-  static_for<0, N>([&](auto jconst) { v[decltype(jconst)::value] = 0.0; });
-  static_for<0, N>([&](auto kconst) {
-    constexpr int k = decltype(kconst)::value;
-    const unsigned hw = (unsigned)((unsigned long long)__double_as_longlong(a[k]) >> 32);
-    const unsigned key = used ? 0u : ((hw & 0x7fffffe0u) | (unsigned)(31 - lane));
-    const int pl = seg_argmax_key<W>(key, lane);
-    plk[k] = pl;
-    const double inv = nr_rcp(__shfl_sync(FULL, a[k], pl, W));
-    const bool me = (lane == pl);
-    if (me) {
-      used = true;
-      myk = k;
-      myinv = inv;
-      v[k] = 1.0;
-    }
-    const double l = me ? 0.0 : a[k] * inv;
-    static_for<k + 1, N>([&](auto jconst) {
-      constexpr int j = decltype(jconst)::value;
-      a[j] = fma(-l, __shfl_sync(FULL, a[j], pl, W), a[j]);
-    });
-    static_for<0, k + 1>([&](auto jconst) {
-      constexpr int j = decltype(jconst)::value;
-      v[j] = fma(-l, __shfl_sync(FULL, v[j], pl, W), v[j]);
-    });
-  });
-  // the lane of step k holds row k of the inverse: Ainv[k][row of plk[m]] = v[m] / pivot
-  if (row && myk >= 0) {
-    double* out = sa.inv + q * (N * N) + myk;
-    static_for<0, N>([&](auto mconst) {
-      constexpr int m = decltype(mconst)::value;
-      out[(plk[m] % W) * N] = v[m] * myinv;
-    });
-  }
-}
-
 // ------------------------------------------------------------------ mixed form, FP64 residual
 //   A32 = fl32 assembly of A from the FP32 factor copy; b in FP64;
 //   xhat = A32^{-1} fl32(b); r = b - A64 xhat (FP64 row); psi = xhat + A32^{-1} fl32(r).
@@ -957,11 +773,18 @@ __device__ __forceinline__ void bodyds(const DevProblem& Pb, const SweepArgs& sa
   publish<DF, W>(Pb, sa, e, d, valid, i);
 }
 
+}  // namespace sn
+
+#include "inverse_body.cuh"
+
+namespace sn {
+
 template <int DIM, int P_, int PREC, bool DF>
 __device__ __forceinline__ void solve_item(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid,
                                            int lane) {
   if constexpr (PREC == SN_PREC_FP64) body64<DIM, P_, DF>(Pb, sa, pr, valid, lane);
   else if constexpr (PREC == SN_PREC_FP64_INV) bodyinv<DIM, P_, DF>(Pb, sa, pr, valid, lane);
+  else if constexpr (PREC == SN_PREC_DS_INV) bodydsinv<DIM, P_, DF>(Pb, sa, pr, valid, lane);
   else if constexpr (PREC == SN_PREC_MIXED) bodymx<DIM, P_, DF>(Pb, sa, pr, valid, lane);
   else bodyds<DIM, P_, DF>(Pb, sa, pr, valid, lane);
 }

@@ -76,9 +76,9 @@ static cudaError_t launch_flow_t(const DevProblem& P, const SweepArgs& sa, const
 }  // namespace sn
 
 namespace sn {
-// Stored-inverse form (sweep_inv.cu), dispatched on the problem's (dim, p).
-cudaError_t launch_level_t_inv(const DevProblem& P, const SweepArgs& sa, const int32_t* pairs, int64_t count,
-                               cudaStream_t s);
-cudaError_t launch_flow_t_inv(const DevProblem& P, const SweepArgs& sa, const int32_t* pairs, int64_t count,
-                              unsigned long long* head, int blocks_per_sm, cudaStream_t s);
+// Stored-inverse forms (sweep_inv.cu), dispatched on the form and the problem's (dim, p).
+cudaError_t launch_level_t_inv(const DevProblem& P, int precision, const SweepArgs& sa, const int32_t* pairs,
+                               int64_t count, cudaStream_t s);
+cudaError_t launch_flow_t_inv(const DevProblem& P, int precision, const SweepArgs& sa, const int32_t* pairs,
+                              int64_t count, unsigned long long* head, int blocks_per_sm, cudaStream_t s);
 }  // namespace sn

@@ -29,7 +29,7 @@ def make_ctxs(probs, stream):
     return ctxs
 
 
-@pytest.mark.parametrize("prec", [0, 2, 3])
+@pytest.mark.parametrize("prec", [0, 2, 3, 4])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_batch_steps_equal_single_problem_steps(prec, mode):
     import paper_1810_11080_gb300 as g

@@ -26,7 +26,7 @@ def _status(fn, *a, **k):
     return g.SN_OK
 
 
-@pytest.mark.parametrize("prec", [0, 2, 3])
+@pytest.mark.parametrize("prec", [0, 2, 3, 4])
 def test_dataflow_wait_limit_gives_timeout_then_recovers(prec):
     prob = si.make_config("2d_smooth_q3_p3_s8", n=24)
     ctx, _ = gpu_ctx(prob, "face")
@@ -110,7 +110,8 @@ def test_invalid_inputs():
     assert _status(ctx.sn_set_launch, 7, 0) == g.SN_EINVAL
     ctx.sn_build_graph("face", 10)
     z = np.zeros((len(prob.w), prob.mesh.n_elem, 4))
-    assert _status(ctx.sn_sweep, np.zeros((prob.mesh.n_elem, 4)), z, z.copy(), 4) == g.SN_EINVAL
+    assert _status(ctx.sn_sweep, np.zeros((prob.mesh.n_elem, 4)), z, z.copy(), 5) == g.SN_EINVAL
+    assert _status(ctx.sn_prepare_inverse, g.SN_PREC_MIXED_DS) == g.SN_EINVAL
 
 
 def test_calls_out_of_order():

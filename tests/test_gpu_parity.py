@@ -102,9 +102,15 @@ def test_stored_inverses_follow_new_materials():
     out2 = np.zeros_like(psi_old)
     ctx.sn_sweep(phi, psi_old, out2, 3)
     assert np.array_equal(out2, out)
+    # the double-single layout of the same records, then the FP64 one again
+    out3 = np.zeros_like(psi_old)
+    ctx.sn_sweep(phi, psi_old, out3, 4)
+    check_mixed(out3, ref2, "stored inverses, double-single application")
+    ctx.sn_sweep(phi, psi_old, out2, 3)
+    assert np.array_equal(out2, out)
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 4])
 @pytest.mark.parametrize("p", [2, 3])
 def test_mixed_sweep_with_direction_sources_and_inflow(p, prec):
     prob = si.make_config("2d_sine_q2_p1_s4", n=6, p=p)
@@ -180,7 +186,7 @@ def check_mixed(out, ref, what):
     assert np.all(np.abs(out - ref) <= MIXED_ELEM_RTOL * np.abs(ref) + MIXED_ELEM_ATOL * scale), (what, elem.max())
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 4])
 @pytest.mark.parametrize("case", ["2d_sine_16", "2d_smooth_10_p3_s8", "3d_twist_4_p2_s8", "2d_reoriented_6_p2",
                                   "3d_twist_3_p1_s4_reoriented", "3d_twist_3_p2_s4_reoriented"])
 def test_mixed_sweep_accuracy(case, prec):
@@ -194,7 +200,7 @@ def test_mixed_sweep_accuracy(case, prec):
     check_mixed(out, ref, f"mixed(prec={prec}) single sweep {case}")
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 4])
 @pytest.mark.parametrize("case", ["2d_sine_16", "3d_twist_4_p2_s8"])
 def test_mixed_source_iteration_reaches_same_tolerance(case, prec):
     prob = CASES[case]()
@@ -219,7 +225,7 @@ def test_mixed_source_iteration_reaches_same_tolerance(case, prec):
     assert rel_l2(phi, ref["phi"]) <= 1e-6          # 1e-8 residual: the iteration error dominates
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("case", ["2d_sine_16", "2d_smooth_10_p3_s8", "3d_twist_4_p2_s8", "2d_reoriented_6_p2",
                                   "3d_twist_3_p1_s4_reoriented", "2d_sine_8_p2_strong"])
 def test_dataflow_schedule_matches_level_schedule(case, prec):
@@ -238,7 +244,7 @@ def test_dataflow_schedule_matches_level_schedule(case, prec):
         assert np.array_equal(out, ref), (bps, rel_l2(out, ref))
 
 
-@pytest.mark.parametrize("prec", [0, 2, 3])
+@pytest.mark.parametrize("prec", [0, 2, 3, 4])
 def test_dataflow_source_iteration(prec):
     import paper_1810_11080_gb300 as g
     prob = CASES["3d_twist_4_p2_s8"]()
@@ -286,7 +292,7 @@ def bench_3d():
 
 
 @pytest.mark.parametrize("launch", ["levels", "dataflow"])
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("shape", ["bench_2d", "bench_3d"])
 def test_benchmark_size_sweep_parity(shape, prec, launch, request):
     import paper_1810_11080_gb300 as g
