@@ -436,6 +436,8 @@ def run_gpu(args):
         out["learned"] = run_learned(g, torch, args)
     if not args.no_dsa_thick:
         out["dsa_thick"] = run_dsa_thick(g, torch, args)
+    if not args.no_straightening:
+        out["straightening"] = run_straightening(g, torch, args)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     return out
@@ -588,6 +590,44 @@ def run_dsa_thick(g, torch, args):
             out[name]["last_cg_iters"] = ctx.sn_dsa_last_iters()
     out["speedup_dsa"] = out["plain_mixed_ds"]["seconds"] / out["dsa_mixed_ds"]["seconds"]
     ctx.close()
+    return out
+
+
+def run_straightening(g, torch, args):
+    """The paper's straightened low-order comparison (Sec. 4.1) on a quarter annulus (radii 0.5
+    and 1, curved boundaries): its manufactured solution solved with cubic elements (p = 3) on a
+    cubic (Q3) mesh, coarse and refined, and with linear elements (p = 1) on the straightened
+    meshes (each element divided 3 times per direction, straight-sided Q1 cells).  L2 error of the
+    scalar flux against the exact one at the volume quadrature points, unknowns, lagged arcs, time
+    of the graph build and of the solve to a 1e-12 change (stored inverses, double-single)."""
+    import sn_inputs.configs as C
+    from sn_inputs.mms import annulus_mms
+    out = {"workload": "quarter annulus rho in [0.5, 1], S4 (12 dirs), sigma_t=1, sigma_s=0.5, manufactured "
+                       "psi = [(1 + x^2 + y^2)/2 + cos(3x + 3y/2)] (mu^2 + eta)"}
+    for label, prob in (("ho_coarse", C.annulus_problem(12, 24, 3, 3)),
+                        ("ho_refined", C.annulus_problem(24, 48, 3, 3)),
+                        ("straightened_coarse", C.straightened_problem(C.annulus_problem(12, 24, 3, 3), 3, 1)),
+                        ("straightened_refined", C.straightened_problem(C.annulus_problem(24, 48, 3, 3), 3, 1))):
+        prob, fex, fac = annulus_mms(prob)
+        stream = torch.cuda.Stream()
+        ctx = g.setup_problem(prob, device=0, stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        gs = ctx.sn_build_graph("face", 10)
+        t1 = time.perf_counter()
+        E, N = prob.mesh.n_elem, (prob.p + 1) ** 2
+        phi = np.zeros((E, N))
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        r = ctx.sn_source_iterate(1e-12, 500, g.SN_PREC_DS_INV, phi_out=phi)
+        t3 = time.perf_counter()
+        err = ctx.sn_l2_error(phi, fac * fex(ctx.sn_volume_points()))
+        out[label] = {"elements": int(E), "geometry_order": int(prob.mesh.r), "dg_order": int(prob.p),
+                      "unknowns": int(E * N), "l2_error": err, "removed_arcs": int(gs["n_removed"]),
+                      "iters": r["iters"], "converged": r["converged"], "graph_s": t1 - t0, "solve_s": t3 - t2}
+        ctx.close()
+    out["error_ratio_straightened_vs_ho_coarse"] = out["straightened_coarse"]["l2_error"] / out["ho_coarse"]["l2_error"]
+    out["error_ratio_straightened_vs_ho_refined"] = (out["straightened_refined"]["l2_error"] /
+                                                     out["ho_refined"]["l2_error"])
     return out
 
 
@@ -824,6 +864,8 @@ def main():
                     help="relative residual of the conjugate-gradient DSA solve in the accelerated legs")
     ap.add_argument("--dsa-max-cg", type=int, default=100, help="CG iteration cap of one DSA solve")
     ap.add_argument("--no-dsa-thick", action="store_true", help="skip the optically thick DSA measurement")
+    ap.add_argument("--no-straightening", action="store_true",
+                    help="skip the curved high-order vs straightened low-order comparison")
     ap.add_argument("--learned-n", type=int, default=48, help="mesh size n^3 of the learned-predictor measurement")
     ap.add_argument("--launch", default="auto", choices=["auto", "levels", "dataflow"],
                     help="sweep schedule per form: the autotuner's choice, one launch per level, or one persistent dataflow launch")

@@ -251,6 +251,18 @@ sn_status sn_si_begin(sn_ctx* ctx, const double* phi0);
 sn_status sn_si_step(sn_ctx* ctx, int precision, double* residual, float* ms_sweep);
 sn_status sn_si_result(sn_ctx* ctx, double* phi_out, double* psi_out);
 
+/* Volume quadrature points and L2 errors (for manufactured solutions; no counterpart in the
+ * paper's solver, whose Sec. 4.1 reports such errors).  Valid after sn_set_discretization.
+ *   sn_num_volume_points: Q, the number of volume quadrature points per element (0 before).
+ *   sn_volume_points: xq [n_elem][Q][dim] receives their physical positions x_e(xi_q) [eq. 1].
+ *   sn_l2_error: *err = sqrt(sum_e sum_q w_q |J_e(xi_q)| (sum_n u_n(xi_q) phi[e][n] - exact_q[e][q])^2),
+ *     phi [n_elem][N] a nodal field (e.g. the scalar flux), exact_q [n_elem][Q] the reference
+ *     field's values at the points of sn_volume_points.
+ * Host or device pointers.  Errors: SN_ESTATE (no discretization), SN_EINVAL (null array). */
+int32_t sn_num_volume_points(const sn_ctx* ctx);
+sn_status sn_volume_points(sn_ctx* ctx, double* xq);
+sn_status sn_l2_error(sn_ctx* ctx, const double* phi, const double* exact_q, double* err);
+
 /* ---- Batches: many independent problems in one persistent launch (no counterpart in the
  * paper; each problem is the method above).  The problems are contexts of the same dimension
  * on the same device whose graphs are built; they may differ in mesh size, geometry order, DG

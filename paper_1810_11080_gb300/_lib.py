@@ -29,7 +29,8 @@ EXPORTED = ["sn_create", "sn_destroy", "sn_last_error", "sn_set_mesh", "sn_set_d
             "sn_mlp_forward", "sn_mlp_grad", "sn_mlp_train", "sn_predictor_features", "sn_predictor_init_targets",
             "sn_predictor_corr_data", "sn_source_iterate_learned", "sn_predictor_initial_phi",
             "sn_quadrature_level_symmetric", "sn_set_spin_limit", "sn_set_dsa", "sn_dsa_correction",
-            "sn_dsa_last_iters", "sn_prepare_inverse", "sn_release_inverse"]
+            "sn_dsa_last_iters", "sn_prepare_inverse", "sn_release_inverse", "sn_num_volume_points",
+            "sn_volume_points", "sn_l2_error"]
 
 
 class sn_graph_stats(ctypes.Structure):
@@ -118,6 +119,9 @@ def load(path=LIB_PATH):
         "sn_dsa_last_iters": (ctypes.c_int32, [P]),
         "sn_prepare_inverse": (I, [P, I, ctypes.POINTER(ctypes.c_float)]),
         "sn_release_inverse": (I, [P]),
+        "sn_num_volume_points": (ctypes.c_int32, [P]),
+        "sn_volume_points": (I, [P, P]),
+        "sn_l2_error": (I, [P, P, P, ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -212,6 +216,7 @@ class Context:
 
     def sn_set_mesh(self, dim, n_elem, r, ctrl, face_nbr, nbr_face, orient):
         self._n_elem = int(n_elem)
+        self._dim = int(dim)
         return self._check(self._lib.sn_set_mesh(self._c, dim, n_elem, r, _ptr(ctrl, np.float64, "ctrl"),
                                                  _ptr(face_nbr, np.int64, "face_nbr"),
                                                  _ptr(nbr_face, np.int32, "nbr_face"),
@@ -298,6 +303,19 @@ class Context:
 
     def sn_release_inverse(self):
         return self._check(self._lib.sn_release_inverse(self._c))
+
+    def sn_volume_points(self):
+        """[n_elem][Q][dim] physical positions of the volume quadrature points."""
+        Q = self._lib.sn_num_volume_points(self._c)
+        out = np.zeros((self._n_elem, Q, self._dim))
+        self._check(self._lib.sn_volume_points(self._c, _ptr(out, np.float64, "xq")))
+        return out
+
+    def sn_l2_error(self, phi, exact_q):
+        err = ctypes.c_double()
+        self._check(self._lib.sn_l2_error(self._c, _ptr(phi, np.float64, "phi"), _ptr(exact_q, np.float64, "exact_q"),
+                                          ctypes.byref(err)))
+        return err.value
 
     def sn_set_spin_limit(self, polls):
         return self._check(self._lib.sn_set_spin_limit(self._c, int(polls)))

@@ -154,6 +154,7 @@ sn::DevProblem sn_ctx::dev() const {
   P.off_B = tab_off[7];
   P.off_dB = tab_off[8];
   P.off_dV = tab_off[9];
+  P.off_V = tab_off[10];
   P.elem = d_elem;
   P.blk = blk;
   P.elem32 = d_elem32;
@@ -348,6 +349,7 @@ sn_status sn_set_discretization(sn_ctx* c, int p, int face_subdiv) {
   add(7, c->tab.B);
   add(8, c->tab.dB);
   add(9, c->tab.dV);
+  add(10, c->tab.V);
   SN_CUDA(c, dalloc(c->d_tab, packed.size()));
   SN_CUDA(c, cudaMemcpy(c->d_tab, packed.data(), packed.size() * 8, cudaMemcpyHostToDevice));
   c->disc_set = true;
@@ -967,6 +969,54 @@ sn_status sn_sweep(sn_ctx* c, const double* phi_in, const double* psi_old, doubl
   }
   if (host_out || !is_device_ptr(phi_in) || !is_device_ptr(psi_old)) SN_CUDA(c, cudaStreamSynchronize(c->stream));
   return check_err(c);
+}
+
+int32_t sn_num_volume_points(const sn_ctx* c) { return (c && c->disc_set) ? c->tab.Q : 0; }
+
+sn_status sn_volume_points(sn_ctx* c, double* xq) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->mesh_set && c->disc_set, SN_ESTATE, "mesh and discretization first");
+  SN_REQ(c, xq, SN_EINVAL, "null array");
+  cudaSetDevice(c->device);
+  const size_t n = (size_t)c->E * c->tab.Q * c->dim;
+  const bool dev_out = is_device_ptr(xq);
+  double* d = dev_out ? xq : nullptr;
+  if (!dev_out) SN_CUDA(c, dalloc(d, n));
+  DevProblem P = c->dev();
+  cudaError_t e = launch_volume_points(P, nullptr, nullptr, d, nullptr, c->stream);
+  if (e == cudaSuccess && !dev_out) e = cudaMemcpyAsync(xq, d, n * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (!dev_out) dfree(d);
+  SN_CUDA(c, e);
+  c->launches++;
+  return SN_OK;
+}
+
+sn_status sn_l2_error(sn_ctx* c, const double* phi, const double* exact_q, double* err) {
+  if (!c) return SN_EINVAL;
+  SN_REQ(c, c->mesh_set && c->disc_set, SN_ESTATE, "mesh and discretization first");
+  SN_REQ(c, phi && exact_q && err, SN_EINVAL, "null array");
+  cudaSetDevice(c->device);
+  const size_t nphi = (size_t)c->E * c->N, nq = (size_t)c->E * c->tab.Q;
+  double *dphi = nullptr, *dex = nullptr, *dacc = nullptr;
+  cudaError_t e = dalloc(dphi, nphi);
+  if (e == cudaSuccess) e = dalloc(dex, nq);
+  if (e == cudaSuccess) e = dalloc(dacc, 1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dphi, phi, nphi * 8, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dex, exact_q, nq * 8, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dacc, 0, 8, c->stream);
+  DevProblem P = c->dev();
+  if (e == cudaSuccess) e = launch_volume_points(P, dphi, dex, nullptr, dacc, c->stream);
+  double acc = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&acc, dacc, 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  dfree(dphi);
+  dfree(dex);
+  dfree(dacc);
+  SN_CUDA(c, e);
+  c->launches++;
+  *err = std::sqrt(acc);
+  return SN_OK;
 }
 
 sn_status sn_moment(sn_ctx* c, const double* psi, const double* phi_prev, double* phi_out, double* residual) {

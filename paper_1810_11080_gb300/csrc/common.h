@@ -33,6 +33,7 @@ struct Tables {
   std::vector<double> B;                // [Q][N] DG basis at volume points
   std::vector<double> dB;               // [Q][N][dim] reference gradients
   std::vector<double> dV;               // [Q][Nv][dim] geometry basis reference gradients
+  std::vector<double> V;                // [Q][Nv] geometry basis values
 };
 
 void gauss_legendre(int n, std::vector<double>& t, std::vector<double>& w);
@@ -85,7 +86,7 @@ struct DevProblem {
   const double* q_dir;       // [M][E][N] or null
   const double* psi_inc;     // [M][n_bdr][Nf] or null
   const double* tab;         // packed tables (see TabOffsets)
-  int off_glv_t, off_glv_w, off_glf_t, off_glf_w, off_gll, off_geo, off_wq, off_B, off_dB, off_dV;
+  int off_glv_t, off_glv_w, off_glf_t, off_glf_w, off_gll, off_geo, off_wq, off_B, off_dB, off_dV, off_V;
   const double* elem;        // [E][blk] element factors
   int64_t blk;               // doubles per element block
   const float* elem32;       // [E][blk] FP32 rounding of elem (mixed forms) or null
@@ -150,6 +151,10 @@ inline int64_t elem_block_doubles(int dim, int N, int Nf) {
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_geometry(const DevProblem& P, double* elem, int* bad_flag, cudaStream_t s);
+// Physical volume quadrature points (xq [E][Q][dim], may be null) and, if phi is not null,
+// acc[0] += sum_e sum_q w_q |J_q| (sum_n B_qn phi_en - exact_q[e][q])^2 (geom.cu).
+cudaError_t launch_volume_points(const DevProblem& P, const double* phi, const double* exact_q, double* xq,
+                                 double* acc, cudaStream_t s);
 cudaError_t launch_elem_to_fp32(const DevProblem& P, float* elem32, float* elem32lo, cudaStream_t s);
 cudaError_t launch_mass_lu(const DevProblem& P, double* lu, int32_t* perm, cudaStream_t s);
 cudaError_t launch_weights(const DevProblem& P, const int32_t* iface, int64_t n_iface, int weighting,
@@ -214,7 +219,7 @@ struct sn_ctx {
   float* d_elem32 = nullptr;
   float* d_elem32lo = nullptr;
   int64_t blk = 0;
-  int tab_off[10] = {0};
+  int tab_off[11] = {0};
   // graph
   bool graph_ready = false;
   uint32_t* d_facecode = nullptr;

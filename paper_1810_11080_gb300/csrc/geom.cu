@@ -144,3 +144,68 @@ cudaError_t launch_elem_to_fp32(const DevProblem& P, float* elem32, float* elem3
 }
 
 }  // namespace sn
+
+namespace sn {
+
+// Volume quadrature points of every element and the squared L2 distance of a nodal field from
+// given point values (for manufactured-solution errors): one CTA per element,
+//   x_q = sum_m x_m v_m(xi_q),  err^2 += sum_q w_q |J_q| (sum_n u_n(xi_q) phi_n - exact_q)^2.
+template <int DIM>
+__global__ void volume_points_kernel(DevProblem P, const double* __restrict__ phi, const double* __restrict__ exact_q,
+                                     double* __restrict__ xq, double* acc) {
+  __shared__ double sctrl[64 * 3];
+  __shared__ double part[4];
+  const int64_t e = blockIdx.x;
+  const int N = P.N, Q = P.Q, Nv = P.Nv;
+  const double* wq = tabp(P, P.off_wq);
+  const double* B = tabp(P, P.off_B);
+  const double* dV = tabp(P, P.off_dV);
+  const double* V = tabp(P, P.off_V);
+  for (int t = threadIdx.x; t < Nv * DIM; t += blockDim.x) sctrl[t] = P.ctrl[e * Nv * DIM + t];
+  __syncthreads();
+  double local = 0.0;
+  for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+    double J[DIM][DIM], x[DIM];
+    for (int i = 0; i < DIM; ++i) {
+      x[i] = 0.0;
+      for (int j = 0; j < DIM; ++j) J[i][j] = 0.0;
+    }
+    for (int m = 0; m < Nv; ++m) {
+      const double v = V[(size_t)q * Nv + m];
+      for (int i = 0; i < DIM; ++i) {
+        x[i] += sctrl[m * DIM + i] * v;
+        for (int j = 0; j < DIM; ++j) J[i][j] += sctrl[m * DIM + i] * dV[((size_t)q * Nv + m) * DIM + j];
+      }
+    }
+    if (xq != nullptr)
+      for (int i = 0; i < DIM; ++i) xq[(e * Q + q) * DIM + i] = x[i];
+    if (phi != nullptr) {
+      double det;
+      if (DIM == 2) {
+        det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      } else {
+        det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+              J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+      }
+      double val = 0.0;
+      for (int n = 0; n < N; ++n) val += B[(size_t)q * N + n] * phi[e * N + n];
+      const double dlt = val - exact_q[e * Q + q];
+      local += wq[q] * det * dlt * dlt;
+    }
+  }
+  if (phi == nullptr) return;
+  for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = local;
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(acc, part[0] + part[1] + part[2] + part[3]);
+}
+
+cudaError_t launch_volume_points(const DevProblem& P, const double* phi, const double* exact_q, double* xq,
+                                 double* acc, cudaStream_t s) {
+  if (P.Nv * P.dim > 64 * 3) return cudaErrorInvalidValue;
+  if (P.dim == 2) volume_points_kernel<2><<<(unsigned)P.E, 128, 0, s>>>(P, phi, exact_q, xq, acc);
+  else volume_points_kernel<3><<<(unsigned)P.E, 128, 0, s>>>(P, phi, exact_q, xq, acc);
+  return cudaGetLastError();
+}
+
+}  // namespace sn

@@ -103,6 +103,7 @@ void build_tables(Tables& T, int dim, int p, int r) {
   T.B.assign((size_t)T.Q * T.N, 0.0);
   T.dB.assign((size_t)T.Q * T.N * dim, 0.0);
   T.dV.assign((size_t)T.Q * T.Nv * dim, 0.0);
+  T.V.assign((size_t)T.Q * T.Nv, 0.0);
   for (int q = 0; q < T.Q; ++q) {
     int qi[3];
     double x[3];
@@ -125,6 +126,7 @@ void build_tables(Tables& T, int dim, int p, int r) {
       for (int k = 0, rem = m; k < dim; ++k, rem /= (r + 1)) mi[k] = rem % (r + 1);
       for (int j = 0; j < dim; ++j)
         T.dV[((size_t)q * T.Nv + m) * dim + j] = tensor_value(T.geo.data(), r + 1, mi, x, dim, j);
+      T.V[(size_t)q * T.Nv + m] = tensor_value(T.geo.data(), r + 1, mi, x, dim, -1);
     }
   }
 }

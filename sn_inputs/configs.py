@@ -107,3 +107,27 @@ def batch_problems(count=256, seed=31, nmin=8, nmax=64):
         out.append(Problem(name=f"batch{i}", mesh=mesh, p=p, omega=om, w=w, sigma_t=st, sigma_s=c * st,
                            q=np.ones((mesh.n_elem, N)), sn_order=sn))
     return out
+
+
+def annulus_problem(n_rho, n_theta, r, p, sn=4):
+    """Quarter annulus rho in [0.5, 1] (curved inner and outer boundaries) as an n_rho x n_theta
+    Q_r mesh, DG order p, level-symmetric S_sn, sigma_t = 1, sigma_s = 0.5, q = 1 (the materials
+    and sources are replaced by sn_inputs.mms.annulus_mms for manufactured-solution runs)."""
+    from .mesh import annulus_mesh
+    mesh = annulus_mesh(n_rho, n_theta, r)
+    om, w = level_symmetric(sn, 2)
+    ne = mesh.n_elem
+    N = (p + 1) ** 2
+    return Problem(name=f"annulus_{n_rho}x{n_theta}_r{r}_p{p}", mesh=mesh, p=p, omega=om, w=w,
+                   sigma_t=np.ones(ne), sigma_s=0.5 * np.ones(ne), q=np.ones((ne, N)), sn_order=sn)
+
+
+def straightened_problem(prob, n_ref, p=1):
+    """The same problem on the straightened mesh (sn_inputs.mesh.straighten: every element divided
+    n_ref times per axis, straight-sided Q_1 sub-elements) with DG order p (low order by default)."""
+    from .mesh import straighten
+    mesh = straighten(prob.mesh, n_ref)
+    ne = mesh.n_elem
+    N = (p + 1) ** mesh.dim
+    return Problem(name=prob.name + f"_straight{n_ref}", mesh=mesh, p=p, omega=prob.omega, w=prob.w,
+                   sigma_t=np.ones(ne), sigma_s=0.5 * np.ones(ne), q=np.ones((ne, N)), sn_order=prob.sn_order)

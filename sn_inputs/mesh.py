@@ -299,3 +299,62 @@ def disp_twist(total_angle=np.pi / 3):
         out[:, 1] = yn - y
         return out
     return f
+
+
+# ---------------------------------------------------------------- curved-boundary domain, straightening
+
+def annulus_mesh(n_rho, n_theta, r, rho=(0.5, 1.0), theta=(0.0, 0.5 * np.pi)):
+    """Sector of an annulus, rho in [rho0, rho1], theta in [theta0, theta1], as an n_rho x n_theta
+    grid of Q_r elements (element index i + n_rho j, i along rho).  The control points are the
+    exact polar images of the equispaced reference nodes, so inner and outer boundaries are
+    curved arcs represented to order r."""
+    def to_polar(X):
+        rr = rho[0] + (rho[1] - rho[0]) * X[:, 0]
+        th = theta[0] + (theta[1] - theta[0]) * X[:, 1]
+        return np.stack([rr * np.cos(th) - X[:, 0], rr * np.sin(th) - X[:, 1]], axis=1)
+    return structured_mesh((n_rho, n_theta), r, to_polar)
+
+
+def _lagrange_1d(nodes, j, x):
+    v = 1.0
+    for k, nk in enumerate(nodes):
+        if k != j:
+            v = v * (x - nk) / (nodes[j] - nk)
+    return v
+
+
+def straighten(mesh, n_ref):
+    """The straightened low-order mesh of a curved Q_r mesh: every element divided n_ref times
+    along each reference axis, the sub-cell vertices placed at their images under the element's
+    map, and those vertices taken as the nodes of a mesh of straight-sided Q_1 elements.  Shared
+    vertices of neighbouring elements are merged by position (rounded to 1e-10)."""
+    dim, r = mesh.dim, mesh.r
+    geo = [a / r for a in range(r + 1)]
+    t = [a / n_ref for a in range(n_ref + 1)]
+    # map weights of the sub-lattice points: [(n_ref+1)^dim][(r+1)^dim]
+    lat = list(itertools.product(*[range(n_ref + 1)] * dim))
+    lat = [tuple(reversed(l)) for l in lat]          # x fastest
+    W = np.zeros((len(lat), (r + 1) ** dim))
+    for a, l in enumerate(lat):
+        for m in range((r + 1) ** dim):
+            v = 1.0
+            for k in range(dim):
+                v *= _lagrange_1d(geo, (m // (r + 1) ** k) % (r + 1), t[l[k]])
+            W[a, m] = v
+    P = np.einsum("am,emd->ead", W, mesh.ctrl)       # [E][(n_ref+1)^dim][dim]
+    key = np.round(P.reshape(-1, dim) * 1e10).astype(np.int64)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    nodes = P.reshape(-1, dim)[first]
+    gid = inv.reshape(mesh.n_elem, len(lat))
+    lidx = {l: a for a, l in enumerate(lat)}
+    elem_nodes = []
+    for e in range(mesh.n_elem):
+        for cell in itertools.product(*[range(n_ref)] * dim):
+            cell = tuple(reversed(cell))
+            loc = []
+            for corner in itertools.product(*[range(2)] * dim):
+                corner = tuple(reversed(corner))
+                loc.append(gid[e, lidx[tuple(c + o for c, o in zip(cell, corner))]])
+            elem_nodes.append(loc)
+    elem_nodes = np.array(elem_nodes, dtype=np.int64)
+    return _finish(dim, 1, nodes, elem_nodes, ())
