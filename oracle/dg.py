@@ -187,7 +187,7 @@ def roots_01(c):
     return [srt[..., k] for k in range(D)]
 
 
-def face_rule(ctrl, r, dim, f, omega, nf, K):
+def face_rule(ctrl, r, dim, f, omega, nf, K, normal=None):
     """Per-direction face quadrature for local face f of the owner elements in ctrl.
 
     Returns s0, s1 (None in 2D), w, g with shape [F, D, P]; g = Omega_d . n_owner(s), n the
@@ -199,13 +199,18 @@ def face_rule(ctrl, r, dim, f, omega, nf, K):
         and c0/qq (qq != 0).  Roots outside (0,1) are replaced by 1.0; rho1 = min, rho2 = max.
         Each piece [lo, hi] carries the n_f GL points s = lo + (hi - lo) t_i, w = (hi - lo) w_i.
     3D: face_rule_3d (kink-aligned splitting in both face coordinates).
+    normal: (ctrl, s, aligned) -> scaled normals, for 2D faces of other element shapes
+    (default: face_normal of the tensor element's face f).
     """
     t, wt = gauss_legendre(nf)
+    if normal is None:
+        def normal(c, s, aligned=False):
+            return face_normal(c, r, f, s, aligned=aligned)
     F = ctrl.shape[0]
     D = omega.shape[0]
     om = [omega[:, k][None, :, None] for k in range(dim)]       # each [1, D, 1]
     if dim == 2:
-        nref = face_normal(ctrl, r, f, np.array([0.0, 0.5, 1.0]))   # [F, 3, 2]
+        nref = normal(ctrl, np.array([0.0, 0.5, 1.0]))              # [F, 3, 2]
         om2 = [omega[:, k][None, :] for k in range(dim)]
         g0 = dot_omega(om2, nref[:, None, 0, :])
         gh = dot_omega(om2, nref[:, None, 1, :])
@@ -242,7 +247,7 @@ def face_rule(ctrl, r, dim, f, omega, nf, K):
                 ws.append(ln * wt[i])
         s0 = np.stack(s0s, axis=-1)                     # [F, D, P]
         w = np.stack(ws, axis=-1)
-        nvec = face_normal(ctrl, r, f, s0, aligned=True)    # [F, D, P, 2]
+        nvec = normal(ctrl, s0, aligned=True)               # [F, D, P, 2]
         g = dot_omega(om, nvec)
         return s0, None, w, g
     return face_rule_3d(ctrl, r, f, omega, nf, K)
@@ -362,6 +367,7 @@ class Discretization:
         self.omega = np.asarray(prob.omega, dtype=np.float64)[:, :dim]
         self.w = np.asarray(prob.w, dtype=np.float64)
         self.M_dirs = self.omega.shape[0]
+        self.n_faces = 2 * dim
         self.fnode = [face_node_volume_index(p, dim, f) for f in range(2 * dim)]
         self._volume()
         self._faces()
@@ -424,12 +430,16 @@ class Discretization:
         return out
 
     # ---------------------------------------------------------------- faces
+    def _face_rule(self, ctrl, f, om):
+        """Face quadrature of face f of the elements in ctrl for the directions om (face_rule)."""
+        return face_rule(ctrl, self.r, self.dim, f, om, self.nf, self.K)
+
     def _faces(self):
         mesh = self.prob.mesh
         self.iface = []      # (owner, f, nbr, f_nbr, orient owner->nbr)
         self.bface = []      # (e, f) in increasing (e, f): the boundary-face numbering
         for e in range(self.E):
-            for f in range(2 * self.dim):
+            for f in range(self.n_faces):
                 n = int(mesh.face_nbr[e, f])
                 if n < 0:
                     self.bface.append((e, f))
@@ -459,11 +469,11 @@ class Discretization:
         out_n = np.zeros_like(out_o)
         bar_o = np.zeros_like(out_o)
         bar_n = np.zeros_like(out_o)
-        for f in range(2 * dim):
+        for f in range(self.n_faces):
             sel = np.nonzero(iface[:, 1] == f)[0] if len(iface) else np.zeros(0, dtype=np.int64)
             if len(sel) == 0:
                 continue
-            s0, s1, w, g = face_rule(ctrl[iface[sel, 0]], self.r, dim, f, om, self.nf, self.K)
+            s0, s1, w, g = self._face_rule(ctrl[iface[sel, 0]], f, om)
             ao = pos(-g) * w
             an = pos(g) * w
             phi_o = face_basis(self.gll, dim, s0, s1)
@@ -482,11 +492,11 @@ class Discretization:
         bface = np.array(self.bface, dtype=np.int64).reshape(-1, 2)
         bout = np.zeros((len(bface), D, Nf, Nf))
         bin_ = np.zeros_like(bout)
-        for f in range(2 * dim):
+        for f in range(self.n_faces):
             sel = np.nonzero(bface[:, 1] == f)[0] if len(bface) else np.zeros(0, dtype=np.int64)
             if len(sel) == 0:
                 continue
-            s0, s1, w, g = face_rule(ctrl[bface[sel, 0]], self.r, dim, f, om, self.nf, self.K)
+            s0, s1, w, g = self._face_rule(ctrl[bface[sel, 0]], f, om)
             phi = face_basis(self.gll, dim, s0, s1)
             bout[sel] = coupling_block(pos(g) * w, phi, phi)
             bin_[sel] = coupling_block(pos(-g) * w, phi, phi)
@@ -505,7 +515,7 @@ class Discretization:
         coup = []
         rhs_b = np.zeros(N)
         mesh = self.prob.mesh
-        for f in range(2 * self.dim):
+        for f in range(self.n_faces):
             n = int(mesh.face_nbr[e, f])
             idx = self.fnode[f]
             if n < 0:

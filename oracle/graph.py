@@ -115,7 +115,7 @@ def _siginv(disc, recv, recv_face, up_face, bar):
     Mt = disc.prob.sigma_t[uniq][:, None, None] * M
     LU, perm = lu_factor_batch(Mt)
     out = np.zeros((F, D))
-    for f in range(2 * disc.dim):
+    for f in range(disc.n_faces):
         sel = np.nonzero(recv_face == f)[0]
         if len(sel) == 0:
             continue

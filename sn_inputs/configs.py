@@ -31,6 +31,8 @@ class Problem:
 
     @property
     def n_dofs(self):
+        if getattr(self.mesh, "simplex", False):
+            return (self.p + 1) * (self.p + 2) // 2
         return (self.p + 1) ** self.mesh.dim
 
 
@@ -131,3 +133,19 @@ def straightened_problem(prob, n_ref, p=1):
     N = (p + 1) ** mesh.dim
     return Problem(name=prob.name + f"_straight{n_ref}", mesh=mesh, p=p, omega=prob.omega, w=prob.w,
                    sigma_t=np.ones(ne), sigma_s=0.5 * np.ones(ne), q=np.ones((ne, N)), sn_order=prob.sn_order)
+
+
+def triangle_problem(n, r, p, sn=4, amp=0.05, rotate_seed=None):
+    """n x n cells of [0,1]^2 cut into 2 n^2 counterclockwise triangles with P_r geometry,
+    interior nodes displaced by amp sin(2 pi x) sin(2 pi y) on both coordinates (zero on the
+    boundary), DG order p (P_p, (p+1)(p+2)/2 unknowns), S_sn, sigma_t = 1, sigma_s = 0.5, q = 1.
+    rotate_seed renumbers the triangles' local nodes by random rotations."""
+    from .mesh import triangle_mesh, rotate_triangles
+    mesh = triangle_mesh((n, n), r, disp_sine_2d(amp))
+    if rotate_seed is not None:
+        mesh = rotate_triangles(mesh, rotate_seed)
+    om, w = level_symmetric(sn, 2)
+    ne = mesh.n_elem
+    N = (p + 1) * (p + 2) // 2
+    return Problem(name=f"tri_{n}_r{r}_p{p}_s{sn}", mesh=mesh, p=p, omega=om, w=w, sigma_t=np.ones(ne),
+                   sigma_s=0.5 * np.ones(ne), q=np.ones((ne, N)), sn_order=sn)

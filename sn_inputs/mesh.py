@@ -21,6 +21,7 @@ class Mesh:
     nodes: np.ndarray = field(repr=False, default=None)       # [n_nodes][dim] global node positions
     elem_nodes: np.ndarray = field(repr=False, default=None)  # [n_elem][(r+1)^dim] global node ids
     shape: tuple = ()           # logical grid size (nx, ny[, nz])
+    simplex: bool = False       # triangles with P_r geometry (see triangle_mesh) instead of Q_r
 
     @property
     def n_elem(self):
@@ -358,3 +359,119 @@ def straighten(mesh, n_ref):
             elem_nodes.append(loc)
     elem_nodes = np.array(elem_nodes, dtype=np.int64)
     return _finish(dim, 1, nodes, elem_nodes, ())
+
+
+# ---------------------------------------------------------------- triangles (P_r geometry)
+#
+# Reference triangle {(xi, eta): xi, eta >= 0, xi + eta <= 1}, vertices v0 = (0,0), v1 = (1,0),
+# v2 = (0,1); faces (edges) counterclockwise f0: v0 -> v1, f1: v1 -> v2, f2: v2 -> v0, each with
+# its own coordinate s in [0, 1] from the first vertex to the second.  Node numbering of an
+# order-k node set: v0, v1, v2, the k - 1 interior nodes of f0, of f1, of f2 (each in increasing
+# s), then the interior nodes (k = 3: the centroid).  Geometry (P_r) nodes sit at s = a/r on the
+# edges.  orient[e][f] = 1 when the neighbour runs the shared edge in the opposite direction
+# (always, for counterclockwise elements), 0 otherwise.
+
+TRI_VERTS = ((0.0, 0.0), (1.0, 0.0), (0.0, 1.0))
+TRI_EDGES = ((0, 1), (1, 2), (2, 0))
+
+
+def tri_node_coords(k, edge_pos):
+    """Reference coordinates [(k+1)(k+2)/2][2] of the order-k node set whose edge nodes sit at
+    the 1D positions edge_pos[1..k-1] (k <= 3)."""
+    pts = [TRI_VERTS[0], TRI_VERTS[1], TRI_VERTS[2]]
+    for a, b in TRI_EDGES:
+        A, B = TRI_VERTS[a], TRI_VERTS[b]
+        for j in range(1, k):
+            s = edge_pos[j]
+            pts.append((A[0] + s * (B[0] - A[0]), A[1] + s * (B[1] - A[1])))
+    if k == 3:
+        pts.append((1.0 / 3.0, 1.0 / 3.0))
+    elif k > 3:
+        raise ValueError("orders up to 3")
+    return np.array(pts)
+
+
+def tri_edge_nodes(k, f):
+    """Local node indices of face f of an order-k node set, in increasing edge coordinate."""
+    a, b = TRI_EDGES[f]
+    return [a] + [3 + f * (k - 1) + j for j in range(k - 1)] + [b]
+
+
+def triangle_mesh(shape, r, disp=None):
+    """Each cell (i, j) of an nx x ny grid on [0,1]^2 cut by its diagonal (i, j) - (i+1, j+1) into
+    the counterclockwise triangles (i,j), (i+1,j), (i+1,j+1) (element 2 (i + nx j)) and
+    (i,j), (i+1,j+1), (i,j+1) (element 2 (i + nx j) + 1), with P_r geometry: the control points
+    are the lattice positions of the reference nodes, displaced by disp (as structured_mesh)."""
+    nx, ny = shape
+    ref = tri_node_coords(r, [a / r for a in range(r + 1)])      # geometry nodes
+    cx, cy = nx * r + 1, ny * r + 1                               # global lattice of spacing h / r
+    elem_nodes, pos = [], []
+    for j in range(ny):
+        for i in range(nx):
+            for tri in ((0, 1, 2), (0, 2, 3)):
+                corner = [(i, j), (i + 1, j), (i + 1, j + 1), (i, j + 1)]
+                P0, P1, P2 = (np.array(corner[t], dtype=float) for t in tri)
+                ids = []
+                for (xi, eta) in ref:
+                    g = P0 + xi * (P1 - P0) + eta * (P2 - P0)
+                    gi, gj = int(round(g[0] * r)), int(round(g[1] * r))
+                    ids.append(gi + cx * gj)
+                elem_nodes.append(ids)
+    elem_nodes = np.array(elem_nodes, dtype=np.int64)
+    gx, gy = np.meshgrid(np.arange(cx) / (nx * r), np.arange(cy) / (ny * r), indexing="xy")
+    X = np.stack([gx.reshape(-1), gy.reshape(-1)], axis=1)
+    if disp is not None:
+        X = X + disp(X.copy())
+    return _finish_tri(r, X, elem_nodes, tuple(shape))
+
+
+def _finish_tri(r, X, elem_nodes, shape):
+    n_elem = elem_nodes.shape[0]
+    face_nbr = -np.ones((n_elem, 3), dtype=np.int64)
+    nbr_face = -np.ones((n_elem, 3), dtype=np.int32)
+    orient = np.zeros((n_elem, 3), dtype=np.int32)
+    table = {}
+    for e in range(n_elem):
+        for f in range(3):
+            ids = elem_nodes[e][tri_edge_nodes(r, f)]
+            table.setdefault(frozenset(ids.tolist()), []).append((e, f))
+    for lst in table.values():
+        if len(lst) == 1:
+            continue
+        if len(lst) != 2:
+            raise ValueError("non-conforming mesh: an edge is shared by more than two elements")
+        (e, f), (e2, f2) = lst
+        a = elem_nodes[e][tri_edge_nodes(r, f)]
+        b = elem_nodes[e2][tri_edge_nodes(r, f2)]
+        code = 0 if np.array_equal(a, b) else (1 if np.array_equal(a, b[::-1]) else -1)
+        if code < 0:
+            raise ValueError("could not match edge orientation")
+        face_nbr[e, f], nbr_face[e, f], orient[e, f] = e2, f2, code
+        face_nbr[e2, f2], nbr_face[e2, f2], orient[e2, f2] = e, f, code
+    ctrl = np.ascontiguousarray(X[elem_nodes])
+    return Mesh(dim=2, r=r, ctrl=ctrl, face_nbr=face_nbr, nbr_face=nbr_face, orient=orient,
+                nodes=X, elem_nodes=elem_nodes, shape=shape, simplex=True)
+
+
+def rotate_triangles(mesh, seed):
+    """Renumber every triangle's local nodes by a random rotation of the reference triangle
+    (v0 v1 v2 -> v1 v2 v0 or v2 v0 v1); the physical mesh is unchanged, local faces and the
+    neighbours' face indices change."""
+    rng = np.random.default_rng(seed)
+    r = mesh.r
+    ne = mesh.n_elem
+    new_nodes = mesh.elem_nodes.copy()
+    nv = (r + 1) * (r + 2) // 2
+    for e in range(ne):
+        k = int(rng.integers(3))
+        if k == 0:
+            continue
+        perm = list(range(nv))
+        # vertex v_i -> v_{(i+k) % 3}; edge f interiors -> edge (f+k) % 3; centroid fixed
+        for i in range(3):
+            perm[i] = (i + k) % 3
+        for f in range(3):
+            for j in range(r - 1):
+                perm[3 + f * (r - 1) + j] = 3 + ((f + k) % 3) * (r - 1) + j
+        new_nodes[e] = mesh.elem_nodes[e][perm]
+    return _finish_tri(r, mesh.nodes, new_nodes, mesh.shape)

@@ -27,8 +27,26 @@ def _lag(nodes, j, x):
     return v
 
 
+def _tri_lagrange_values(nodes, pts):
+    """[len(pts)][len(nodes)] values of the Lagrange basis of the triangle node set `nodes`
+    (total degree k with (k+1)(k+2)/2 nodes) at `pts`, through the monomial Vandermonde."""
+    n = len(nodes)
+    k = {3: 1, 6: 2, 10: 3}[n]
+    mono = [(a, d - a) for d in range(k + 1) for a in range(d, -1, -1)]
+    V = np.array([[x ** a * y ** b for (a, b) in mono] for (x, y) in nodes])
+    C = np.linalg.inv(V)                                   # columns: node basis coefficients
+    P = np.array([[x ** a * y ** b for (a, b) in mono] for (x, y) in pts])
+    return P @ C
+
+
 def dg_node_positions(mesh, p):
-    """[n_elem][(p+1)^dim][dim] physical positions of the DG nodes."""
+    """[n_elem][N][dim] physical positions of the DG nodes."""
+    if getattr(mesh, "simplex", False):
+        from .mesh import tri_node_coords
+        dg = tri_node_coords(p, _gll(p))
+        geo = tri_node_coords(mesh.r, [a / mesh.r for a in range(mesh.r + 1)])
+        W = _tri_lagrange_values(geo, dg)                  # [N][Nv]
+        return np.einsum("nm,emd->end", W, mesh.ctrl)
     dim, r = mesh.dim, mesh.r
     g = _gll(p)
     geo = [a / r for a in range(r + 1)]
@@ -46,7 +64,19 @@ def dg_node_positions(mesh, p):
 
 def boundary_faces(mesh):
     """Boundary faces (e, f) in increasing (e, f) order: the library's boundary numbering."""
-    return [(e, f) for e in range(mesh.n_elem) for f in range(2 * mesh.dim) if mesh.face_nbr[e, f] < 0]
+    nfc = mesh.face_nbr.shape[1]
+    return [(e, f) for e in range(mesh.n_elem) for f in range(nfc) if mesh.face_nbr[e, f] < 0]
+
+
+def _face_ids(mesh, p, f):
+    if getattr(mesh, "simplex", False):
+        from .mesh import tri_edge_nodes
+        return tri_edge_nodes(p, f)
+    return face_node_ids(p, mesh.dim, f)
+
+
+def _n_face_nodes(mesh, p):
+    return p + 1 if getattr(mesh, "simplex", False) else (p + 1) ** (mesh.dim - 1)
 
 
 def face_node_ids(p, dim, f):
@@ -87,10 +117,10 @@ def annulus_mms(prob, sigma_t=1.0, sigma_s=0.5):
         qd[d] = (om[d, 0] * fx + om[d, 1] * fy) * ang[d] + sigma_t * f * ang[d] - sigma_s / (4 * np.pi) * f * phi_fac
     prob.q_dir = qd
     bf = boundary_faces(mesh)
-    nf = (prob.p + 1) ** (mesh.dim - 1)
+    nf = _n_face_nodes(mesh, prob.p)
     pin = np.zeros((len(w), len(bf), nf))
     for k, (e, fc) in enumerate(bf):
-        ids = face_node_ids(prob.p, mesh.dim, fc)
+        ids = _face_ids(mesh, prob.p, fc)
         pin[:, k, :] = f[e, ids][None, :] * ang[:, None]
     prob.psi_inc = pin
 
@@ -109,14 +139,14 @@ def attenuation(prob, sigma_t=2.0):
     ne = mesh.n_elem
     prob.sigma_t = sigma_t * np.ones(ne)
     prob.sigma_s = np.zeros(ne)
-    prob.q = np.zeros((ne, (prob.p + 1) ** mesh.dim))
-    prob.q_dir = None
     X = dg_node_positions(mesh, prob.p)
+    prob.q = np.zeros(X.shape[:2])
+    prob.q_dir = None
     bf = boundary_faces(mesh)
-    nf = (prob.p + 1) ** (mesh.dim - 1)
+    nf = _n_face_nodes(mesh, prob.p)
     pin = np.zeros((len(om), len(bf), nf))
     for k, (e, fc) in enumerate(bf):
-        ids = face_node_ids(prob.p, mesh.dim, fc)
+        ids = _face_ids(mesh, prob.p, fc)
         xb = X[e, ids, 0]
         for d in range(len(om)):
             x_in = 0.0 if om[d, 0] > 0 else 1.0
