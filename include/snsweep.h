@@ -102,6 +102,23 @@ const char* sn_last_error(const sn_ctx* ctx);
 sn_status sn_set_mesh(sn_ctx* ctx, int dim, int64_t n_elem, int r, const double* ctrl,
                       const int64_t* face_nbr, const int32_t* nbr_face, const int32_t* orient);
 
+/* Triangle mesh [Sec. 2: simplicial elements, P_r geometry]: as sn_set_mesh with dim = 2 (only;
+ * SN_EINVAL otherwise) and three faces per element.  Reference triangle {xi, eta >= 0,
+ * xi + eta <= 1}, vertices v0 = (0,0), v1 = (1,0), v2 = (0,1), counterclockwise faces f0 = v0 v1,
+ * f1 = v1 v2, f2 = v2 v0, each with the coordinate s in [0,1] from its first vertex to its second.
+ *   ctrl      [n_elem][(r+1)(r+2)/2][2] control points in the node order v0, v1, v2, the r - 1
+ *             interior nodes of f0, f1, f2 (at s = a/r, increasing s), then (r = 3) the centroid.
+ *   face_nbr, nbr_face, orient [n_elem][3]; orient 1 when the neighbour runs the shared face in
+ *   the opposite direction (counterclockwise neighbours always do), 0 when in the same.
+ * The DG basis is then P_p (sn_set_discretization, p = 1..3, (p+1)(p+2)/2 unknowns) on the same
+ * node pattern with the face nodes at the Gauss-Lobatto-Legendre positions of order p; volume
+ * integrals use the collapsed Gauss rule (xi = u, eta = v (1 - u)) with p + r points per
+ * direction.  Triangle problems are swept by the stored-inverse forms (SN_PREC_FP64_INV,
+ * SN_PREC_DS_INV); the other forms, diffusion acceleration, the flux predictor and batches
+ * return SN_EINVAL. */
+sn_status sn_set_mesh_simplex(sn_ctx* ctx, int dim, int64_t n_elem, int r, const double* ctrl,
+                              const int64_t* face_nbr, const int32_t* nbr_face, const int32_t* orient);
+
 /* DG order p: 1..3 in 2D, 1..2 in 3D (N = (p+1)^dim <= 32 unknowns per element) and, for 3D, the number K of
  * sub-squares per face axis of the composite face rule (K >= 1; ignored in 2D).
  * Quadrature: volume n_v = p + ceil(dim r / 2) Gauss-Legendre points per axis, faces

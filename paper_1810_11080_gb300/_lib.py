@@ -30,7 +30,7 @@ EXPORTED = ["sn_create", "sn_destroy", "sn_last_error", "sn_set_mesh", "sn_set_d
             "sn_predictor_corr_data", "sn_source_iterate_learned", "sn_predictor_initial_phi",
             "sn_quadrature_level_symmetric", "sn_set_spin_limit", "sn_set_dsa", "sn_dsa_correction",
             "sn_dsa_last_iters", "sn_prepare_inverse", "sn_release_inverse", "sn_num_volume_points",
-            "sn_volume_points", "sn_l2_error"]
+            "sn_volume_points", "sn_l2_error", "sn_set_mesh_simplex"]
 
 
 class sn_graph_stats(ctypes.Structure):
@@ -122,6 +122,7 @@ def load(path=LIB_PATH):
         "sn_num_volume_points": (ctypes.c_int32, [P]),
         "sn_volume_points": (I, [P, P]),
         "sn_l2_error": (I, [P, P, P, ctypes.POINTER(D)]),
+        "sn_set_mesh_simplex": (I, [P, I, I64, I, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -213,6 +214,14 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def sn_set_mesh_simplex(self, dim, n_elem, r, ctrl, face_nbr, nbr_face, orient):
+        self._n_elem = int(n_elem)
+        self._dim = int(dim)
+        return self._check(self._lib.sn_set_mesh_simplex(self._c, dim, n_elem, r, _ptr(ctrl, np.float64, "ctrl"),
+                                                         _ptr(face_nbr, np.int64, "face_nbr"),
+                                                         _ptr(nbr_face, np.int32, "nbr_face"),
+                                                         _ptr(orient, np.int32, "orient")))
 
     def sn_set_mesh(self, dim, n_elem, r, ctrl, face_nbr, nbr_face, orient):
         self._n_elem = int(n_elem)

@@ -128,6 +128,8 @@ sn::DevProblem sn_ctx::dev() const {
   P.K = (dim == 3) ? K : 1;
   P.Q = tab.Q;
   P.Nv = tab.Nv;
+  P.nfc = nfc;
+  P.simplex = simplex ? 1 : 0;
   P.M = M;
   P.E = E;
   P.n_bdr = n_bdr;
@@ -228,17 +230,21 @@ int64_t sn_kernel_launches(const sn_ctx* c) { return c ? c->launches : 0; }
 
 int64_t sn_num_boundary_faces(const sn_ctx* c) { return c ? c->n_bdr : 0; }
 
-sn_status sn_set_mesh(sn_ctx* c, int dim, int64_t n_elem, int r, const double* ctrl, const int64_t* face_nbr,
-                      const int32_t* nbr_face, const int32_t* orient) {
+namespace {
+sn_status set_mesh_impl(sn_ctx* c, int dim, int64_t n_elem, int r, const double* ctrl, const int64_t* face_nbr,
+                        const int32_t* nbr_face, const int32_t* orient, bool simplex) {
   if (!c) return SN_EINVAL;
   SN_REQ(c, dim == 2 || dim == 3, SN_EINVAL, "dim must be 2 or 3");
+  SN_REQ(c, !simplex || dim == 2, SN_EINVAL, "simplicial meshes: triangles (dim 2) only");
   SN_REQ(c, r >= 1 && r <= MAX_R, SN_EINVAL, "geometry order r must be 1..3");
   SN_REQ(c, n_elem >= 1 && n_elem < (1LL << 31) / 8, SN_EINVAL, "n_elem out of range");
   SN_REQ(c, ctrl && face_nbr && nbr_face && orient, SN_EINVAL, "null mesh array");
   cudaSetDevice(c->device);
-  const int nfc = 2 * dim;
+  const int nfc = simplex ? 3 : 2 * dim;
   int64_t nv = 1;
-  for (int k = 0; k < dim; ++k) nv *= (r + 1);
+  if (simplex) nv = (int64_t)(r + 1) * (r + 2) / 2;
+  else
+    for (int k = 0; k < dim; ++k) nv *= (r + 1);
   std::vector<double> hc(n_elem * nv * dim);
   std::vector<int64_t> hn(n_elem * nfc);
   std::vector<int32_t> hf(n_elem * nfc), ho(n_elem * nfc);
@@ -267,6 +273,8 @@ sn_status sn_set_mesh(sn_ctx* c, int dim, int64_t n_elem, int r, const double* c
   free_graph_state(c);
   c->dim = dim;
   c->r = r;
+  c->simplex = simplex;
+  c->nfc = nfc;
   c->E = n_elem;
   c->h_ctrl.swap(hc);
   c->h_nbr.swap(hn);
@@ -309,6 +317,17 @@ sn_status sn_set_mesh(sn_ctx* c, int dim, int64_t n_elem, int r, const double* c
   c->mat_set = false;
   return SN_OK;
 }
+}  // namespace
+
+sn_status sn_set_mesh(sn_ctx* c, int dim, int64_t n_elem, int r, const double* ctrl, const int64_t* face_nbr,
+                      const int32_t* nbr_face, const int32_t* orient) {
+  return set_mesh_impl(c, dim, n_elem, r, ctrl, face_nbr, nbr_face, orient, false);
+}
+
+sn_status sn_set_mesh_simplex(sn_ctx* c, int dim, int64_t n_elem, int r, const double* ctrl,
+                              const int64_t* face_nbr, const int32_t* nbr_face, const int32_t* orient) {
+  return set_mesh_impl(c, dim, n_elem, r, ctrl, face_nbr, nbr_face, orient, true);
+}
 
 sn_status sn_set_discretization(sn_ctx* c, int p, int face_subdiv) {
   if (!c) return SN_EINVAL;
@@ -325,14 +344,15 @@ sn_status sn_set_discretization(sn_ctx* c, int p, int face_subdiv) {
   c->p = p;
   c->K = face_subdiv;
   try {
-    build_tables(c->tab, c->dim, p, c->r);
+    if (c->simplex) build_tables_tri(c->tab, p, c->r);
+    else build_tables(c->tab, c->dim, p, c->r);
   } catch (const std::exception& ex) {
     set_err(c, ex.what());
     return SN_EINVAL;
   }
   c->N = c->tab.N;
   c->Nf = c->tab.Nf;
-  c->blk = elem_block_doubles(c->dim, c->N, c->Nf);
+  c->blk = elem_block_doubles(c->dim, c->N, c->Nf, c->nfc);
   std::vector<double> packed;
   auto add = [&](int slot, const std::vector<double>& v) {
     c->tab_off[slot] = (int)packed.size();
@@ -477,7 +497,7 @@ sn_status sn_build_graph(sn_ctx* c, int weighting, int exact_max, sn_graph_stats
   cudaEvent_t ev[5];
   for (auto& x : ev) SN_CUDA(c, cudaEventCreate(&x));
   const int64_t E = c->E, M = c->M;
-  const int nfc = 2 * c->dim;
+  const int nfc = c->nfc;
   // geometric factors
   SN_CUDA(c, dalloc(c->d_elem, (size_t)E * c->blk));
   SN_CUDA(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
@@ -753,7 +773,7 @@ sn_status form_inverse(sn_ctx* c, int prec, float* ms) {
     int64_t tot = 0;
     for (size_t q = 0; q < npair; ++q) {
       fidx[q] = (int32_t)tot;
-      for (int f = 0; f < 2 * c->dim; ++f) tot += face_mode(code[q], f) != MODE_NONE;
+      for (int f = 0; f < c->nfc; ++f) tot += face_mode(code[q], f) != MODE_NONE;
       if (tot > INT32_MAX) {
         set_err(c, "stored inverses: more than 2^31 inflow face blocks");
         return SN_EINVAL;
@@ -811,6 +831,8 @@ sn_status run_levels(sn_ctx* c, int prec, const double* psi_old, double* psi_new
   int* err = reinterpret_cast<int*>(c->d_red + 2);
   unsigned long long* head = c->d_red + 3;
   const bool stored = prec == SN_PREC_FP64_INV || prec == SN_PREC_DS_INV;
+  SN_REQ(c, stored || !c->simplex, SN_EINVAL,
+         "triangle meshes: use a stored-inverse form (SN_PREC_FP64_INV or SN_PREC_DS_INV)");
   if (stored && c->inv_form != prec) {     // outside any capture: it synchronises
     sn_status st = form_inverse(c, prec, nullptr);
     if (st != SN_OK) return st;
@@ -1052,6 +1074,7 @@ namespace {
 sn_status dsa_prepare(sn_ctx* c) {
   sn::DsaState& D = c->dsa;
   if (D.ready) return SN_OK;
+  SN_REQ(c, !c->simplex, SN_EINVAL, "diffusion synthetic acceleration: quadrilateral and hexahedral meshes only");
   const size_t N = c->N, E = c->E, nfc = 2 * c->dim;
   SN_CUDA(c, dalloc(D.diag, E * N * N));
   SN_CUDA(c, dalloc(D.inv, E * N * N));

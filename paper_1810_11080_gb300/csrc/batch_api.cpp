@@ -111,6 +111,7 @@ sn_status sn_batch_create(sn_batch** out, int n_problems, sn_ctx* const* problem
   for (int k = 0; k < n_problems; ++k) {
     sn_ctx* c = problems[k];
     if (!c || !c->graph_ready) return fail(SN_ESTATE);
+    if (c->simplex) return fail(SN_EINVAL);         // batches: quadrilateral and hexahedral problems
     if (k == 0) {
       b->device = c->device;
       b->dim = c->dim;

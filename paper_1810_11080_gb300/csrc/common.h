@@ -41,6 +41,7 @@ void gll_nodes(int p, std::vector<double>& x);
 double lagrange(const double* nodes, int n, int j, double x);
 double lagrange_deriv(const double* nodes, int n, int j, double x);
 void build_tables(Tables& T, int dim, int p, int r);
+void build_tables_tri(Tables& T, int p, int r);
 
 // Components and feedback arc sets of every direction's graph on the device (scc.cu).
 struct DeviceFasStats {
@@ -71,6 +72,8 @@ cudaError_t dsa_apply(const DevProblem& P, DsaState& D, const double* half, cons
 // Device-side view of a problem passed to kernels by value.
 struct DevProblem {
   int dim, r, p, N, Nf, nv, nf, K, Q, Nv, M;
+  int nfc;                   // faces per element: 2 dim (quadrilaterals, hexahedra) or 3 (triangles)
+  int simplex;               // 1: triangles with P_r geometry and P_p DG (see tables.cpp)
   int64_t E;
   int64_t n_bdr;
   const double* ctrl;        // [E][Nv][dim]
@@ -145,8 +148,8 @@ cudaError_t launch_batch_moment(const DevProblem* probs, const MomentArgs* margs
 // Element factor block layout: S^0..S^{dim-1} (N x N, S^k[m][n] = int du_m/dx_k u_n),
 // mass M (N x N), then face matrices FN[f][k][i][j] = int_face w N_k phi_i phi_j with the
 // element's own outward scaled normal (2 dim faces x dim components x Nf x Nf).
-inline int64_t elem_block_doubles(int dim, int N, int Nf) {
-  return (int64_t)(dim + 1) * N * N + (int64_t)2 * dim * dim * Nf * Nf;
+inline int64_t elem_block_doubles(int dim, int N, int Nf, int nfc) {
+  return (int64_t)(dim + 1) * N * N + (int64_t)nfc * dim * Nf * Nf;
 }
 
 // Launchers (return cudaError_t of the launch).
@@ -191,6 +194,8 @@ struct sn_ctx {
   int64_t launches = 0;
   // mesh (host copies)
   int dim = 0, r = 0;
+  bool simplex = false;            // triangles (sn_set_mesh_simplex)
+  int nfc = 0;                     // faces per element
   int64_t E = 0;
   std::vector<double> h_ctrl;
   std::vector<int64_t> h_nbr;

@@ -78,6 +78,28 @@ __host__ __device__ constexpr int face_vol_index(int dim, int p, int f, int i, i
   return t0 + n * (t1 + n * t2);
 }
 
+// Triangles: local node index of node j (0..k, increasing face coordinate) of face f of an
+// order-k node set numbered v0, v1, v2, the k - 1 interior nodes of f0, f1, f2, then the interior
+// node; faces f0 = v0 v1, f1 = v1 v2, f2 = v2 v0.
+__host__ __device__ constexpr int tri_edge_node(int k, int f, int j) {
+  return j == 0 ? f : (j == k ? (f + 1) % 3 : 3 + f * (k - 1) + (j - 1));
+}
+
+// Triangle face f: outward scaled normal (T_y, -T_x), T(s) = sum_j x_j l_j'(s) over the face's
+// r + 1 control points in increasing j from 0.0 (1D Lagrange on the equispaced nodes geo).
+__device__ inline void face_normal_tri(int r, const double* geo, const double* ctrl, int f, double s,
+                                       double* nvec) {
+  double T0 = 0.0, T1 = 0.0;
+  for (int j = 0; j <= r; ++j) {
+    const int m = tri_edge_node(r, f, j);
+    const double dv = dlagrange_deriv(geo, r + 1, j, s);
+    T0 = T0 + ctrl[m * 2 + 0] * dv;
+    T1 = T1 + ctrl[m * 2 + 1] * dv;
+  }
+  nvec[0] = T1;
+  nvec[1] = -T0;
+}
+
 // Outward face normal scaled by the face Jacobian (cof(J) n_hat) at face coordinates of
 // local face f, from the element's control points ctrl [Nv][dim].  Tangents
 // T_b = sum over the face's control points (increasing index) of x_m * dv_m/dxi_b, where
@@ -169,6 +191,23 @@ __device__ inline void face_basis_all(int dim, const double* gll, int np1, doubl
   }
   for (int a = 0; a < np1; ++a) l1[a] = dlagrange(gll, np1, a, t1);
   for (int fn = 0; fn < np1 * np1; ++fn) out[fn] = l0[fn % np1] * l1[fn / np1];
+}
+
+}  // namespace sn
+
+namespace sn {
+
+// Scaled outward normal of face f of either element family at face coordinates (s0, s1).
+__device__ inline void face_normal_el(const DevProblem& P, const double* geo, const double* ctrl, int f, double s0,
+                                      double s1, double* nvec) {
+  if (P.simplex) face_normal_tri(P.r, geo, ctrl, f, s0, nvec);
+  else face_normal(P.dim, P.r, geo, ctrl, f, s0, s1, nvec);
+}
+
+// Volume node index of face node i of face f (face nodes in face-coordinate order).
+__device__ inline int face_node_vol(const DevProblem& P, int f, int i) {
+  if (P.simplex) return tri_edge_node(P.p, f, i);
+  return face_vol_index(P.dim, P.p, f, i % (P.p + 1), i / (P.p + 1));
 }
 
 }  // namespace sn

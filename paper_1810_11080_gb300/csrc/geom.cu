@@ -83,20 +83,20 @@ __global__ void geometry_kernel(DevProblem P, double* __restrict__ elem, int* ba
   const double* gw = tabp(P, P.off_glf_w);
   const double* geo = tabp(P, P.off_geo);
   const double* gll = tabp(P, P.off_gll);
-  double* wn = gradw;                          // reuse: [2DIM][Pf][DIM]
-  for (int t = threadIdx.x; t < 2 * DIM * Pf; t += blockDim.x) {
+  double* wn = gradw;                          // reuse: [nfc][Pf][DIM]
+  for (int t = threadIdx.x; t < P.nfc * Pf; t += blockDim.x) {
     const int f = t / Pf, q = t % Pf;
     const int qi = q % nf, qj = q / nf;
     const double s0 = gt[qi], s1 = (DIM == 3) ? gt[qj] : 0.0;
     const double w = (DIM == 3) ? gw[qi] * gw[qj] : gw[qi];
     double nv[3];
-    face_normal(DIM, r, geo, sctrl, f, s0, s1, nv);
+    face_normal_el(P, geo, sctrl, f, s0, s1, nv);
     for (int k = 0; k < DIM; ++k) wn[(f * Pf + q) * DIM + k] = w * nv[k];
   }
   __syncthreads();
   const int np1 = p + 1;
   double* fnout = out + (size_t)(DIM + 1) * N * N;
-  for (int t = threadIdx.x; t < 2 * DIM * Nf * Nf; t += blockDim.x) {
+  for (int t = threadIdx.x; t < P.nfc * Nf * Nf; t += blockDim.x) {
     const int f = t / (Nf * Nf), ij = t % (Nf * Nf), i = ij / Nf, j = ij % Nf;
     double acc[DIM];
     for (int k = 0; k < DIM; ++k) acc[k] = 0.0;
@@ -114,7 +114,7 @@ cudaError_t launch_geometry(const DevProblem& P, double* elem, int* bad, cudaStr
   const int nf = P.nf;
   const int Pf = (P.dim == 2) ? nf : nf * nf;
   size_t shmem = sizeof(double) * ((size_t)P.Nv * P.dim + P.Q + (size_t)P.Q * P.dim * P.dim +
-                                   std::max((size_t)P.Q * P.N * P.dim, (size_t)2 * P.dim * Pf * P.dim));
+                                   std::max((size_t)P.Q * P.N * P.dim, (size_t)P.nfc * Pf * P.dim));
   if (P.dim == 2) {
     auto k = geometry_kernel<2>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);

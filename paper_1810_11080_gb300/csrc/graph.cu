@@ -21,9 +21,9 @@ struct PointData {
 __device__ void split_2d(const DevProblem& P, const double* ctrl, int f, const double* om, double* brk) {
   const double* geo = tabp(P, P.off_geo);
   double n0[3], nh[3], n1[3];
-  face_normal(2, P.r, geo, ctrl, f, 0.0, 0.0, n0);
-  face_normal(2, P.r, geo, ctrl, f, 0.5, 0.0, nh);
-  face_normal(2, P.r, geo, ctrl, f, 1.0, 0.0, n1);
+  face_normal_el(P, geo, ctrl, f, 0.0, 0.0, n0);
+  face_normal_el(P, geo, ctrl, f, 0.5, 0.0, nh);
+  face_normal_el(P, geo, ctrl, f, 1.0, 0.0, n1);
   const double g0 = dot_omega(2, om, n0), gh = dot_omega(2, om, nh), g1 = dot_omega(2, om, n1);
   const double c0 = g0;
   const double c2 = 2.0 * ((g0 - 2.0 * gh) + g1);
@@ -396,7 +396,7 @@ __device__ void fill_points_brk(const DevProblem& P, const double* ctrl, int f, 
   for (int q = lane; q < np; q += 32) {
     PointData pd = face_point(P, brk, q);
     double nv[3];
-    face_normal(P.dim, P.r, geo, ctrl, f, pd.s0, pd.s1, nv);
+    face_normal_el(P, geo, ctrl, f, pd.s0, pd.s1, nv);
     const double g = dot_omega(P.dim, om, nv);
     const double mg = -g;
     double* o = sp + q * stride;
@@ -434,7 +434,7 @@ __device__ void fill_cache(const DevProblem& P, const double* ctrl, int f, int c
   for (int q = lane; q < np; q += 32) {
     PointData pd = face_point(P, brk, q);
     double nv[3];
-    face_normal(dim, P.r, geo, ctrl, f, pd.s0, pd.s1, nv);
+    face_normal_el(P, geo, ctrl, f, pd.s0, pd.s1, nv);
     double* w = wn + q * (1 + dim);
     w[0] = pd.w;
     for (int c = 0; c < dim; ++c) w[1 + c] = nv[c];
@@ -495,7 +495,7 @@ __device__ double siginv_weight(const DevProblem& P, const double* fbar, int64_t
     double b[27];
     for (int i = 0; i < N; ++i) b[i] = 0.0;
     for (int i = 0; i < Nf; ++i) {
-      const int vi = face_vol_index(P.dim, P.p, recv_face, i % (P.p + 1), i / (P.p + 1));
+      const int vi = face_node_vol(P, recv_face, i);
       b[vi] = fbar[i * Nf + lane];
     }
     for (int i = 0; i < N; ++i) y[i] = b[pm[i]];
@@ -617,7 +617,7 @@ __device__ void emit_weights(const DevProblem& P, int64_t fi, int d, int64_t own
     wv = en ? siginv_weight(P, fb + Nf * Nf, nbr, fn, mt_lu, mt_perm, lane) : 0.0;
   }
   if (lane == 0) {
-    const int nfc = 2 * P.dim;
+    const int nfc = P.nfc;
     win[((int64_t)d * P.E + owner) * nfc + f] = wo;         // arc nbr -> owner, owner's face f
     win[((int64_t)d * P.E + nbr) * nfc + fn] = wv;          // arc owner -> nbr, nbr's face fn
     if (eo) atomicOr(&facecode[(int64_t)d * P.E + owner], (en ? MODE_MIXED : MODE_PURE) << (2 * f));
@@ -665,7 +665,7 @@ __global__ void weights_face_kernel(DevProblem P, const int32_t* __restrict__ if
   const double* geo = tabp(P, P.off_geo);
   if (dim == 2 && lane < 3) {
     double nv[3];
-    face_normal(2, P.r, geo, ctrl, f, lane == 0 ? 0.0 : (lane == 1 ? 0.5 : 1.0), 0.0, nv);
+    face_normal_el(P, geo, ctrl, f, lane == 0 ? 0.0 : (lane == 1 ? 0.5 : 1.0), 0.0, nv);
     nref[2 * lane] = nv[0];
     nref[2 * lane + 1] = nv[1];
   }
@@ -1034,7 +1034,7 @@ cudaError_t launch_levels_init(const DevProblem& P, int32_t* levels, cudaStream_
 __global__ void levels_relax_kernel(DevProblem P, const uint32_t* __restrict__ facecode, int32_t* levels,
                                     int* changed) {
   const int64_t n = (int64_t)P.M * P.E;
-  const int nfc = 2 * P.dim;
+  const int nfc = P.nfc;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = i / P.E, e = i % P.E;
     const uint32_t code = facecode[i];

@@ -8,18 +8,107 @@
 // inflow face, row-major, at fblk + (fidx[q] + r) Nf^2 (r counts the inflow faces in face order).
 // SN_PREC_FP64_INV keeps doubles and applies them in FP64; SN_PREC_DS_INV keeps (hi, lo) FP32
 // pairs of the same FP64 values and applies them in double-single arithmetic on the FP32 pipe.
+// The code is written for an element policy El (node counts, face count, face-node maps), so the
+// same bodies serve quadrilaterals / hexahedra (TensorEl) and triangles (TriEl).
 #pragma once
 
 namespace sn {
 
+// ---- element policies
+// N, NF: unknowns per element and per face; W: lanes per system (power of two >= N), SPW systems
+// per warp; NFC: faces; face_node(f, i): face-node index of volume node i on face f, or -1;
+// vol_node(f, fj): volume index of face node fj; trace_node(fn, oc, fj): volume index, in the
+// neighbour's numbering, of our face node fj seen through the neighbour's face fn with
+// orientation code oc; SLOTS / slot(f): registers for inflow block rows kept across the wait (a
+// node lies on at most one face of each slot).
+template <int DIM, int P_>
+struct TensorEl {
+  using S = Shape<DIM, P_>;
+  static constexpr int DIMV = DIM, N = S::N, NF = S::NF, W = S::W, SPW = S::SPW, NFC = 2 * DIM, NP1 = P_ + 1;
+  static constexpr int SLOTS = DIM;
+  __host__ __device__ static constexpr int slot(int f) { return f >> 1; }
+  __device__ static int face_node(int f, int i) { return on_face<DIM, P_>(f, i); }
+  __host__ __device__ static constexpr int vol_node(int f, int fj) { return fvi<DIM, P_>(f, fj); }
+  __device__ static int trace_node(int fn, int oc, int fj) {
+    int c0, ci, cj;
+    trace_affine<DIM, P_>(fn, oc, c0, ci, cj);
+    return c0 + ci * (fj % NP1) + cj * (fj / NP1);
+  }
+};
+
+// Triangles: faces f0 = v0 v1, f1 = v1 v2, f2 = v2 v0, face nodes in increasing face coordinate
+// (tri_edge_node); a neighbour running the shared face the other way (oc = 1) sees face node fj
+// as its node P_ - fj.
+template <int P_>
+struct TriEl {
+  static constexpr int DIMV = 2, N = (P_ + 1) * (P_ + 2) / 2, NF = P_ + 1, NP1 = P_ + 1;
+  static constexpr int W = N <= 4 ? 4 : (N <= 8 ? 8 : (N <= 16 ? 16 : 32)), SPW = 32 / W, NFC = 3;
+  static constexpr int SLOTS = 3;
+  __host__ __device__ static constexpr int slot(int f) { return f; }
+  __device__ static int face_node(int f, int i) {
+    int out = -1;
+#pragma unroll
+    for (int j = 0; j <= P_; ++j)
+      if (tri_edge_node(P_, f, j) == i) out = j;
+    return out;
+  }
+  __host__ __device__ static constexpr int vol_node(int f, int fj) { return tri_edge_node(P_, f, fj); }
+  __device__ static int trace_node(int fn, int oc, int fj) { return tri_edge_node(P_, fn, (oc & 1) ? P_ - fj : fj); }
+};
+
+// FP64 inflow block row fi of face f: -Omega . FN_f (whole-inflow face) or the stored block of a
+// partially-inflow face (slot).
+template <class El>
+__device__ __forceinline__ void brow_el(const double* blk, const SweepArgs& sa, uint32_t mode, int f, int fi,
+                                        int slot, double om0, double om1, double om2, double* Brow) {
+  constexpr int N = El::N, NF = El::NF, DIM = El::DIMV;
+  if (mode == MODE_PURE) {
+    const double* fnm = blk + (DIM + 1) * N * N + f * DIM * NF * NF + fi * NF;
+#pragma unroll
+    for (int fj = 0; fj < NF; ++fj) {
+      double v = om0 * __ldg(fnm + fj);
+      v = fma(om1, __ldg(fnm + NF * NF + fj), v);
+      if (DIM == 3) v = fma(om2, __ldg(fnm + 2 * NF * NF + fj), v);
+      Brow[fj] = -v;
+    }
+  } else {
+    const double* mb = sa.mixedB + (int64_t)slot * NF * NF + fi * NF;
+#pragma unroll
+    for (int fj = 0; fj < NF; ++fj) Brow[fj] = __ldg(mb + fj);
+  }
+}
+
+// b += B_f trace_f (FP64) for one inflow face row: the upwind neighbour's trace (new iterate, or
+// the previous one through a lagged arc) or the incident flux on the domain boundary.
+template <class El, bool DF>
+__device__ __forceinline__ void face_rhs_el(const DevProblem& Pb, const SweepArgs& sa, uint32_t code, int f,
+                                            int64_t e, int d, const double* Brow, double& b) {
+  constexpr int N = El::N, NF = El::NF, NFC = El::NFC;
+  const int64_t nb = Pb.nbr[e * NFC + f];
+  if (nb >= 0) {
+    const bool lag = face_lagged(code, f);
+    const double* ps = lag ? sa.psi_old : sa.psi_new;
+    const int fn = Pb.nbr_face[e * NFC + f], oc = Pb.orient[e * NFC + f];
+    const double* pnb = ps + ((int64_t)d * Pb.E + nb) * N;
+#pragma unroll
+    for (int fj = 0; fj < NF; ++fj) {
+      const double* pt = pnb + El::trace_node(fn, oc, fj);
+      b = fma(Brow[fj], lag ? __ldg(pt) : trace_load<DF>(pt), b);
+    }
+  } else if (Pb.psi_inc != nullptr) {
+    const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * NFC + f]) * NF;
+#pragma unroll
+    for (int fj = 0; fj < NF; ++fj) b = fma(Brow[fj], __ldg(pin + fj), b);
+  }
+}
+
 // Inverse and inflow blocks of one pair, formed in FP64 by Gauss-Jordan elimination with partial
 // pivoting (row-per-lane; see gj32 for the bookkeeping of V in pivot-step order).  A is assembled
 // as in body64.  DSOUT: store (hi, lo) FP32 pairs instead of doubles.
-template <int DIM, int P_, bool DSOUT>
+template <class El, bool DSOUT>
 __device__ __forceinline__ void invert_pair(const DevProblem& Pb, const SweepArgs& sa, int64_t q, bool valid,
                                             int lane) {
-  using S = Shape<DIM, P_>;
-  constexpr int N = S::N, NF = S::NF, W = S::W;
+  constexpr int N = El::N, NF = El::NF, W = El::W, DIM = El::DIMV;
   constexpr unsigned FULL = 0xffffffffu;
   const int i = lane % W;
   const int64_t E = Pb.E;
@@ -54,17 +143,17 @@ __device__ __forceinline__ void invert_pair(const DevProblem& Pb, const SweepArg
   const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[q] : 0;
   const int64_t bidx = valid ? sa.fidx[q] : 0;
   int mrank = 0, rank = 0;
-  static_for<0, 2 * DIM>([&](auto fconst) {
+  static_for<0, El::NFC>([&](auto fconst) {
     constexpr int f = decltype(fconst)::value;
     const uint32_t mode = face_mode(code, f);
-    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+    const int fi = row ? El::face_node(f, i) : -1;
     if (mode != MODE_NONE && fi >= 0) {
       double Brow[NF];
-      brow64<DIM, P_>(blk, sa, mode, f, fi, mbase + mrank, om0, om1, om2, Brow);
+      brow_el<El>(blk, sa, mode, f, fi, mbase + mrank, om0, om1, om2, Brow);
       const int64_t o = (bidx + rank) * (NF * NF) + fi * NF;
       static_for<0, NF>([&](auto jconst) {
         constexpr int fj = decltype(jconst)::value;
-        a[fvi<DIM, P_>(f, fj)] += Brow[fj];
+        a[El::vol_node(f, fj)] += Brow[fj];
         put(o + fj, Brow[fj], sa.fblk);
       });
     }
@@ -112,10 +201,9 @@ __device__ __forceinline__ void invert_pair(const DevProblem& Pb, const SweepArg
 }
 
 // ------------------------------------------------------------------ FP64 application
-template <int DIM, int P_, bool DF>
+template <class El, bool DF>
 __device__ __forceinline__ void bodyinv(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid, int lane) {
-  using S = Shape<DIM, P_>;
-  constexpr int N = S::N, NF = S::NF, W = S::W;
+  constexpr int N = El::N, NF = El::NF, W = El::W, DIM = El::DIMV;
   constexpr unsigned FULL = 0xffffffffu;
   constexpr bool BPRE = DIM == 2;      // inflow block rows held in registers across the wait (2D)
   const int i = lane % W;
@@ -144,40 +232,41 @@ __device__ __forceinline__ void bodyinv(const DevProblem& Pb, const SweepArgs& s
   }
   const uint32_t code = valid ? sa.facecode[q] : 0u;
   const int64_t bidx = valid ? sa.fidx[q] : 0;
-  // 2D: a node lies on at most one face per axis; that face's block row goes to slot axis.
-  double Bax[BPRE ? DIM : 1][NF];
+  double Bax[BPRE ? El::SLOTS : 1][NF];
   if constexpr (BPRE) {
     int rank = 0;
-    static_for<0, 2 * DIM>([&](auto fconst) {
+    static_for<0, El::NFC>([&](auto fconst) {
       constexpr int f = decltype(fconst)::value;
       const uint32_t mode = face_mode(code, f);
-      const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+      const int fi = row ? El::face_node(f, i) : -1;
       if (mode != MODE_NONE && fi >= 0) {
         const double* br = sa.fblk + (bidx + rank) * (NF * NF) + fi * NF;
-        static_for<0, NF>([&](auto jconst) { Bax[f >> 1][decltype(jconst)::value] = __ldcs(br + decltype(jconst)::value); });
+        static_for<0, NF>([&](auto jconst) {
+          Bax[El::slot(f)][decltype(jconst)::value] = __ldcs(br + decltype(jconst)::value);
+        });
       }
       if (mode != MODE_NONE) ++rank;
     });
   }
-  if constexpr (DF) wait_upwind<DIM>(Pb, sa, code, e, d, valid);
+  if constexpr (DF) wait_upwind_n<El::NFC>(Pb, sa, code, e, d, valid);
   else {
     pdl_wait();                          // sources and upwind traces come from earlier launches
     pdl_launch_dependents();
   }
   if (row) b += sa.src[e * N + i];
   int rank = 0;
-  static_for<0, 2 * DIM>([&](auto fconst) {
+  static_for<0, El::NFC>([&](auto fconst) {
     constexpr int f = decltype(fconst)::value;
     const uint32_t mode = face_mode(code, f);
-    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+    const int fi = row ? El::face_node(f, i) : -1;
     if (mode != MODE_NONE && fi >= 0) {
       if constexpr (BPRE) {
-        face_rhs<DIM, P_, DF>(Pb, sa, code, f, e, d, Bax[f >> 1], b);
+        face_rhs_el<El, DF>(Pb, sa, code, f, e, d, Bax[El::slot(f)], b);
       } else {
         double Brow[NF];
         const double* br = sa.fblk + (bidx + rank) * (NF * NF) + fi * NF;
         static_for<0, NF>([&](auto jconst) { Brow[decltype(jconst)::value] = __ldcs(br + decltype(jconst)::value); });
-        face_rhs<DIM, P_, DF>(Pb, sa, code, f, e, d, Brow, b);
+        face_rhs_el<El, DF>(Pb, sa, code, f, e, d, Brow, b);
       }
     }
     if (mode != MODE_NONE) ++rank;
@@ -208,11 +297,10 @@ __device__ __forceinline__ void bodyinv(const DevProblem& Pb, const SweepArgs& s
 // (error-free FP32 products and sums, ~2^-48 relative), from the (hi, lo) splits of the stored
 // FP64 inverse and blocks, of the source and of the upwind traces; no FP64 instruction on the
 // solve path except the final psi = hi + lo.
-template <int DIM, int P_, bool DF>
+template <class El, bool DF>
 __device__ __forceinline__ void bodydsinv(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid,
                                           int lane) {
-  using S = Shape<DIM, P_>;
-  constexpr int N = S::N, NF = S::NF, W = S::W, NP1 = S::NP1;
+  constexpr int N = El::N, NF = El::NF, W = El::W, DIM = El::DIMV, NFC = El::NFC;
   constexpr unsigned FULL = 0xffffffffu;
   constexpr bool BPRE = DIM == 2;
   const int i = lane % W;
@@ -245,29 +333,31 @@ __device__ __forceinline__ void bodydsinv(const DevProblem& Pb, const SweepArgs&
   }
   const uint32_t code = valid ? sa.facecode[q] : 0u;
   const int64_t bidx = valid ? sa.fidx[q] : 0;
-  int64_t nbv[2 * DIM];
-  int fov[2 * DIM];
-  static_for<0, 2 * DIM>([&](auto fconst) {
+  int64_t nbv[NFC];
+  int fov[NFC];
+  static_for<0, NFC>([&](auto fconst) {
     constexpr int f = decltype(fconst)::value;
-    nbv[f] = valid ? Pb.nbr[e * 2 * DIM + f] : -1;
-    fov[f] = valid ? (Pb.nbr_face[e * 2 * DIM + f] | (Pb.orient[e * 2 * DIM + f] << 8)) : 0;
+    nbv[f] = valid ? Pb.nbr[e * NFC + f] : -1;
+    fov[f] = valid ? (Pb.nbr_face[e * NFC + f] | (Pb.orient[e * NFC + f] << 8)) : 0;
   });
-  float2 Bax[BPRE ? DIM : 1][NF];
+  float2 Bax[BPRE ? El::SLOTS : 1][NF];
   if constexpr (BPRE) {
     int rank = 0;
-    static_for<0, 2 * DIM>([&](auto fconst) {
+    static_for<0, NFC>([&](auto fconst) {
       constexpr int f = decltype(fconst)::value;
       const uint32_t mode = face_mode(code, f);
-      const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+      const int fi = row ? El::face_node(f, i) : -1;
       if (mode != MODE_NONE && fi >= 0) {
         const float2* br = fb2 + (bidx + rank) * (NF * NF) + fi * NF;
-        static_for<0, NF>([&](auto jconst) { Bax[f >> 1][decltype(jconst)::value] = __ldcs(br + decltype(jconst)::value); });
+        static_for<0, NF>([&](auto jconst) {
+          Bax[El::slot(f)][decltype(jconst)::value] = __ldcs(br + decltype(jconst)::value);
+        });
       }
       if (mode != MODE_NONE) ++rank;
     });
   }
   if constexpr (DF) {
-    wait_upwind<DIM>(Pb, sa, code, e, d, valid);
+    wait_upwind_n<NFC>(Pb, sa, code, e, d, valid);
   } else {
     pdl_wait();                          // sources and upwind traces come from earlier launches
     pdl_launch_dependents();
@@ -275,29 +365,27 @@ __device__ __forceinline__ void bodydsinv(const DevProblem& Pb, const SweepArgs&
   if (row) ds_add(rbh, rbl, sa.src_h[e * N + i], sa.src_l[e * N + i]);
   float sh2 = 0.0f, sl2 = 0.0f;          // second accumulation chain for the face terms
   int rank = 0;
-  static_for<0, 2 * DIM>([&](auto fconst) {
+  static_for<0, NFC>([&](auto fconst) {
     constexpr int f = decltype(fconst)::value;
     const uint32_t mode = face_mode(code, f);
-    const int fi = row ? on_face<DIM, P_>(f, i) : -1;
+    const int fi = row ? El::face_node(f, i) : -1;
     const int64_t nb = nbv[f];
     if (mode != MODE_NONE && fi >= 0 && (nb >= 0 || Pb.psi_inc != nullptr)) {
       float2 B[NF];
       if constexpr (BPRE) {
-        static_for<0, NF>([&](auto jconst) { B[decltype(jconst)::value] = Bax[f >> 1][decltype(jconst)::value]; });
+        static_for<0, NF>([&](auto jconst) { B[decltype(jconst)::value] = Bax[El::slot(f)][decltype(jconst)::value]; });
       } else {
         const float2* br = fb2 + (bidx + rank) * (NF * NF) + fi * NF;
         static_for<0, NF>([&](auto jconst) { B[decltype(jconst)::value] = __ldcs(br + decltype(jconst)::value); });
       }
       if (nb >= 0) {                     // upwind neighbour's (hi, lo) split of the trace
         const bool lag = face_lagged(code, f);
-        int c0, ci, cj;
-        trace_affine<DIM, P_>(fov[f] & 0xff, fov[f] >> 8, c0, ci, cj);
-        const int64_t base = ((int64_t)d * E + nb) * N + c0;
+        const int64_t base = ((int64_t)d * E + nb) * N;
         const float* ph_ = (lag ? sa.psi_old_h : sa.psi_new_h) + base;
         const float* pl_ = (lag ? sa.psi_old_l : sa.psi_new_l) + base;
 #pragma unroll
         for (int fj = 0; fj < NF; ++fj) {
-          const int o = ci * (fj % NP1) + cj * (fj / NP1);
+          const int o = El::trace_node(fov[f] & 0xff, fov[f] >> 8, fj);
           float th, tl, qh, ql;
           if (!lag && DF) {
             th = __ldcg(ph_ + o);
@@ -311,7 +399,7 @@ __device__ __forceinline__ void bodydsinv(const DevProblem& Pb, const SweepArgs&
           else ds_add(rbh, rbl, qh, ql);
         }
       } else {                           // incident flux on the domain boundary
-        const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * 2 * DIM + f]) * NF;
+        const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * NFC + f]) * NF;
 #pragma unroll
         for (int fj = 0; fj < NF; ++fj) {
           float th, tl, qh, ql;

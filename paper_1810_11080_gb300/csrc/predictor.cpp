@@ -315,6 +315,10 @@ sn_status sn_predictor_features(sn_ctx* c, float* feat, double* phi_ref) {
     c->err = "sn_build_graph first";
     return SN_ESTATE;
   }
+  if (c->simplex) {
+    c->err = "flux predictor: quadrilateral and hexahedral meshes only";
+    return SN_EINVAL;
+  }
   cudaSetDevice(c->device);
   float bb[6] = {1e30f, 1e30f, 1e30f, -1e30f, -1e30f, -1e30f};
   for (size_t i = 0; i < c->h_ctrl.size(); ++i) {

@@ -494,7 +494,7 @@ cudaError_t alloc_n(T*& p, size_t n) {
 // within the bound the graph size implies.
 cudaError_t device_fas(const DevProblem& P, uint32_t* fc, const double* win, int exact_max, DeviceFasStats* stats,
                        cudaStream_t s) {
-  FasGraph G{P.M, 2 * P.dim, P.E, P.nbr, P.nbr_face, fc, win};
+  FasGraph G{P.M, P.nfc, P.E, P.nbr, P.nbr_face, fc, win};
   const int64_t n = (int64_t)P.M * P.E;
   const unsigned grid = 1216, block = 256;
   int8_t *alive = nullptr, *mark = nullptr;

@@ -155,14 +155,15 @@ __device__ __forceinline__ double trace_load(const double* p) {
 // Wait until every kept upwind neighbour of (e, d) has published its angular flux.  A wait that
 // exceeds its poll limit (sa.spin_limit, or SPIN_LIMIT when that is <= 0) sets *err and gives up
 // (the result is then wrong and the host reports SN_ETIMEOUT); it never traps.
-template <int DIM>
-__device__ void wait_upwind(const DevProblem& Pb, const SweepArgs& sa, uint32_t code, int64_t e, int d, bool valid) {
+template <int NFC>
+__device__ void wait_upwind_n(const DevProblem& Pb, const SweepArgs& sa, uint32_t code, int64_t e, int d,
+                              bool valid) {
   if (!valid) return;
   const long long limit = sa.spin_limit > 0 ? sa.spin_limit : SPIN_LIMIT;
 #pragma unroll
-  for (int f = 0; f < 2 * DIM; ++f) {
+  for (int f = 0; f < NFC; ++f) {
     if (face_mode(code, f) == MODE_NONE || face_lagged(code, f)) continue;
-    const int64_t nb = Pb.nbr[e * 2 * DIM + f];
+    const int64_t nb = Pb.nbr[e * NFC + f];
     if (nb < 0) continue;
     const int* flag = sa.done + (int64_t)d * Pb.E + nb;
     long long spins = 0;
@@ -175,6 +176,12 @@ __device__ void wait_upwind(const DevProblem& Pb, const SweepArgs& sa, uint32_t 
       __nanosleep(64);
     }
   }
+}
+
+template <int DIM>
+__device__ __forceinline__ void wait_upwind(const DevProblem& Pb, const SweepArgs& sa, uint32_t code, int64_t e,
+                                            int d, bool valid) {
+  wait_upwind_n<2 * DIM>(Pb, sa, code, e, d, valid);
 }
 
 // Publish (e, d): every lane's flux store is made visible device-wide before the flag.
@@ -783,8 +790,8 @@ template <int DIM, int P_, int PREC, bool DF>
 __device__ __forceinline__ void solve_item(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid,
                                            int lane) {
   if constexpr (PREC == SN_PREC_FP64) body64<DIM, P_, DF>(Pb, sa, pr, valid, lane);
-  else if constexpr (PREC == SN_PREC_FP64_INV) bodyinv<DIM, P_, DF>(Pb, sa, pr, valid, lane);
-  else if constexpr (PREC == SN_PREC_DS_INV) bodydsinv<DIM, P_, DF>(Pb, sa, pr, valid, lane);
+  else if constexpr (PREC == SN_PREC_FP64_INV) bodyinv<TensorEl<DIM, P_>, DF>(Pb, sa, pr, valid, lane);
+  else if constexpr (PREC == SN_PREC_DS_INV) bodydsinv<TensorEl<DIM, P_>, DF>(Pb, sa, pr, valid, lane);
   else if constexpr (PREC == SN_PREC_MIXED) bodymx<DIM, P_, DF>(Pb, sa, pr, valid, lane);
   else bodyds<DIM, P_, DF>(Pb, sa, pr, valid, lane);
 }

@@ -2,8 +2,10 @@
 // here is an exact function of the stated operation order, because the device computes the
 // graph (face normals, coupling blocks, edge weights) from these tables and the graph must
 // be reproducible bit for bit.
+#include <algorithm>
 #include <cmath>
 #include <stdexcept>
+#include <utility>
 #include "common.h"
 
 namespace sn {
@@ -129,6 +131,162 @@ void build_tables(Tables& T, int dim, int p, int r) {
       T.V[(size_t)q * T.Nv + m] = tensor_value(T.geo.data(), r + 1, mi, x, dim, -1);
     }
   }
+}
+
+// ------------------------------------------------------------------ triangles
+// Reference triangle {xi, eta >= 0, xi + eta <= 1}; an order-k node set is v0 = (0,0), v1 = (1,0),
+// v2 = (0,1), the k - 1 interior nodes of the faces f0 = v0 v1, f1 = v1 v2, f2 = v2 v0 (at the 1D
+// positions pos[1..k-1] along each face), then (k = 3) the centroid.  Its Lagrange basis (total
+// degree k) is evaluated through the monomials x^a y^b (a + b <= k) and the inverse Vandermonde
+// matrix.  Geometry: P_r on the equispaced positions a/r; DG: P_p on the GLL positions, whose
+// restriction to a face is the 1D Lagrange basis of those positions.
+namespace {
+
+void tri_nodes(int k, const std::vector<double>& pos, std::vector<double>& xy) {
+  const double V[3][2] = {{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}};
+  xy.clear();
+  for (int i = 0; i < 3; ++i) {
+    xy.push_back(V[i][0]);
+    xy.push_back(V[i][1]);
+  }
+  for (int f = 0; f < 3; ++f) {
+    const double* A = V[f];
+    const double* B = V[(f + 1) % 3];
+    for (int j = 1; j < k; ++j) {
+      xy.push_back(A[0] + pos[j] * (B[0] - A[0]));
+      xy.push_back(A[1] + pos[j] * (B[1] - A[1]));
+    }
+  }
+  if (k == 3) {
+    xy.push_back(1.0 / 3.0);
+    xy.push_back(1.0 / 3.0);
+  }
+}
+
+// Monomial exponents (a, b), total degree 0..k, a descending within a degree.
+void tri_monomials(int k, std::vector<int>& ea, std::vector<int>& eb) {
+  ea.clear();
+  eb.clear();
+  for (int d = 0; d <= k; ++d)
+    for (int a = d; a >= 0; --a) {
+      ea.push_back(a);
+      eb.push_back(d - a);
+    }
+}
+
+double ipow_d(double x, int a) {
+  double v = 1.0;
+  for (int i = 0; i < a; ++i) v *= x;
+  return v;
+}
+
+// Inverse of the n x n matrix A (row-major) by Gauss-Jordan elimination with partial pivoting.
+void invert(int n, std::vector<double> A, std::vector<double>& inv) {
+  inv.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int rr = c + 1; rr < n; ++rr)
+      if (std::fabs(A[rr * n + c]) > std::fabs(A[piv * n + c])) piv = rr;
+    if (A[piv * n + c] == 0.0) throw std::runtime_error("singular Vandermonde matrix");
+    for (int j = 0; j < n; ++j) {
+      std::swap(A[c * n + j], A[piv * n + j]);
+      std::swap(inv[c * n + j], inv[piv * n + j]);
+    }
+    const double d = A[c * n + c];
+    for (int j = 0; j < n; ++j) {
+      A[c * n + j] /= d;
+      inv[c * n + j] /= d;
+    }
+    for (int rr = 0; rr < n; ++rr) {
+      if (rr == c) continue;
+      const double m = A[rr * n + c];
+      if (m == 0.0) continue;
+      for (int j = 0; j < n; ++j) {
+        A[rr * n + j] -= m * A[c * n + j];
+        inv[rr * n + j] -= m * inv[c * n + j];
+      }
+    }
+  }
+}
+
+// Coefficients C [n_mono][n_nodes] (column i = basis function of node i) of the Lagrange basis.
+void tri_basis(int k, const std::vector<double>& xy, std::vector<double>& C) {
+  std::vector<int> ea, eb;
+  tri_monomials(k, ea, eb);
+  const int n = (int)ea.size();
+  std::vector<double> V((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int m = 0; m < n; ++m) V[i * n + m] = ipow_d(xy[2 * i], ea[m]) * ipow_d(xy[2 * i + 1], eb[m]);
+  invert(n, V, C);
+}
+
+// value and gradient of basis function i at (x, y)
+void tri_eval(int k, const std::vector<double>& C, int i, double x, double y, double& v, double& gx, double& gy) {
+  std::vector<int> ea, eb;
+  tri_monomials(k, ea, eb);
+  const int n = (int)ea.size();
+  v = gx = gy = 0.0;
+  for (int m = 0; m < n; ++m) {
+    const double c = C[m * n + i];
+    v += c * ipow_d(x, ea[m]) * ipow_d(y, eb[m]);
+    if (ea[m] > 0) gx += c * ea[m] * ipow_d(x, ea[m] - 1) * ipow_d(y, eb[m]);
+    if (eb[m] > 0) gy += c * eb[m] * ipow_d(x, ea[m]) * ipow_d(y, eb[m] - 1);
+  }
+}
+
+}  // namespace
+
+// Tables of a triangle problem: collapsed Gauss volume rule (xi = u, eta = v (1 - u), weight
+// (w_i w_j) (1 - u_i), n_v = p + r points per direction, point q = i + n_v j); face rule n_f =
+// p + r Gauss points per piece as for the tensor elements; DG (P_p) and geometry (P_r) bases at
+// the volume points.
+void build_tables_tri(Tables& T, int p, int r) {
+  if (p < 1 || p > 3 || r < 1 || r > 3) throw std::invalid_argument("triangles: p and r must be 1..3");
+  T.dim = 2;
+  T.p = p;
+  T.r = r;
+  T.nv = p + r;
+  T.nf = p + r;
+  T.N = (p + 1) * (p + 2) / 2;
+  T.Nf = p + 1;
+  T.Nv = (r + 1) * (r + 2) / 2;
+  T.Q = T.nv * T.nv;
+  gauss_legendre(T.nv, T.glv_t, T.glv_w);
+  gauss_legendre(T.nf, T.glf_t, T.glf_w);
+  gll_nodes(p, T.gll);
+  T.geo.resize(r + 1);
+  for (int a = 0; a <= r; ++a) T.geo[a] = (double)a / r;
+  std::vector<double> dgxy, gxy, Cd, Cg;
+  tri_nodes(p, T.gll, dgxy);
+  tri_nodes(r, T.geo, gxy);
+  tri_basis(p, dgxy, Cd);
+  tri_basis(r, gxy, Cg);
+  T.wq.assign(T.Q, 0.0);
+  T.B.assign((size_t)T.Q * T.N, 0.0);
+  T.dB.assign((size_t)T.Q * T.N * 2, 0.0);
+  T.dV.assign((size_t)T.Q * T.Nv * 2, 0.0);
+  T.V.assign((size_t)T.Q * T.Nv, 0.0);
+  for (int j = 0; j < T.nv; ++j)
+    for (int i = 0; i < T.nv; ++i) {
+      const int q = i + T.nv * j;
+      const double u = T.glv_t[i], x = u, y = T.glv_t[j] * (1.0 - u);
+      T.wq[q] = (T.glv_w[i] * T.glv_w[j]) * (1.0 - u);
+      for (int m = 0; m < T.N; ++m) {
+        double v, gx, gy;
+        tri_eval(p, Cd, m, x, y, v, gx, gy);
+        T.B[(size_t)q * T.N + m] = v;
+        T.dB[((size_t)q * T.N + m) * 2 + 0] = gx;
+        T.dB[((size_t)q * T.N + m) * 2 + 1] = gy;
+      }
+      for (int m = 0; m < T.Nv; ++m) {
+        double v, gx, gy;
+        tri_eval(r, Cg, m, x, y, v, gx, gy);
+        T.V[(size_t)q * T.Nv + m] = v;
+        T.dV[((size_t)q * T.Nv + m) * 2 + 0] = gx;
+        T.dV[((size_t)q * T.Nv + m) * 2 + 1] = gy;
+      }
+    }
 }
 
 }  // namespace sn

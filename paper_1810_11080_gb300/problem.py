@@ -8,11 +8,13 @@ def setup_problem(prob, device=0, stream=None, face_subdiv=2, ctx=None):
     """Create (or reuse) a Context and pass it the arrays of an sn_inputs Problem."""
     ctx = ctx or Context(device, stream)
     m = prob.mesh
-    ctx.sn_set_mesh(m.dim, m.n_elem, m.r, np.ascontiguousarray(m.ctrl, dtype=np.float64),
-                    np.ascontiguousarray(m.face_nbr, dtype=np.int64), np.ascontiguousarray(m.nbr_face, dtype=np.int32),
-                    np.ascontiguousarray(m.orient, dtype=np.int32))
+    simplex = getattr(m, "simplex", False)
+    setm = ctx.sn_set_mesh_simplex if simplex else ctx.sn_set_mesh
+    setm(m.dim, m.n_elem, m.r, np.ascontiguousarray(m.ctrl, dtype=np.float64),
+         np.ascontiguousarray(m.face_nbr, dtype=np.int64), np.ascontiguousarray(m.nbr_face, dtype=np.int32),
+         np.ascontiguousarray(m.orient, dtype=np.int32))
     ctx.sn_set_discretization(prob.p, face_subdiv)
-    ctx._N = (prob.p + 1) ** m.dim
+    ctx._N = (prob.p + 1) * (prob.p + 2) // 2 if simplex else (prob.p + 1) ** m.dim
     ctx.sn_set_quadrature(np.ascontiguousarray(prob.omega, dtype=np.float64),
                           np.ascontiguousarray(prob.w, dtype=np.float64))
     arr = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)

@@ -7,8 +7,15 @@ from oracle.graph import build_graph
 from oracle.sweep import Sweeper
 
 
+def oracle_disc(prob):
+    if getattr(prob.mesh, "simplex", False):
+        from oracle.simplex import SimplexDiscretization
+        return SimplexDiscretization(prob)
+    return Discretization(prob)
+
+
 def oracle_graph(prob, weighting="face", exact_max=10):
-    disc = Discretization(prob)
+    disc = oracle_disc(prob)
     return disc, build_graph(disc, weighting, exact_max)
 
 
