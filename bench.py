@@ -438,6 +438,8 @@ def run_gpu(args):
         out["dsa_thick"] = run_dsa_thick(g, torch, args)
     if not args.no_straightening:
         out["straightening"] = run_straightening(g, torch, args)
+    if not args.no_triangles:
+        out["triangles"] = run_triangles(g, torch, args)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     return out
@@ -628,6 +630,53 @@ def run_straightening(g, torch, args):
     out["error_ratio_straightened_vs_ho_coarse"] = out["straightened_coarse"]["l2_error"] / out["ho_coarse"]["l2_error"]
     out["error_ratio_straightened_vs_ho_refined"] = (out["straightened_refined"]["l2_error"] /
                                                      out["ho_refined"]["l2_error"])
+    return out
+
+
+def run_triangles(g, torch, args):
+    """Simplicial elements (Sec. 2): 128 x 128 cells of [0,1]^2 cut into 32,768 counterclockwise
+    triangles, P3 geometry with the sine perturbation 0.05 sin(2 pi x) sin(2 pi y), P3 DG (10
+    unknowns), S8 (40 directions), sigma_t = 1, sigma_s = 0.5, q = 1: 1,310,720 updates per sweep,
+    swept by the two stored-inverse forms; sweep rate, HBM fraction and time to a 1e-8 change
+    (formation of the stored inverses included)."""
+    import sn_inputs.configs as C
+    prob = C.triangle_problem(128, 3, 3, sn=8)
+    stream = torch.cuda.Stream()
+    ctx = g.setup_problem(prob, device=0, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    gs = ctx.sn_build_graph("face", 10)
+    E, N = prob.mesh.n_elem, 10
+    ups = E * len(prob.w)
+    pk, _ = peaks()
+    ib = 8.0 * (N * N + 2 * N)
+    out = {"workload": "32768 P3 triangles (128x128 cells), sine perturbation 0.05, P3 DG, S8 (40 dirs), "
+                       "sigma_t=1, sigma_s=0.5, q=1", "updates_per_sweep": int(ups),
+           "graph_build_s": time.perf_counter() - t0, "removed_arcs": int(gs["n_removed"]),
+           "levels": int(gs["max_level"] + 1), "mixed_faces": int(gs["n_mixed_faces"])}
+    for name, prec in (("fp64_inv", g.SN_PREC_FP64_INV), ("ds_inv", g.SN_PREC_DS_INV)):
+        mode, bps = ctx.sn_autotune(prec)
+        for _ in range(args.warmup):
+            ctx.sn_si_step(prec)
+        tot = 0.0
+        steps = max(10, args.steps // 2)
+        for _ in range(steps):
+            _, ms = ctx.sn_si_step(prec, time_sweep=True)
+            tot += ms
+        rate = ups * steps / (tot / 1e3)
+        inv_ms = ctx.sn_prepare_inverse(prec)
+        ctx.sn_release_inverse()             # formed again inside the timed solve
+        phi = np.zeros((E, N))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r = ctx.sn_source_iterate(1e-8, 2000, prec, phi_out=phi)
+        out[name] = {"sweep_updates_per_s": rate, "sweep_ms": tot / steps,
+                     "schedule": {"mode": "dataflow" if mode == 1 else "levels", "blocks_per_sm": bps},
+                     "roofline": {"bound": "hbm", "achieved_gbs": rate * ib / 1e9, "peak_gbs": pk["hbm_gbs"],
+                                  "frac": rate * ib / 1e9 / pk["hbm_gbs"], "alg_bytes_per_update": ib},
+                     "inverse_ms": inv_ms, "time_to_1e-8_s": time.perf_counter() - t1, "iters": r["iters"],
+                     "converged": r["converged"]}
+        ctx.sn_release_inverse()
+    ctx.close()
     return out
 
 
@@ -864,6 +913,7 @@ def main():
                     help="relative residual of the conjugate-gradient DSA solve in the accelerated legs")
     ap.add_argument("--dsa-max-cg", type=int, default=100, help="CG iteration cap of one DSA solve")
     ap.add_argument("--no-dsa-thick", action="store_true", help="skip the optically thick DSA measurement")
+    ap.add_argument("--no-triangles", action="store_true", help="skip the triangle-mesh measurement")
     ap.add_argument("--no-straightening", action="store_true",
                     help="skip the curved high-order vs straightened low-order comparison")
     ap.add_argument("--learned-n", type=int, default=48, help="mesh size n^3 of the learned-predictor measurement")
