@@ -69,7 +69,15 @@ void free_dsa(sn_ctx* c) {
   D.ready = false;
 }
 
+// The captured sweep graphs hold the record addresses in their kernel arguments: every graph is
+// dropped whenever the records are freed (and, in form_inverse, before they are allocated).
+void drop_graphs(sn_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+}
+
 void free_inverse(sn_ctx* c) {
+  if (c->d_inv || c->d_fblk || c->d_fidx) drop_graphs(c);
   dfree(c->d_inv);
   dfree(c->d_fblk);
   dfree(c->d_fidx);
@@ -765,6 +773,7 @@ sn_status form_inverse(sn_ctx* c, int prec, float* ms) {
   const size_t npair = (size_t)c->M * c->E;
   const size_t nblk = (size_t)c->Nf * c->Nf;
   c->inv_form = -1;
+  if (!c->d_fidx || !c->d_inv) drop_graphs(c);   // new record addresses: captured sweeps are stale
   if (!c->d_fidx) {
     std::vector<uint32_t> code(npair);
     SN_CUDA(c, cudaMemcpyAsync(code.data(), c->d_facecode, npair * 4, cudaMemcpyDeviceToHost, c->stream));

@@ -110,6 +110,26 @@ def test_stored_inverses_follow_new_materials():
     assert np.array_equal(out2, out)
 
 
+@pytest.mark.parametrize("prec", [3, 4])
+def test_captured_sweeps_follow_reallocated_records(prec):
+    """Sweeps are replayed from captured CUDA graphs whose kernel arguments hold the stored
+    records' addresses: after the records are released and formed again at other addresses (the
+    old ones held by another allocation meanwhile), the replayed sweep must use the new ones."""
+    prob = si.make_config("2d_smooth_q3_p3_s8", n=8)
+    ctx, _ = gpu_ctx(prob, "face")
+    phi, psi_old = random_state(prob, seed=12)
+    first = np.zeros_like(psi_old)
+    ctx.sn_sweep(phi, psi_old, first, prec)                 # captures the sweep graph
+    ctx.sn_release_inverse()
+    N = (prob.p + 1) ** 2
+    hold = torch.empty(len(prob.w) * prob.mesh.n_elem * N * N, dtype=torch.float64, device="cuda")
+    again = np.full_like(psi_old, np.nan)
+    ctx.sn_sweep(phi, psi_old, again, prec)
+    torch.cuda.synchronize()
+    del hold
+    assert np.array_equal(again, first)
+
+
 @pytest.mark.parametrize("prec", [1, 2, 4])
 @pytest.mark.parametrize("p", [2, 3])
 def test_mixed_sweep_with_direction_sources_and_inflow(p, prec):
