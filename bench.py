@@ -175,16 +175,17 @@ FP32_PEAK_TFLOPS = 75.0
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant sweep
 # kernel of a form, from one ncu capture of this workload.  Valid only for the kernel sources it
 # was taken on (SHA-256 of the files below); any later change to them reports null.
-KERNEL_SOURCES = ["paper_1810_11080_gb300/csrc/sweep.cu", "paper_1810_11080_gb300/csrc/sweep_body.cuh",
-                  "paper_1810_11080_gb300/csrc/common.h"]
+KERNEL_SOURCES = ["paper_1810_11080_gb300/csrc/" + f for f in
+                  ("sweep.cu", "sweep_inv.cu", "sweep_kernels.cuh", "sweep_body.cuh", "inverse_body.cuh",
+                   "devmath.cuh", "common.h")]
 TRAFFIC = {
-    # one launch = one sweep: the whole launch captured (350.3 MB read + 154.6 MB written)
-    ("fp64", "dataflow"): {"bytes_per_launch": 504885760, "capture": "ncu --set full, sweep_flow_kernel<2,3,0>, "
-                           "first timed launch", "sources_sha256": "19dfca2fad2059fa3bd974b94c9b5c6306f594fa3f737cc9f4077892309646d1"},
-    # three mid-sweep level launches (5,000-5,080 pairs, 5.69-5.72 MB read, cold caches), scaled to the
-    # sweep's average level of 2,570 pairs at the captured 1,124 bytes per pair
-    ("mixed_ds", "levels"): {"bytes_per_launch": 2888000, "capture": "ncu --set full, sweep_level_kernel<2,3,2>, "
-                             "levels 128-130 scaled per pair", "sources_sha256": "19dfca2fad2059fa3bd974b94c9b5c6306f594fa3f737cc9f4077892309646d1"},
+    # one launch = one sweep: the whole launch captured (350.6 MB read + 154.3 MB written)
+    ("fp64", "dataflow"): {"bytes_per_launch": 504915712, "capture": "ncu --set full, sweep_flow_kernel<2,3,0>, "
+                           "first timed launch", "sources_sha256": "1924cdd6ac9841e31d1c02bffb651ec50dc485d2065dc32795c2baf70a110eeb"},
+    # three mid-sweep level launches (5,000-5,080 pairs, 14.4-14.6 MB read, writes still in L2 at the
+    # end of each launch), scaled to the sweep's average level of 2,570 pairs at 2,885 bytes per pair
+    ("ds_inv", "levels"): {"bytes_per_launch": 7414450, "capture": "ncu --set full, el_level_kernel<TensorEl<2,3>,4>, "
+                           "levels 128-130 scaled per pair", "sources_sha256": "1924cdd6ac9841e31d1c02bffb651ec50dc485d2065dc32795c2baf70a110eeb"},
 }
 
 
