@@ -185,10 +185,11 @@ sn_status sn_set_launch(sn_ctx* ctx, int mode, int blocks_per_sm);
  * context and of batches created afterwards.  Errors: SN_EINVAL (polls < 0). */
 sn_status sn_set_spin_limit(sn_ctx* ctx, int64_t polls);
 
-/* Autotuner (no counterpart in the paper): times three source iterations of every candidate
- * schedule -- per-level launches, or the dataflow launch with 1, 2, 3, 4 or the maximum resident
- * CTAs per SM -- keeps the fastest via sn_set_launch and resets the iteration state
- * (sn_si_begin(ctx, NULL)).  mode_out / blocks_per_sm_out may be NULL. */
+/* Autotuner (no counterpart in the paper): runs two warm-up source iterations and then five
+ * timed ones of every candidate schedule -- per-level launches, or the dataflow launch with 1, 2,
+ * 3, 4 or the maximum resident CTAs per SM -- keeps the one with the fastest sweep via
+ * sn_set_launch and resets the iteration state (sn_si_begin(ctx, NULL)).  mode_out /
+ * blocks_per_sm_out may be NULL. */
 sn_status sn_autotune(sn_ctx* ctx, int precision, int* mode_out, int* blocks_per_sm_out);
 
 /* Stored local inverses of the stored-inverse forms (no counterpart in the paper, which factors

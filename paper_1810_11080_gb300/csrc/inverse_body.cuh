@@ -4,8 +4,14 @@
 // (invert_pair) and a sweep only forms the right-hand side and applies the inverse:
 //   psi_e = Ainv (src_e + sum_{inflow faces f} B_f trace_f).
 // Stored per pair q = d E + e: Ainv column-major at inv + q N^2 (entry (i, j) at j N + i, so the
-// lanes of a segment read each column as one contiguous run), and the block B_f of its r-th
-// inflow face, row-major, at fblk + (fidx[q] + r) Nf^2 (r counts the inflow faces in face order).
+// lanes of a segment read each column as one contiguous run), and per inflow face (rank r among
+// the pair's inflow faces, in face order, slot fidx[q] + r):
+//   2D: the folded block C_f = Ainv B_f (N x Nf, column-major, at fblk + slot N Nf), so that
+//       psi_e = Ainv src_e + sum_f C_f trace_f: every lane applies the faces with Nf multiply-adds
+//       per face and no exchange, and in the dataflow schedule Ainv src_e is formed before the
+//       wait for upwind data;
+//   3D: the block B_f itself (Nf x Nf, row-major, at fblk + slot Nf^2; C_f would add 27 x 9
+//       entries per face to 27 x 27, too much memory at the largest sizes).
 // SN_PREC_FP64_INV keeps doubles and applies them in FP64; SN_PREC_DS_INV keeps (hi, lo) FP32
 // pairs of the same FP64 values and applies them in double-single arithmetic on the FP32 pipe.
 // The code is written for an element policy El (node counts, face count, face-node maps), so the
@@ -104,11 +110,14 @@ __device__ __forceinline__ void face_rhs_el(const DevProblem& Pb, const SweepArg
 
 // Inverse and inflow blocks of one pair, formed in FP64 by Gauss-Jordan elimination with partial
 // pivoting (row-per-lane; see gj32 for the bookkeeping of V in pivot-step order).  A is assembled
-// as in body64.  DSOUT: store (hi, lo) FP32 pairs instead of doubles.
+// as in body64.  DSOUT: store (hi, lo) FP32 pairs instead of doubles.  2D: after the inverse is
+// stored, every lane forms its rows of C_f = Ainv B_f from its stored row of Ainv and the block
+// rows held by the face lanes.
 template <class El, bool DSOUT>
 __device__ __forceinline__ void invert_pair(const DevProblem& Pb, const SweepArgs& sa, int64_t q, bool valid,
                                             int lane) {
-  constexpr int N = El::N, NF = El::NF, W = El::W, DIM = El::DIMV;
+  constexpr int N = El::N, NF = El::NF, W = El::W, DIM = El::DIMV, NFC = El::NFC;
+  constexpr bool FOLD = DIM == 2;
   constexpr unsigned FULL = 0xffffffffu;
   const int i = lane % W;
   const int64_t E = Pb.E;
@@ -124,6 +133,14 @@ __device__ __forceinline__ void invert_pair(const DevProblem& Pb, const SweepArg
       reinterpret_cast<float2*>(base)[idx] = v;
     } else {
       base[idx] = x;
+    }
+  };
+  auto get = [&](int64_t idx, const double* base) -> double {
+    if constexpr (DSOUT) {
+      const float2 v = reinterpret_cast<const float2*>(base)[idx];
+      return (double)v.x + (double)v.y;
+    } else {
+      return base[idx];
     }
   };
   double a[N];
@@ -142,8 +159,13 @@ __device__ __forceinline__ void invert_pair(const DevProblem& Pb, const SweepArg
   const uint32_t code = valid ? sa.facecode[q] : 0u;
   const int mbase = (valid && (code & 0xAAAu)) ? sa.mixed_off[q] : 0;
   const int64_t bidx = valid ? sa.fidx[q] : 0;
+  double Bkeep[FOLD ? NFC : 1][NF];       // 2D: this lane's block row of each inflow face (else 0)
+  if constexpr (FOLD)
+    static_for<0, NFC>([&](auto fconst) {
+      static_for<0, NF>([&](auto jconst) { Bkeep[decltype(fconst)::value][decltype(jconst)::value] = 0.0; });
+    });
   int mrank = 0, rank = 0;
-  static_for<0, El::NFC>([&](auto fconst) {
+  static_for<0, NFC>([&](auto fconst) {
     constexpr int f = decltype(fconst)::value;
     const uint32_t mode = face_mode(code, f);
     const int fi = row ? El::face_node(f, i) : -1;
@@ -154,7 +176,8 @@ __device__ __forceinline__ void invert_pair(const DevProblem& Pb, const SweepArg
       static_for<0, NF>([&](auto jconst) {
         constexpr int fj = decltype(jconst)::value;
         a[El::vol_node(f, fj)] += Brow[fj];
-        put(o + fj, Brow[fj], sa.fblk);
+        if constexpr (FOLD) Bkeep[f][fj] = Brow[fj];
+        else put(o + fj, Brow[fj], sa.fblk);
       });
     }
     if (mode == MODE_MIXED) ++mrank;
@@ -198,11 +221,47 @@ __device__ __forceinline__ void invert_pair(const DevProblem& Pb, const SweepArg
       put(o + (plk[m] % W) * N, v[m] * myinv, sa.inv);
     });
   }
+  if constexpr (FOLD) {
+    __syncwarp();                        // the segment's stored rows are visible to all its lanes
+    int r2 = 0;
+    static_for<0, NFC>([&](auto fconst) {
+      constexpr int f = decltype(fconst)::value;
+      const uint32_t mode = face_mode(code, f);
+      // block rows of face f from the face lanes (exchanged by every lane, used if f is inflow)
+      double bsh[NF][NF];
+      static_for<0, NF>([&](auto iconst) {
+        constexpr int fi = decltype(iconst)::value;
+        static_for<0, NF>([&](auto jconst) {
+          constexpr int fj = decltype(jconst)::value;
+          bsh[fi][fj] = __shfl_sync(FULL, Bkeep[f][fj], El::vol_node(f, fi), W);
+        });
+      });
+      if (row && mode != MODE_NONE) {
+        double arow[NF];
+        static_for<0, NF>([&](auto iconst) {
+          constexpr int fi = decltype(iconst)::value;
+          arow[fi] = get(q * (N * N) + El::vol_node(f, fi) * N + i, sa.inv);
+        });
+        const int64_t o = (bidx + r2) * (N * NF) + i;
+        static_for<0, NF>([&](auto jconst) {
+          constexpr int fj = decltype(jconst)::value;
+          double c = 0.0;
+          static_for<0, NF>([&](auto iconst) {
+            constexpr int fi = decltype(iconst)::value;
+            c = fma(arow[fi], bsh[fi][fj], c);
+          });
+          put(o + fj * N, c, sa.fblk);
+        });
+      }
+      if (mode != MODE_NONE) ++r2;
+    });
+  }
 }
 
-// ------------------------------------------------------------------ FP64 application
+// ------------------------------------------------------------------ FP64 application, stored blocks (3D)
 template <class El, bool DF>
-__device__ __forceinline__ void bodyinv(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid, int lane) {
+__device__ __forceinline__ void bodyinv_blocks(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid,
+                                               int lane) {
   constexpr int N = El::N, NF = El::NF, W = El::W, DIM = El::DIMV;
   constexpr unsigned FULL = 0xffffffffu;
   constexpr bool BPRE = DIM == 2;      // inflow block rows held in registers across the wait (2D)
@@ -292,14 +351,14 @@ __device__ __forceinline__ void bodyinv(const DevProblem& Pb, const SweepArgs& s
   publish<DF, W>(Pb, sa, e, d, valid, i);
 }
 
-// ------------------------------------------------------------------ double-single application
+// ------------------------------------------------------------------ double-single application, stored blocks (3D)
 // The right-hand side is accumulated and the inverse applied in double-single arithmetic
 // (error-free FP32 products and sums, ~2^-48 relative), from the (hi, lo) splits of the stored
 // FP64 inverse and blocks, of the source and of the upwind traces; no FP64 instruction on the
 // solve path except the final psi = hi + lo.
 template <class El, bool DF>
-__device__ __forceinline__ void bodydsinv(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid,
-                                          int lane) {
+__device__ __forceinline__ void bodydsinv_blocks(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid,
+                                                 int lane) {
   constexpr int N = El::N, NF = El::NF, W = El::W, DIM = El::DIMV, NFC = El::NFC;
   constexpr unsigned FULL = 0xffffffffu;
   constexpr bool BPRE = DIM == 2;
@@ -434,4 +493,247 @@ __device__ __forceinline__ void bodydsinv(const DevProblem& Pb, const SweepArgs&
   publish<DF, W>(Pb, sa, e, d, valid, i);
 }
 
+// ------------------------------------------------------------------ folded blocks (2D)
+// psi_i = sum_j Ainv[i][j] src_j + sum_{inflow f} sum_fj C_f[i][fj] trace_f[fj]: every lane loads
+// the face traces itself (the same addresses across the segment) and applies its rows of C_f; the
+// source part needs the segment's right-hand side values (exchanged by shuffles) and, in the
+// dataflow schedule, is formed before the wait (the source was written by an earlier launch).
+template <class El, bool DF>
+__device__ __forceinline__ void bodyinv_fold(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid,
+                                             int lane) {
+  constexpr int N = El::N, NF = El::NF, W = El::W, DIM = El::DIMV, NFC = El::NFC;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int i = lane % W;
+  const int M = Pb.M;
+  const int64_t E = Pb.E;
+  const int64_t e = pr / M;
+  const int d = pr % M;
+  const int64_t q = (int64_t)d * E + e;
+  const bool row = valid && (i < N);
+  const uint32_t code = valid ? sa.facecode[q] : 0u;
+  const int64_t bidx = valid ? sa.fidx[q] : 0;
+  double ainv[N];
+  double Cf[NFC][NF];
+  double bs = 0.0;
+  if (row) {
+    const double* ai = sa.inv + q * (N * N) + i;
+    static_for<0, N>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      ainv[j] = __ldcs(ai + j * N);      // read once per sweep: streamed past the caches
+    });
+    if (Pb.q_dir != nullptr) {
+      const double* blk = Pb.elem + e * Pb.blk;
+      const double* qd = Pb.q_dir + q * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) bs = fma(__ldg(blk + DIM * N * N + i * N + j), qd[j], bs);
+    }
+  } else {
+    static_for<0, N>([&](auto jconst) { ainv[decltype(jconst)::value] = 0.0; });
+  }
+  int rank = 0;
+  static_for<0, NFC>([&](auto fconst) {
+    constexpr int f = decltype(fconst)::value;
+    const uint32_t mode = face_mode(code, f);
+    const double* cf = sa.fblk + (bidx + rank) * (N * NF) + i;
+    static_for<0, NF>([&](auto jconst) {
+      constexpr int fj = decltype(jconst)::value;
+      Cf[f][fj] = (row && mode != MODE_NONE) ? __ldcs(cf + fj * N) : 0.0;
+    });
+    if (mode != MODE_NONE) ++rank;
+  });
+  int64_t nbv[NFC];
+  int fov[NFC];
+  static_for<0, NFC>([&](auto fconst) {
+    constexpr int f = decltype(fconst)::value;
+    nbv[f] = valid ? Pb.nbr[e * NFC + f] : -1;
+    fov[f] = valid ? (Pb.nbr_face[e * NFC + f] | (Pb.orient[e * NFC + f] << 8)) : 0;
+  });
+  double y0 = 0.0, y1 = 0.0;
+  auto apply_src = [&]() {
+    if (row) bs += sa.src[e * N + i];
+    static_for<0, N>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      const double bj = __shfl_sync(FULL, bs, j, W);
+      if (j & 1) y1 = fma(ainv[j], bj, y1);
+      else y0 = fma(ainv[j], bj, y0);
+    });
+  };
+  if constexpr (DF) {
+    apply_src();
+    wait_upwind_n<NFC>(Pb, sa, code, e, d, valid);
+  } else {
+    pdl_wait();                          // sources and upwind traces come from earlier launches
+    pdl_launch_dependents();
+    apply_src();
+  }
+  double x = y0 + y1;
+  static_for<0, NFC>([&](auto fconst) {
+    constexpr int f = decltype(fconst)::value;
+    const uint32_t mode = face_mode(code, f);
+    const int64_t nb = nbv[f];
+    if (row && mode != MODE_NONE) {
+      if (nb >= 0) {
+        const bool lag = face_lagged(code, f);
+        const double* pnb = (lag ? sa.psi_old : sa.psi_new) + ((int64_t)d * E + nb) * N;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) {
+          const double* pt = pnb + El::trace_node(fov[f] & 0xff, fov[f] >> 8, fj);
+          x = fma(Cf[f][fj], lag ? __ldg(pt) : trace_load<DF>(pt), x);
+        }
+      } else if (Pb.psi_inc != nullptr) {
+        const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * NFC + f]) * NF;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) x = fma(Cf[f][fj], __ldg(pin + fj), x);
+      }
+    }
+  });
+  if (row) {
+    const int64_t o = q * N + i;
+    sa.psi_new[o] = x;
+    if (sa.psi_new_h != nullptr) {
+      const float h = (float)x;
+      sa.psi_new_h[o] = h;
+      sa.psi_new_l[o] = (float)(x - (double)h);
+    }
+  }
+  publish<DF, W>(Pb, sa, e, d, valid, i);
+}
+
+template <class El, bool DF>
+__device__ __forceinline__ void bodydsinv_fold(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid,
+                                               int lane) {
+  constexpr int N = El::N, NF = El::NF, W = El::W, DIM = El::DIMV, NFC = El::NFC;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int i = lane % W;
+  const int M = Pb.M;
+  const int64_t E = Pb.E;
+  const int64_t e = pr / M;
+  const int d = pr % M;
+  const int64_t q = (int64_t)d * E + e;
+  const bool row = valid && (i < N);
+  const uint32_t code = valid ? sa.facecode[q] : 0u;
+  const int64_t bidx = valid ? sa.fidx[q] : 0;
+  const float2* inv2 = reinterpret_cast<const float2*>(sa.inv);
+  const float2* fb2 = reinterpret_cast<const float2*>(sa.fblk);
+  float2 A[N];
+  float2 Cf[NFC][NF];
+  float bh = 0.0f, bl = 0.0f;
+  if (row) {
+    const float2* ai = inv2 + q * (N * N) + i;
+    static_for<0, N>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      A[j] = __ldcs(ai + j * N);
+    });
+    if (Pb.q_dir != nullptr) {           // direction-dependent source (tests): FP64, then split
+      const double* blk = Pb.elem + e * Pb.blk;
+      const double* qd = Pb.q_dir + q * N;
+      double qb = 0.0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) qb = fma(__ldg(blk + DIM * N * N + i * N + j), qd[j], qb);
+      ds_split(qb, bh, bl);
+    }
+  } else {
+    static_for<0, N>([&](auto jconst) { A[decltype(jconst)::value] = make_float2(0.0f, 0.0f); });
+  }
+  int rank = 0;
+  static_for<0, NFC>([&](auto fconst) {
+    constexpr int f = decltype(fconst)::value;
+    const uint32_t mode = face_mode(code, f);
+    const float2* cf = fb2 + (bidx + rank) * (N * NF) + i;
+    static_for<0, NF>([&](auto jconst) {
+      constexpr int fj = decltype(jconst)::value;
+      Cf[f][fj] = (row && mode != MODE_NONE) ? __ldcs(cf + fj * N) : make_float2(0.0f, 0.0f);
+    });
+    if (mode != MODE_NONE) ++rank;
+  });
+  int64_t nbv[NFC];
+  int fov[NFC];
+  static_for<0, NFC>([&](auto fconst) {
+    constexpr int f = decltype(fconst)::value;
+    nbv[f] = valid ? Pb.nbr[e * NFC + f] : -1;
+    fov[f] = valid ? (Pb.nbr_face[e * NFC + f] | (Pb.orient[e * NFC + f] << 8)) : 0;
+  });
+  // y = Ainv src in double-single, four independent chains
+  float xh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, xl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  auto apply_src = [&]() {
+    if (row) ds_add(bh, bl, sa.src_h[e * N + i], sa.src_l[e * N + i]);
+    static_for<0, N>([&](auto jconst) {
+      constexpr int j = decltype(jconst)::value;
+      const float bjh = __shfl_sync(FULL, bh, j, W);
+      const float bjl = __shfl_sync(FULL, bl, j, W);
+      float ph, pl;
+      ds_mul(A[j].x, A[j].y, bjh, bjl, ph, pl);
+      ds_add(xh[j & 3], xl[j & 3], ph, pl);
+    });
+  };
+  if constexpr (DF) {
+    apply_src();
+    wait_upwind_n<NFC>(Pb, sa, code, e, d, valid);
+  } else {
+    pdl_wait();                          // sources and upwind traces come from earlier launches
+    pdl_launch_dependents();
+    apply_src();
+  }
+  // faces: C_f trace_f into chains 2 and 3 (even / odd face nodes)
+  static_for<0, NFC>([&](auto fconst) {
+    constexpr int f = decltype(fconst)::value;
+    const uint32_t mode = face_mode(code, f);
+    const int64_t nb = nbv[f];
+    if (row && mode != MODE_NONE) {
+      if (nb >= 0) {
+        const bool lag = face_lagged(code, f);
+        const int64_t base = ((int64_t)d * E + nb) * N;
+        const float* ph_ = (lag ? sa.psi_old_h : sa.psi_new_h) + base;
+        const float* pl_ = (lag ? sa.psi_old_l : sa.psi_new_l) + base;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) {
+          const int o = El::trace_node(fov[f] & 0xff, fov[f] >> 8, fj);
+          float th, tl, qh, ql;
+          if (!lag && DF) {
+            th = __ldcg(ph_ + o);
+            tl = __ldcg(pl_ + o);
+          } else {
+            th = __ldg(ph_ + o);
+            tl = __ldg(pl_ + o);
+          }
+          ds_mul(Cf[f][fj].x, Cf[f][fj].y, th, tl, qh, ql);
+          ds_add(xh[2 + (fj & 1)], xl[2 + (fj & 1)], qh, ql);
+        }
+      } else if (Pb.psi_inc != nullptr) {
+        const double* pin = Pb.psi_inc + ((int64_t)d * Pb.n_bdr + Pb.bdr_index[e * NFC + f]) * NF;
+#pragma unroll
+        for (int fj = 0; fj < NF; ++fj) {
+          float th, tl, qh, ql;
+          ds_split(__ldg(pin + fj), th, tl);
+          ds_mul(Cf[f][fj].x, Cf[f][fj].y, th, tl, qh, ql);
+          ds_add(xh[2 + (fj & 1)], xl[2 + (fj & 1)], qh, ql);
+        }
+      }
+    }
+  });
+  ds_add(xh[0], xl[0], xh[1], xl[1]);
+  ds_add(xh[2], xl[2], xh[3], xl[3]);
+  ds_add(xh[0], xl[0], xh[2], xl[2]);
+  if (row) {
+    const int64_t o = q * N + i;
+    sa.psi_new_h[o] = xh[0];
+    sa.psi_new_l[o] = xl[0];
+    sa.psi_new[o] = (double)xh[0] + (double)xl[0];
+  }
+  publish<DF, W>(Pb, sa, e, d, valid, i);
+}
+
+// The two application forms: folded blocks in 2D, stored blocks in 3D.
+template <class El, bool DF>
+__device__ __forceinline__ void bodyinv(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid, int lane) {
+  if constexpr (El::DIMV == 2) bodyinv_fold<El, DF>(Pb, sa, pr, valid, lane);
+  else bodyinv_blocks<El, DF>(Pb, sa, pr, valid, lane);
+}
+
+template <class El, bool DF>
+__device__ __forceinline__ void bodydsinv(const DevProblem& Pb, const SweepArgs& sa, int32_t pr, bool valid,
+                                          int lane) {
+  if constexpr (El::DIMV == 2) bodydsinv_fold<El, DF>(Pb, sa, pr, valid, lane);
+  else bodydsinv_blocks<El, DF>(Pb, sa, pr, valid, lane);
+}
 }  // namespace sn
