@@ -40,6 +40,13 @@ struct TensorEl {
     trace_affine<DIM, P_>(fn, oc, c0, ci, cj);
     return c0 + ci * (fj % NP1) + cj * (fj / NP1);
   }
+  // all NF trace indices of one face at once (the face's constants computed once)
+  __device__ static void trace_nodes(int fn, int oc, int (&t)[NF]) {
+    int c0, ci, cj;
+    trace_affine<DIM, P_>(fn, oc, c0, ci, cj);
+#pragma unroll
+    for (int fj = 0; fj < NF; ++fj) t[fj] = c0 + ci * (fj % NP1) + cj * (fj / NP1);
+  }
 };
 
 // Triangles: faces f0 = v0 v1, f1 = v1 v2, f2 = v2 v0, face nodes in increasing face coordinate
@@ -60,6 +67,10 @@ struct TriEl {
   }
   __host__ __device__ static constexpr int vol_node(int f, int fj) { return tri_edge_node(P_, f, fj); }
   __device__ static int trace_node(int fn, int oc, int fj) { return tri_edge_node(P_, fn, (oc & 1) ? P_ - fj : fj); }
+  __device__ static void trace_nodes(int fn, int oc, int (&t)[NF]) {
+#pragma unroll
+    for (int fj = 0; fj < NF; ++fj) t[fj] = trace_node(fn, oc, fj);
+  }
 };
 
 // FP64 inflow block row fi of face f: -Omega . FN_f (whole-inflow face) or the stored block of a
@@ -96,9 +107,11 @@ __device__ __forceinline__ void face_rhs_el(const DevProblem& Pb, const SweepArg
     const double* ps = lag ? sa.psi_old : sa.psi_new;
     const int fn = Pb.nbr_face[e * NFC + f], oc = Pb.orient[e * NFC + f];
     const double* pnb = ps + ((int64_t)d * Pb.E + nb) * N;
+    int tix[NF];
+    El::trace_nodes(fn, oc, tix);
 #pragma unroll
     for (int fj = 0; fj < NF; ++fj) {
-      const double* pt = pnb + El::trace_node(fn, oc, fj);
+      const double* pt = pnb + tix[fj];
       b = fma(Brow[fj], lag ? __ldg(pt) : trace_load<DF>(pt), b);
     }
   } else if (Pb.psi_inc != nullptr) {
@@ -442,9 +455,11 @@ __device__ __forceinline__ void bodydsinv_blocks(const DevProblem& Pb, const Swe
         const int64_t base = ((int64_t)d * E + nb) * N;
         const float* ph_ = (lag ? sa.psi_old_h : sa.psi_new_h) + base;
         const float* pl_ = (lag ? sa.psi_old_l : sa.psi_new_l) + base;
+        int tix[NF];
+        El::trace_nodes(fov[f] & 0xff, fov[f] >> 8, tix);
 #pragma unroll
         for (int fj = 0; fj < NF; ++fj) {
-          const int o = El::trace_node(fov[f] & 0xff, fov[f] >> 8, fj);
+          const int o = tix[fj];
           float th, tl, qh, ql;
           if (!lag && DF) {
             th = __ldcg(ph_ + o);
@@ -575,9 +590,11 @@ __device__ __forceinline__ void bodyinv_fold(const DevProblem& Pb, const SweepAr
       if (nb >= 0) {
         const bool lag = face_lagged(code, f);
         const double* pnb = (lag ? sa.psi_old : sa.psi_new) + ((int64_t)d * E + nb) * N;
+        int tix[NF];
+        El::trace_nodes(fov[f] & 0xff, fov[f] >> 8, tix);
 #pragma unroll
         for (int fj = 0; fj < NF; ++fj) {
-          const double* pt = pnb + El::trace_node(fov[f] & 0xff, fov[f] >> 8, fj);
+          const double* pt = pnb + tix[fj];
           x = fma(Cf[f][fj], lag ? __ldg(pt) : trace_load<DF>(pt), x);
         }
       } else if (Pb.psi_inc != nullptr) {
@@ -685,9 +702,11 @@ __device__ __forceinline__ void bodydsinv_fold(const DevProblem& Pb, const Sweep
         const int64_t base = ((int64_t)d * E + nb) * N;
         const float* ph_ = (lag ? sa.psi_old_h : sa.psi_new_h) + base;
         const float* pl_ = (lag ? sa.psi_old_l : sa.psi_new_l) + base;
+        int tix[NF];
+        El::trace_nodes(fov[f] & 0xff, fov[f] >> 8, tix);
 #pragma unroll
         for (int fj = 0; fj < NF; ++fj) {
-          const int o = El::trace_node(fov[f] & 0xff, fov[f] >> 8, fj);
+          const int o = tix[fj];
           float th, tl, qh, ql;
           if (!lag && DF) {
             th = __ldcg(ph_ + o);

@@ -54,6 +54,13 @@ __global__ void __launch_bounds__(128, (inv_minb<El, PREC>())) el_level_kernel(D
   solve_el<El, PREC, false>(Pb, sa, pr < 0 ? 0 : pr, pr >= 0, lane);
 }
 
+// Work-queue granularity of the dataflow kernel: a warp takes FLOW_CHUNK consecutive tasks
+// (FLOW_CHUNK El::SPW pairs of the level-ordered list) per atomic on the queue head and solves
+// them in order; the bodies here are light enough that one atomic per task would make the shared
+// queue head the bottleneck.  Still deadlock-free: a pair waits only for pairs earlier in the
+// list, which were handed out before it to running warps.
+constexpr int FLOW_CHUNK = 2;
+
 template <class El, int PREC>
 __global__ void __launch_bounds__(128, (inv_minb<El, PREC>() > 2 ? inv_minb<El, PREC>() - 1 : 2))
     el_flow_kernel(DevProblem Pb, SweepArgs sa, const int32_t* __restrict__ pairs, int64_t count,
@@ -62,12 +69,16 @@ __global__ void __launch_bounds__(128, (inv_minb<El, PREC>() > 2 ? inv_minb<El, 
   const int lane = threadIdx.x & 31;
   while (true) {
     long long t = 0;
-    if (lane == 0) t = (*(volatile int*)sa.err) ? count : (long long)atomicAdd(head, (unsigned long long)El::SPW);
+    if (lane == 0)
+      t = (*(volatile int*)sa.err) ? count : (long long)atomicAdd(head, (unsigned long long)(FLOW_CHUNK * El::SPW));
     t = __shfl_sync(FULL, t, 0);
     if (t >= count) break;
-    const int64_t item = t + lane / El::W;
-    const int32_t pr = item < count ? pairs[item] : -1;
-    solve_el<El, PREC, true>(Pb, sa, pr < 0 ? 0 : pr, pr >= 0, lane);
+#pragma unroll 1
+    for (int c = 0; c < FLOW_CHUNK; ++c) {
+      const int64_t item = t + c * El::SPW + lane / El::W;
+      const int32_t pr = item < count ? pairs[item] : -1;
+      solve_el<El, PREC, true>(Pb, sa, pr < 0 ? 0 : pr, pr >= 0, lane);
+    }
   }
 }
 
