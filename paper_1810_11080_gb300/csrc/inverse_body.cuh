@@ -452,14 +452,16 @@ __device__ __forceinline__ void bodydsinv_blocks(const DevProblem& Pb, const Swe
       }
       if (nb >= 0) {                     // upwind neighbour's (hi, lo) split of the trace
         const bool lag = face_lagged(code, f);
-        const int64_t base = ((int64_t)d * E + nb) * N;
+        // the blocks path serves the tensor elements (3D): the trace index is affine in the face
+        // node, c0 + ci I + cj J, with three registers instead of a table of NF
+        int c0, ci, cj;
+        trace_affine<DIM, El::NP1 - 1>(fov[f] & 0xff, fov[f] >> 8, c0, ci, cj);
+        const int64_t base = ((int64_t)d * E + nb) * N + c0;
         const float* ph_ = (lag ? sa.psi_old_h : sa.psi_new_h) + base;
         const float* pl_ = (lag ? sa.psi_old_l : sa.psi_new_l) + base;
-        int tix[NF];
-        El::trace_nodes(fov[f] & 0xff, fov[f] >> 8, tix);
 #pragma unroll
         for (int fj = 0; fj < NF; ++fj) {
-          const int o = tix[fj];
+          const int o = ci * (fj % El::NP1) + cj * (fj / El::NP1);
           float th, tl, qh, ql;
           if (!lag && DF) {
             th = __ldcg(ph_ + o);
