@@ -72,12 +72,18 @@ def alg_work(dim, p):
     return ALG_WORK.get((dim, p), {"flops": None, "bytes": None})
 
 
-def inv_alg_bytes(dim, p):
-    """DRAM bytes one update of the stored-inverse form must move: its row block of the stored
-    inverse (N^2 doubles, read once per sweep, far larger than L2), the angular flux written
-    (N doubles) and about N doubles of inflow traces and source."""
-    N = (p + 1) ** dim
-    return 8.0 * (N * N + 2 * N)
+def inv_alg_bytes(dim, p, simplex=False):
+    """DRAM bytes one update of a stored-inverse form must move: its record, read once per sweep
+    and far larger than L2 -- the inverse (N^2 entries) and one block per inflow face (2D: the
+    folded N x Nf block, 3D: the Nf x Nf block; dim inflow faces on average for quadrilaterals
+    and hexahedra, 1.5 for triangles) -- plus the angular flux written (N) and about N entries of
+    traces and source; 8 bytes per entry."""
+    if simplex:
+        N, Nf, faces = (p + 1) * (p + 2) // 2, p + 1, 1.5
+    else:
+        N, Nf, faces = (p + 1) ** dim, (p + 1) ** (dim - 1), dim
+    blk = N * Nf if dim == 2 else Nf * Nf
+    return 8.0 * (N * N + faces * blk + 2 * N)
 
 
 class ClockSampler:
@@ -179,13 +185,13 @@ KERNEL_SOURCES = ["paper_1810_11080_gb300/csrc/" + f for f in
                   ("sweep.cu", "sweep_inv.cu", "sweep_kernels.cuh", "sweep_body.cuh", "inverse_body.cuh",
                    "devmath.cuh", "common.h")]
 TRAFFIC = {
-    # one launch = one sweep: the whole launch captured (350.6 MB read + 154.3 MB written)
-    ("fp64", "dataflow"): {"bytes_per_launch": 504915712, "capture": "ncu --set full, sweep_flow_kernel<2,3,0>, "
-                           "first timed launch", "sources_sha256": "1924cdd6ac9841e31d1c02bffb651ec50dc485d2065dc32795c2baf70a110eeb"},
-    # three mid-sweep level launches (5,000-5,080 pairs, 14.4-14.6 MB read, writes still in L2 at the
-    # end of each launch), scaled to the sweep's average level of 2,570 pairs at 2,885 bytes per pair
-    ("ds_inv", "levels"): {"bytes_per_launch": 7414450, "capture": "ncu --set full, el_level_kernel<TensorEl<2,3>,4>, "
-                           "levels 128-130 scaled per pair", "sources_sha256": "1924cdd6ac9841e31d1c02bffb651ec50dc485d2065dc32795c2baf70a110eeb"},
+    # one launch = one sweep: the whole launch captured (351.4 MB read + 154.7 MB written)
+    ("fp64", "dataflow"): {"bytes_per_launch": 506104320, "capture": "ncu --set full, sweep_flow_kernel<2,3,0>, "
+                           "first timed launch", "sources_sha256": "cad2ebc8eb59e2feb8334a6d551d51ef50523e11fa4d8035182663b5f82601c5"},
+    # three mid-sweep level launches (5,000-5,080 pairs, 18.3-18.5 MB read, writes still in L2 at the
+    # end of each launch), scaled to the sweep's average level of 2,570 pairs at 3,652 bytes per pair
+    ("ds_inv", "levels"): {"bytes_per_launch": 9385640, "capture": "ncu --set full, el_level_kernel<TensorEl<2,3>,4>, "
+                           "levels 128-130 scaled per pair", "sources_sha256": "cad2ebc8eb59e2feb8334a6d551d51ef50523e11fa4d8035182663b5f82601c5"},
 }
 
 
@@ -649,7 +655,7 @@ def run_triangles(g, torch, args):
     E, N = prob.mesh.n_elem, 10
     ups = E * len(prob.w)
     pk, _ = peaks()
-    ib = 8.0 * (N * N + 2 * N)
+    ib = inv_alg_bytes(2, 3, simplex=True)
     out = {"workload": "32768 P3 triangles (128x128 cells), sine perturbation 0.05, P3 DG, S8 (40 dirs), "
                        "sigma_t=1, sigma_s=0.5, q=1", "updates_per_sweep": int(ups),
            "graph_build_s": time.perf_counter() - t0, "removed_arcs": int(gs["n_removed"]),
