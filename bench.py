@@ -448,7 +448,10 @@ def run_gpu(args):
     if not args.no_triangles:
         out["triangles"] = run_triangles(g, torch, args)
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args)
+        iters = {"2d": tts["fp64"]["iters"],
+                 "3d_twist": out.get("twisted_3d", {}).get("fp64", {}).get("iters"),
+                 "3d_s12": out.get("learned", {}).get("plain_fp64", {}).get("iters")}
+        out["cpu_baseline"] = cpu_baseline(args, iters)
     return out
 
 
@@ -793,14 +796,18 @@ def run_batch(g, torch, args):
     return res
 
 
-def _oracle_worker(conn, d):
+def _oracle_worker(conn, d, workload=None, n=None):
     """One host process of the oracle timing: builds the workload's discretisation and direction
     d's graph once, then on every "go" times the oracle's work for one direction of one sweep
     (local assembly + factorisation of every element's system, and the lagged sweep)."""
     from oracle.dg import Discretization
     from oracle.graph import build_graph_dirs
     from oracle.sweep import Sweeper
-    prob = make_problem()
+    if workload is None:
+        prob = make_problem()
+    else:
+        import sn_inputs as si
+        prob = si.make_config(workload, n=n)
     disc = Discretization(prob)
     G = build_graph_dirs(disc, [d], "face")
     E, N, M = disc.E, disc.N, disc.M_dirs
@@ -821,7 +828,7 @@ class OracleWorkers:
     owning direction i mod 40 of the workload; round() runs one direction in every process at
     once and returns the wall time until the last one finishes."""
 
-    def __init__(self, procs):
+    def __init__(self, procs, workload=None, n=None, n_dirs=40):
         import multiprocessing as mp
         for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
             os.environ[k] = "1"                                # one thread per process
@@ -829,7 +836,7 @@ class OracleWorkers:
         self.conns, self.procs = [], []
         for i in range(procs):
             a, b = ctx.Pipe()
-            pr = ctx.Process(target=_oracle_worker, args=(b, i % 40), daemon=True)
+            pr = ctx.Process(target=_oracle_worker, args=(b, i % n_dirs, workload, n), daemon=True)
             pr.start()
             self.conns.append(a)
             self.procs.append(pr)
@@ -855,9 +862,12 @@ def oracle_procs():
     return max(1, min(os.cpu_count() or 1, 16))
 
 
-def cpu_baseline(args):
+def cpu_baseline(args, iters=None):
     """The oracle as it stands, on a bounded sample of the workload: one direction of one sweep
-    per process (local assembly + factorisation + the lagged sweep), on one core and on all cores."""
+    per process (local assembly + factorisation + the lagged sweep), on one core and on all cores;
+    and the same for the 3D p = 2 family on a 12^3 twisted mesh.  iters = the GPU's source-iteration
+    counts to 1e-8 ({"2d": .., "3d_twist": .., "3d_s12": ..}) turn the all-core rates into
+    extrapolated oracle times to 1e-8 of the full workloads (stated as extrapolations)."""
     import multiprocessing as mp
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     single = OracleWorkers(1)
@@ -870,12 +880,32 @@ def cpu_baseline(args):
     dtp = pool.round()
     pool.close()
     E = pool.E
-    return {"value": E * P / dtp, "unit": "updates/s", "cores": P, "nproc": os.cpu_count(), "kind": "oracle",
-            "sample": f"{P} directions of one sweep of the same workload at once, one per process "
-                      f"({E * P} updates in {dtp:.1f} s): local assembly, LU and the lagged sweep, numpy/scipy FP64",
-            "single_core": {"value": E / dt1, "unit": "updates/s", "cores": 1,
-                            "sample": f"one direction ({E} updates) in {dt1:.1f} s"},
-            "start_method": mp.get_context("spawn").get_start_method()}
+    rate = E * P / dtp
+    out = {"value": rate, "unit": "updates/s", "cores": P, "nproc": os.cpu_count(), "kind": "oracle",
+           "sample": f"{P} directions of one sweep of the same workload at once, one per process "
+                     f"({E * P} updates in {dtp:.1f} s): local assembly, LU and the lagged sweep, numpy/scipy FP64",
+           "single_core": {"value": E / dt1, "unit": "updates/s", "cores": 1,
+                           "sample": f"one direction ({E} updates) in {dt1:.1f} s"},
+           "start_method": mp.get_context("spawn").get_start_method()}
+    # 3D p = 2 sample: one direction of a 12^3 twisted Q2 mesh per process
+    pool3 = OracleWorkers(P, workload="3d_twist_q2_p2_s8", n=12, n_dirs=80)
+    pool3.round()
+    dt3 = pool3.round()
+    pool3.close()
+    rate3 = pool3.E * P / dt3
+    out["3d_p2"] = {"value": rate3, "unit": "updates/s", "cores": P,
+                    "sample": f"{P} directions of one sweep of a 12^3 twisted Q2 p=2 mesh, one per process "
+                              f"({pool3.E * P} updates in {dt3:.1f} s)"}
+    if iters:
+        ext = {"note": "oracle all-core rate x the workload's updates per sweep x the GPU's iteration count"}
+        if iters.get("2d"):
+            ext["2d_128x128_p3_s8_s"] = 655360 * iters["2d"] / rate
+        if iters.get("3d_twist"):
+            ext["3d_32cubed_p2_s8_s"] = 2621440 * iters["3d_twist"] / rate3
+        if iters.get("3d_s12"):
+            ext["3d_48cubed_p2_s12_s"] = 18579456 * iters["3d_s12"] / rate3
+        out["extrapolated_time_to_1e-8"] = ext
+    return out
 
 
 def run_reference(args):
