@@ -434,6 +434,14 @@ class Discretization:
         """Face quadrature of face f of the elements in ctrl for the directions om (face_rule)."""
         return face_rule(ctrl, self.r, self.dim, f, om, self.nf, self.K)
 
+    def _face_basis(self, s0, s1):
+        """Face-node basis values at face coordinates (list of Nf arrays)."""
+        return face_basis(self.gll, self.dim, s0, s1)
+
+    def _orient(self, code, s0, s1):
+        """The neighbour's face coordinates of our face coordinates (orientation code)."""
+        return orient_coords(code, s0, s1)
+
     def _faces(self):
         mesh = self.prob.mesh
         self.iface = []      # (owner, f, nbr, f_nbr, orient owner->nbr)
@@ -476,13 +484,13 @@ class Discretization:
             s0, s1, w, g = self._face_rule(ctrl[iface[sel, 0]], f, om)
             ao = pos(-g) * w
             an = pos(g) * w
-            phi_o = face_basis(self.gll, dim, s0, s1)
+            phi_o = self._face_basis(s0, s1)
             codes = iface[sel, 4]
             phi_n = [np.zeros_like(s0) for _ in range(Nf)]
             for code in np.unique(codes):
                 cs = codes == code
-                t0, t1 = orient_coords(int(code), s0[cs], None if s1 is None else s1[cs])
-                vals = face_basis(self.gll, dim, t0, t1)
+                t0, t1 = self._orient(int(code), s0[cs], None if s1 is None else s1[cs])
+                vals = self._face_basis(t0, t1)
                 for i in range(Nf):
                     phi_n[i][cs] = vals[i]
             out_o[sel] = coupling_block(an, phi_o, phi_o)
@@ -497,7 +505,7 @@ class Discretization:
             if len(sel) == 0:
                 continue
             s0, s1, w, g = self._face_rule(ctrl[bface[sel, 0]], f, om)
-            phi = face_basis(self.gll, dim, s0, s1)
+            phi = self._face_basis(s0, s1)
             bout[sel] = coupling_block(pos(g) * w, phi, phi)
             bin_[sel] = coupling_block(pos(-g) * w, phi, phi)
         res.update(out_o=out_o, out_n=out_n, bar_o=bar_o, bar_n=bar_n, bout=bout, bin=bin_)

@@ -31,6 +31,8 @@ class Problem:
 
     @property
     def n_dofs(self):
+        if getattr(self.mesh, "simplex", False) and self.mesh.dim == 3:
+            return (self.p + 1) * (self.p + 2) * (self.p + 3) // 6
         if getattr(self.mesh, "simplex", False):
             return (self.p + 1) * (self.p + 2) // 2
         return (self.p + 1) ** self.mesh.dim
@@ -148,4 +150,19 @@ def triangle_problem(n, r, p, sn=4, amp=0.05, rotate_seed=None):
     ne = mesh.n_elem
     N = (p + 1) * (p + 2) // 2
     return Problem(name=f"tri_{n}_r{r}_p{p}_s{sn}", mesh=mesh, p=p, omega=om, w=w, sigma_t=np.ones(ne),
+                   sigma_s=0.5 * np.ones(ne), q=np.ones((ne, N)), sn_order=sn)
+
+
+def tet_problem(n, p, sn=4, rotate_seed=None):
+    """The unit cube as n^3 cubes of six straight tetrahedra each (6 n^3 elements, P_1 geometry),
+    DG order p (1 or 2: 4 or 10 unknowns), S_sn, sigma_t = 1, sigma_s = 0.5, q = 1.  rotate_seed
+    renumbers the tetrahedra's vertices by random even permutations."""
+    from .mesh import tet_mesh, rotate_tets
+    mesh = tet_mesh(n)
+    if rotate_seed is not None:
+        mesh = rotate_tets(mesh, rotate_seed)
+    om, w = level_symmetric(sn, 3)
+    ne = mesh.n_elem
+    N = (p + 1) * (p + 2) * (p + 3) // 6
+    return Problem(name=f"tet_{n}_p{p}_s{sn}", mesh=mesh, p=p, omega=om, w=w, sigma_t=np.ones(ne),
                    sigma_s=0.5 * np.ones(ne), q=np.ones((ne, N)), sn_order=sn)

@@ -475,3 +475,88 @@ def rotate_triangles(mesh, seed):
                 perm[3 + f * (r - 1) + j] = 3 + ((f + k) % 3) * (r - 1) + j
         new_nodes[e] = mesh.elem_nodes[e][perm]
     return _finish_tri(r, mesh.nodes, new_nodes, mesh.shape)
+
+
+# ---------------------------------------------------------------- tetrahedra (affine, P_1 geometry)
+#
+# Reference tetrahedron with vertices v0 = (0,0,0), v1 = (1,0,0), v2 = (0,1,0), v3 = (0,0,1).
+# Face f is opposite vertex f, with the vertex triple TET_FACES[f] ordered so that
+# (B - A) x (C - A) points out of the element.  A face's own coordinates are the barycentric
+# (s, t) of the triple: x = A + s (B - A) + t (C - A).  orient[e][f] = index k of the permutation
+# TRI_PERMS[k] that takes this face's triple to the neighbour's: the neighbour's vertex
+# TRI_PERMS[k][j] of its triple is our vertex j.
+
+TET_FACES = ((1, 2, 3), (0, 3, 2), (0, 1, 3), (0, 2, 1))
+TRI_PERMS = ((0, 1, 2), (1, 2, 0), (2, 0, 1), (0, 2, 1), (2, 1, 0), (1, 0, 2))
+
+
+def tet_mesh(n, disp=None):
+    """The unit cube as n^3 cubes, each cut into the six tetrahedra of the Kuhn triangulation
+    (vertex paths from the cube's corner (0,0,0) to (1,1,1) along the axes in every order;
+    conforming across cubes), vertices ordered for positive volume; P_1 geometry (the control
+    points are the vertices), optionally displaced by disp (an affine disp keeps it exact)."""
+    import itertools as it
+    c = n + 1
+    gid = lambda i, j, k: i + c * (j + c * k)
+    elems = []
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                for perm in it.permutations(range(3)):
+                    p = [0, 0, 0]
+                    verts = [gid(i, j, k)]
+                    for ax in perm:
+                        p[ax] += 1
+                        verts.append(gid(i + p[0], j + p[1], k + p[2]))
+                    elems.append(verts)
+    g = np.arange(c) / n
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    nodes = np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], axis=1)
+    if disp is not None:
+        nodes = nodes + disp(nodes.copy())
+    elems = np.array(elems, dtype=np.int64)
+    # positive volume: swap the last two vertices where the orientation is negative
+    P = nodes[elems]
+    vol = np.einsum("ei,ei->e", np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), P[:, 3] - P[:, 0])
+    neg = vol < 0
+    elems[neg, 2], elems[neg, 3] = elems[neg, 3].copy(), elems[neg, 2].copy()
+    return _finish_tet(nodes, elems, (n, n, n))
+
+
+def _finish_tet(nodes, elems, shape):
+    ne = elems.shape[0]
+    face_nbr = -np.ones((ne, 4), dtype=np.int64)
+    nbr_face = -np.ones((ne, 4), dtype=np.int32)
+    orient = np.zeros((ne, 4), dtype=np.int32)
+    table = {}
+    for e in range(ne):
+        for f in range(4):
+            tri = tuple(int(elems[e, v]) for v in TET_FACES[f])
+            table.setdefault(frozenset(tri), []).append((e, f, tri))
+    for lst in table.values():
+        if len(lst) == 1:
+            continue
+        if len(lst) != 2:
+            raise ValueError("non-conforming mesh: a face is shared by more than two elements")
+        for (a, fa, ta), (b, fb, tb) in ((lst[0], lst[1]), (lst[1], lst[0])):
+            code = next(k for k, pm in enumerate(TRI_PERMS) if all(tb[pm[j]] == ta[j] for j in range(3)))
+            face_nbr[a, fa], nbr_face[a, fa], orient[a, fa] = b, fb, code
+    ctrl = np.ascontiguousarray(nodes[elems])
+    return Mesh(dim=3, r=1, ctrl=ctrl, face_nbr=face_nbr, nbr_face=nbr_face, orient=orient,
+                nodes=nodes, elem_nodes=elems, shape=shape, simplex=True)
+
+
+TET_EDGES = ((0, 1), (1, 2), (2, 0), (0, 3), (1, 3), (2, 3))
+_EVEN_PERMS = tuple(p for p in itertools.permutations(range(4))
+                    if sum(1 for i in range(4) for j in range(i + 1, 4) if p[i] > p[j]) % 2 == 0)
+
+
+def rotate_tets(mesh, seed):
+    """Renumber every tetrahedron's vertices by a random even permutation (orientation kept);
+    the physical mesh is unchanged, local faces and orientation codes change."""
+    rng = np.random.default_rng(seed)
+    en = mesh.elem_nodes.copy()
+    for e in range(mesh.n_elem):
+        p = _EVEN_PERMS[rng.integers(len(_EVEN_PERMS))]
+        en[e] = mesh.elem_nodes[e][list(p)]
+    return _finish_tet(mesh.nodes, en, mesh.shape)

@@ -41,6 +41,12 @@ def _tri_lagrange_values(nodes, pts):
 
 def dg_node_positions(mesh, p):
     """[n_elem][N][dim] physical positions of the DG nodes."""
+    if getattr(mesh, "simplex", False) and mesh.dim == 3:
+        from .mesh import TET_EDGES
+        lam = [[1.0, 0.0, 0.0, 0.0], [0.0, 1.0, 0.0, 0.0], [0.0, 0.0, 1.0, 0.0], [0.0, 0.0, 0.0, 1.0]]
+        if p == 2:
+            lam += [[0.5 if k in e else 0.0 for k in range(4)] for e in TET_EDGES]
+        return np.einsum("nm,emd->end", np.array(lam), mesh.ctrl)
     if getattr(mesh, "simplex", False):
         from .mesh import tri_node_coords
         dg = tri_node_coords(p, _gll(p))
@@ -69,6 +75,14 @@ def boundary_faces(mesh):
 
 
 def _face_ids(mesh, p, f):
+    if getattr(mesh, "simplex", False) and mesh.dim == 3:
+        from .mesh import TET_FACES, TET_EDGES
+        a, b, c = TET_FACES[f]
+        ids = [a, b, c]
+        if p == 2:
+            ei = lambda x, y: next(k for k, e in enumerate(TET_EDGES) if set(e) == {x, y})
+            ids += [4 + ei(a, b), 4 + ei(b, c), 4 + ei(c, a)]
+        return ids
     if getattr(mesh, "simplex", False):
         from .mesh import tri_edge_nodes
         return tri_edge_nodes(p, f)
@@ -76,7 +90,9 @@ def _face_ids(mesh, p, f):
 
 
 def _n_face_nodes(mesh, p):
-    return p + 1 if getattr(mesh, "simplex", False) else (p + 1) ** (mesh.dim - 1)
+    if getattr(mesh, "simplex", False):
+        return (p + 1) * (p + 2) // 2 if mesh.dim == 3 else p + 1
+    return (p + 1) ** (mesh.dim - 1)
 
 
 def face_node_ids(p, dim, f):
