@@ -126,6 +126,19 @@ def test_source_iteration_equals_the_dense_solve_on_tets(p, weighting):
     assert np.allclose(R["phi"], phi, rtol=1e-11, atol=1e-13)
 
 
+@pytest.mark.parametrize("p", [1, 2])
+def test_lagged_source_iteration_equals_the_dense_solve_on_twisted_tets(p):
+    """A twisted column of straight tetrahedra has sweep cycles; the lagged iteration still
+    converges to the coupled solution."""
+    prob = tet_problem(2, p, twist=2.5, rotate_seed=3)
+    D = TetDiscretization(prob)
+    G = build_graph(D, "face")
+    assert len(G["removed"]) > 0
+    R = Sweeper(D, G).source_iterate(tol=1e-14, max_iter=400)
+    _psi, phi = global_solve(D)
+    assert np.allclose(R["phi"], phi, rtol=1e-11, atol=1e-13)
+
+
 def test_renumbered_tets_give_the_same_solution():
     out = []
     for seed in (None, 6):
