@@ -16,6 +16,7 @@ bounded sample of the same workload, on all host cores (one direction per proces
 """
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -76,9 +77,11 @@ def inv_alg_bytes(dim, p, simplex=False):
     """DRAM bytes one update of a stored-inverse form must move: its record, read once per sweep
     and far larger than L2 -- the inverse (N^2 entries) and one block per inflow face (2D: the
     folded N x Nf block, 3D: the Nf x Nf block; dim inflow faces on average for quadrilaterals
-    and hexahedra, 1.5 for triangles) -- plus the angular flux written (N) and about N entries of
-    traces and source; 8 bytes per entry."""
-    if simplex:
+    and hexahedra, 1.5 for triangles, 2 for tetrahedra) -- plus the angular flux written (N) and
+    about N entries of traces and source; 8 bytes per entry."""
+    if simplex and dim == 3:
+        N, Nf, faces = (p + 1) * (p + 2) * (p + 3) // 6, (p + 1) * (p + 2) // 2, 2.0
+    elif simplex:
         N, Nf, faces = (p + 1) * (p + 2) // 2, p + 1, 1.5
     else:
         N, Nf, faces = (p + 1) ** dim, (p + 1) ** (dim - 1), dim
@@ -185,15 +188,16 @@ KERNEL_SOURCES = ["paper_1810_11080_gb300/csrc/" + f for f in
                   ("sweep.cu", "sweep_inv.cu", "sweep_kernels.cuh", "sweep_body.cuh", "inverse_body.cuh",
                    "devmath.cuh", "common.h")]
 TRAFFIC = {
-    # one launch = one sweep: the whole launch captured (351.4 MB read + 154.7 MB written)
-    ("fp64", "dataflow"): {"bytes_per_launch": 506104320, "capture": "ncu --set full, sweep_flow_kernel<2,3,0>, "
-                           "first timed launch", "sources_sha256": "cad2ebc8eb59e2feb8334a6d551d51ef50523e11fa4d8035182663b5f82601c5"},
+    # one launch = one sweep: the whole launch captured (351.0 MB read + 153.5 MB written)
+    ("fp64", "dataflow"): {"bytes_per_launch": 504556032, "capture": "ncu --metrics dram__bytes_read.sum,"
+                           "dram__bytes_write.sum, sweep_flow_kernel<2,3,0>, first timed launch",
+                           "sources_sha256": "1caa067b110e74a954fd909489faacf6cfd90d4c91be52330e8c1b2bd749d13b"},
     # three mid-sweep level launches (5,000-5,080 pairs, 18.3-18.5 MB read, writes still in L2 at the
-    # end of each launch), scaled to the sweep's average level of 2,570 pairs at 3,652 bytes per pair
-    ("ds_inv", "levels"): {"bytes_per_launch": 9385640, "capture": "ncu --set full, el_level_kernel<TensorEl<2,3>,4>, "
-                           "levels 128-130 scaled per pair", "sources_sha256": "cad2ebc8eb59e2feb8334a6d551d51ef50523e11fa4d8035182663b5f82601c5"},
+    # end of each launch), scaled to the sweep's average level of 2,570 pairs at 3,653 bytes per pair
+    ("ds_inv", "levels"): {"bytes_per_launch": 9389197, "capture": "ncu --metrics dram__bytes_read.sum,"
+                           "dram__bytes_write.sum, el_level_kernel<TensorEl<2,3>,4>, levels 128-130 scaled per pair",
+                           "sources_sha256": "1caa067b110e74a954fd909489faacf6cfd90d4c91be52330e8c1b2bd749d13b"},
 }
-
 
 def kernel_sources_sha256():
     import hashlib
@@ -447,6 +451,8 @@ def run_gpu(args):
         out["straightening"] = run_straightening(g, torch, args)
     if not args.no_triangles:
         out["triangles"] = run_triangles(g, torch, args)
+    if not args.no_tets:
+        out["tetrahedra"] = run_tets(g, torch, args)
     if not args.no_cpu_baseline:
         iters = {"2d": tts["fp64"]["iters"],
                  "3d_twist": out.get("twisted_3d", {}).get("fp64", {}).get("iters"),
@@ -650,17 +656,32 @@ def run_triangles(g, torch, args):
     swept by the two stored-inverse forms; sweep rate, HBM fraction and time to a 1e-8 change
     (formation of the stored inverses included)."""
     import sn_inputs.configs as C
-    prob = C.triangle_problem(128, 3, 3, sn=8)
+    return run_simplex(g, torch, args, C.triangle_problem(128, 3, 3, sn=8),
+                       "32768 P3 triangles (128x128 cells), sine perturbation 0.05, P3 DG, S8 (40 dirs), "
+                       "sigma_t=1, sigma_s=0.5, q=1")
+
+
+def run_tets(g, torch, args):
+    """Straight-sided tetrahedra (Sec. 2): the unit cube as 32^3 cubes of six Kuhn tetrahedra
+    (196,608 elements), twisted about the vertical axis by pi/3 over its height, P2 DG (10
+    unknowns), S8 (80 directions), sigma_t = 1, sigma_s = 0.5, q = 1: 15,728,640 updates per
+    sweep, swept by the two stored-inverse forms as the triangles are."""
+    import sn_inputs.configs as C
+    return run_simplex(g, torch, args, C.tet_problem(32, 2, sn=8, twist=math.pi / 3),
+                       "196608 straight P2 tetrahedra (32^3 Kuhn-cut cubes), twist pi/3, S8 (80 dirs), "
+                       "sigma_t=1, sigma_s=0.5, q=1")
+
+
+def run_simplex(g, torch, args, prob, workload):
     stream = torch.cuda.Stream()
     ctx = g.setup_problem(prob, device=0, stream=stream.cuda_stream)
     t0 = time.perf_counter()
     gs = ctx.sn_build_graph("face", 10)
-    E, N = prob.mesh.n_elem, 10
+    E, N, dim = prob.mesh.n_elem, ctx._N, prob.mesh.dim
     ups = E * len(prob.w)
     pk, _ = peaks()
-    ib = inv_alg_bytes(2, 3, simplex=True)
-    out = {"workload": "32768 P3 triangles (128x128 cells), sine perturbation 0.05, P3 DG, S8 (40 dirs), "
-                       "sigma_t=1, sigma_s=0.5, q=1", "updates_per_sweep": int(ups),
+    ib = inv_alg_bytes(dim, prob.p, simplex=True)
+    out = {"workload": workload, "updates_per_sweep": int(ups),
            "graph_build_s": time.perf_counter() - t0, "removed_arcs": int(gs["n_removed"]),
            "levels": int(gs["max_level"] + 1), "mixed_faces": int(gs["n_mixed_faces"])}
     for name, prec in (("fp64_inv", g.SN_PREC_FP64_INV), ("ds_inv", g.SN_PREC_DS_INV)):
@@ -951,6 +972,7 @@ def main():
     ap.add_argument("--dsa-max-cg", type=int, default=100, help="CG iteration cap of one DSA solve")
     ap.add_argument("--no-dsa-thick", action="store_true", help="skip the optically thick DSA measurement")
     ap.add_argument("--no-triangles", action="store_true", help="skip the triangle-mesh measurement")
+    ap.add_argument("--no-tets", action="store_true", help="skip the tetrahedral-mesh measurement")
     ap.add_argument("--no-straightening", action="store_true",
                     help="skip the curved high-order vs straightened low-order comparison")
     ap.add_argument("--learned-n", type=int, default=48, help="mesh size n^3 of the learned-predictor measurement")

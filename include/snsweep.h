@@ -102,8 +102,9 @@ const char* sn_last_error(const sn_ctx* ctx);
 sn_status sn_set_mesh(sn_ctx* ctx, int dim, int64_t n_elem, int r, const double* ctrl,
                       const int64_t* face_nbr, const int32_t* nbr_face, const int32_t* orient);
 
-/* Triangle mesh [Sec. 2: simplicial elements, P_r geometry]: as sn_set_mesh with dim = 2 (only;
- * SN_EINVAL otherwise) and three faces per element.  Reference triangle {xi, eta >= 0,
+/* Simplex mesh [Sec. 2: simplicial elements]: triangles (dim = 2, P_r geometry) or straight-sided
+ * tetrahedra (dim = 3, r = 1 only; SN_EINVAL otherwise).
+ * Triangles: as sn_set_mesh with three faces per element.  Reference triangle {xi, eta >= 0,
  * xi + eta <= 1}, vertices v0 = (0,0), v1 = (1,0), v2 = (0,1), counterclockwise faces f0 = v0 v1,
  * f1 = v1 v2, f2 = v2 v0, each with the coordinate s in [0,1] from its first vertex to its second.
  *   ctrl      [n_elem][(r+1)(r+2)/2][2] control points in the node order v0, v1, v2, the r - 1
@@ -113,9 +114,21 @@ sn_status sn_set_mesh(sn_ctx* ctx, int dim, int64_t n_elem, int r, const double*
  * The DG basis is then P_p (sn_set_discretization, p = 1..3, (p+1)(p+2)/2 unknowns) on the same
  * node pattern with the face nodes at the Gauss-Lobatto-Legendre positions of order p; volume
  * integrals use the collapsed Gauss rule (xi = u, eta = v (1 - u)) with p + r points per
- * direction.  Triangle problems are swept by the stored-inverse forms (SN_PREC_FP64_INV,
- * SN_PREC_DS_INV); the other forms, diffusion acceleration, the flux predictor and batches
- * return SN_EINVAL. */
+ * direction.
+ * Tetrahedra: four faces per element.  Reference vertices v0 = (0,0,0), v1 = (1,0,0),
+ * v2 = (0,1,0), v3 = (0,0,1); face f is opposite vertex f with the vertex triples (v1 v2 v3),
+ * (v0 v3 v2), (v0 v1 v3), (v0 v2 v1) = (A, B, C), ordered so that (B - A) x (C - A) points out
+ * of the element, and face coordinates (s, t) the barycentrics of B and C.
+ *   ctrl      [n_elem][4][3] vertices (positive volume).
+ *   face_nbr, nbr_face, orient [n_elem][4]; orient k in 0..5: our face vertex j is the
+ *   neighbour's face vertex pi_k(j), pi = (0 1 2), (1 2 0), (2 0 1), (0 2 1), (2 1 0), (1 0 2).
+ * The DG basis is P_1 (4 unknowns: the vertices) or P_2 (10: the vertices, then the midpoints of
+ * the edges v0v1, v1v2, v2v0, v0v3, v1v3, v2v3); volume integrals use the collapsed Gauss rule
+ * (x = u, y = v (1 - u), z = w (1 - u)(1 - v)) with p + 2 points per direction, face integrals
+ * the collapsed triangle rule with p + 1.  A flat face is wholly inflow or wholly outflow for
+ * every direction, so no face is split.
+ * Simplex problems are swept by the stored-inverse forms (SN_PREC_FP64_INV, SN_PREC_DS_INV); the
+ * other forms, diffusion acceleration, the flux predictor and batches return SN_EINVAL. */
 sn_status sn_set_mesh_simplex(sn_ctx* ctx, int dim, int64_t n_elem, int r, const double* ctrl,
                               const int64_t* face_nbr, const int32_t* nbr_face, const int32_t* orient);
 

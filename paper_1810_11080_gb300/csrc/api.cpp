@@ -133,7 +133,7 @@ sn::DevProblem sn_ctx::dev() const {
   P.Nf = Nf;
   P.nv = tab.nv;
   P.nf = tab.nf;
-  P.K = (dim == 3) ? K : 1;
+  P.K = (dim == 3 && !simplex) ? K : 1;
   P.Q = tab.Q;
   P.Nv = tab.Nv;
   P.nfc = nfc;
@@ -243,14 +243,14 @@ sn_status set_mesh_impl(sn_ctx* c, int dim, int64_t n_elem, int r, const double*
                         const int32_t* nbr_face, const int32_t* orient, bool simplex) {
   if (!c) return SN_EINVAL;
   SN_REQ(c, dim == 2 || dim == 3, SN_EINVAL, "dim must be 2 or 3");
-  SN_REQ(c, !simplex || dim == 2, SN_EINVAL, "simplicial meshes: triangles (dim 2) only");
+  SN_REQ(c, !simplex || dim == 2 || r == 1, SN_EINVAL, "tetrahedra: straight-sided (geometry order r = 1) only");
   SN_REQ(c, r >= 1 && r <= MAX_R, SN_EINVAL, "geometry order r must be 1..3");
   SN_REQ(c, n_elem >= 1 && n_elem < (1LL << 31) / 8, SN_EINVAL, "n_elem out of range");
   SN_REQ(c, ctrl && face_nbr && nbr_face && orient, SN_EINVAL, "null mesh array");
   cudaSetDevice(c->device);
-  const int nfc = simplex ? 3 : 2 * dim;
+  const int nfc = simplex ? dim + 1 : 2 * dim;
   int64_t nv = 1;
-  if (simplex) nv = (int64_t)(r + 1) * (r + 2) / 2;
+  if (simplex) nv = dim == 2 ? (int64_t)(r + 1) * (r + 2) / 2 : 4;
   else
     for (int k = 0; k < dim; ++k) nv *= (r + 1);
   std::vector<double> hc(n_elem * nv * dim);
@@ -276,7 +276,7 @@ sn_status set_mesh_impl(sn_ctx* c, int dim, int64_t n_elem, int r, const double*
       SN_REQ(c, fn >= 0 && fn < nfc, SN_EMESH, "neighbour face out of range");
       SN_REQ(c, hn[nb * nfc + fn] == e && hf[nb * nfc + fn] == f, SN_EMESH, "neighbour relation not symmetric");
       int oc = ho[e * nfc + f];
-      SN_REQ(c, oc >= 0 && oc < (dim == 2 ? 2 : 8), SN_EINVAL, "orientation code out of range");
+      SN_REQ(c, oc >= 0 && oc < (dim == 2 ? 2 : (simplex ? 6 : 8)), SN_EINVAL, "orientation code out of range");
     }
   free_graph_state(c);
   c->dim = dim;
@@ -343,7 +343,7 @@ sn_status sn_set_discretization(sn_ctx* c, int p, int face_subdiv) {
   SN_REQ(c, p >= 1 && p <= MAX_P, SN_EINVAL, "DG order p must be 1..3");
   SN_REQ(c, c->dim == 2 || p <= 2, SN_EINVAL, "3D DG order p must be 1 or 2 ((p+1)^3 <= 32 unknowns per element)");
   SN_REQ(c, face_subdiv >= 1 && face_subdiv <= 4, SN_EINVAL, "face_subdiv must be 1..4");
-  if (c->dim == 3) {
+  if (c->dim == 3 && !c->simplex) {
     const int nf = p + c->r;
     SN_REQ(c, face_subdiv * face_subdiv * nf * nf <= 256, SN_EINVAL, "3D face rule too large (K^2 n_f^2 > 256)");
   }
@@ -352,7 +352,8 @@ sn_status sn_set_discretization(sn_ctx* c, int p, int face_subdiv) {
   c->p = p;
   c->K = face_subdiv;
   try {
-    if (c->simplex) build_tables_tri(c->tab, p, c->r);
+    if (c->simplex && c->dim == 3) build_tables_tet(c->tab, p);
+    else if (c->simplex) build_tables_tri(c->tab, p, c->r);
     else build_tables(c->tab, c->dim, p, c->r);
   } catch (const std::exception& ex) {
     set_err(c, ex.what());

@@ -42,6 +42,7 @@ double lagrange(const double* nodes, int n, int j, double x);
 double lagrange_deriv(const double* nodes, int n, int j, double x);
 void build_tables(Tables& T, int dim, int p, int r);
 void build_tables_tri(Tables& T, int p, int r);
+void build_tables_tet(Tables& T, int p);
 
 // Components and feedback arc sets of every direction's graph on the device (scc.cu).
 struct DeviceFasStats {
@@ -72,8 +73,8 @@ cudaError_t dsa_apply(const DevProblem& P, DsaState& D, const double* half, cons
 // Device-side view of a problem passed to kernels by value.
 struct DevProblem {
   int dim, r, p, N, Nf, nv, nf, K, Q, Nv, M;
-  int nfc;                   // faces per element: 2 dim (quadrilaterals, hexahedra) or 3 (triangles)
-  int simplex;               // 1: triangles with P_r geometry and P_p DG (see tables.cpp)
+  int nfc;                   // faces per element: 2 dim (quadrilaterals, hexahedra) or dim + 1 (simplices)
+  int simplex;               // 1: triangles (P_r geometry) or straight tetrahedra, P_p DG (see tables.cpp)
   int64_t E;
   int64_t n_bdr;
   const double* ctrl;        // [E][Nv][dim]
@@ -194,7 +195,7 @@ struct sn_ctx {
   int64_t launches = 0;
   // mesh (host copies)
   int dim = 0, r = 0;
-  bool simplex = false;            // triangles (sn_set_mesh_simplex)
+  bool simplex = false;            // triangles or tetrahedra (sn_set_mesh_simplex)
   int nfc = 0;                     // faces per element
   int64_t E = 0;
   std::vector<double> h_ctrl;

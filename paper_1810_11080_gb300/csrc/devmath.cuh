@@ -197,17 +197,112 @@ __device__ inline void face_basis_all(int dim, const double* gll, int np1, doubl
 
 namespace sn {
 
-// Scaled outward normal of face f of either element family at face coordinates (s0, s1).
+// ---- straight-sided tetrahedra (P_1 geometry, P_1 / P_2 DG).  Vertices v0..v3 of the reference
+// tetrahedron (0,0,0), (1,0,0), (0,1,0), (0,0,1); face f opposite vertex f with the vertex triple
+// tet_face_vert(f, 0..2) ordered so that (B - A) x (C - A) points outwards; face coordinates
+// (s, t) = the barycentrics of B and C.  DG nodes: vertices, then (p = 2) the midpoints of the
+// edges (0,1), (1,2), (2,0), (0,3), (1,3), (2,3); face nodes: A, B, C, then the AB, BC, CA
+// midpoints.  Orientation code k of a shared face: the neighbour's vertex tet_perm(k, j) of its
+// triple is our vertex j.
+__host__ __device__ constexpr int tet_face_vert(int f, int j) {
+  return f == 0 ? (j == 0 ? 1 : (j == 1 ? 2 : 3))
+       : f == 1 ? (j == 0 ? 0 : (j == 1 ? 3 : 2))
+       : f == 2 ? (j == 0 ? 0 : (j == 1 ? 1 : 3))
+                : (j == 0 ? 0 : (j == 1 ? 2 : 1));
+}
+__host__ __device__ constexpr int tet_perm(int k, int j) {
+  return k == 0 ? j : k == 1 ? (j + 1) % 3 : k == 2 ? (j + 2) % 3 : k == 3 ? (j == 0 ? 0 : 3 - j)
+       : k == 4 ? 2 - j : (j == 2 ? 2 : 1 - j);
+}
+__host__ __device__ constexpr int tet_edge_index(int a, int b) {
+  return (a + b == 1 && a * b == 0) ? 0 : (a + b == 3 && a * b == 2) ? 1 : (a + b == 2 && a * b == 0) ? 2
+       : (a + b == 3 && a * b == 0) ? 3 : (a + b == 4 && a * b == 3) ? 4 : 5;
+}
+// Volume node of face node j of face f (order p DG).
+__host__ __device__ constexpr int tet_face_node(int p, int f, int j) {
+  return j < 3 ? tet_face_vert(f, j)
+               : 4 + tet_edge_index(tet_face_vert(f, j - 3), tet_face_vert(f, (j - 2) % 3));
+}
+// Face node of the neighbour that sees our face node j (orientation code k): vertices permuted,
+// the midpoint of our face edge (j, j + 1) goes to the neighbour's edge (perm j, perm (j + 1)).
+__host__ __device__ constexpr int tet_face_edge(int a, int b) {
+  return ((a == 0 && b == 1) || (a == 1 && b == 0)) ? 0 : ((a == 1 && b == 2) || (a == 2 && b == 1)) ? 1 : 2;
+}
+__host__ __device__ constexpr int tet_nbr_face_node(int k, int j) {
+  return j < 3 ? tet_perm(k, j) : 3 + tet_face_edge(tet_perm(k, j - 3), tet_perm(k, (j - 2) % 3));
+}
+
+// Outward scaled normal (B - A) x (C - A) of face f: component c = u_a v_b - u_b v_a, a = c + 1,
+// b = c + 2 (mod 3); ctrl [4][3].
+__device__ inline void face_normal_tet(const double* ctrl, int f, double* nvec) {
+  const int A = tet_face_vert(f, 0), B = tet_face_vert(f, 1), C = tet_face_vert(f, 2);
+  double u[3], v[3];
+  for (int c = 0; c < 3; ++c) {
+    u[c] = ctrl[B * 3 + c] - ctrl[A * 3 + c];
+    v[c] = ctrl[C * 3 + c] - ctrl[A * 3 + c];
+  }
+  for (int c = 0; c < 3; ++c) {
+    const int a = (c + 1) % 3, b = (c + 2) % 3;
+    nvec[c] = u[a] * v[b] - u[b] * v[a];
+  }
+}
+
+// Face-node basis values at face coordinates (s, t): p = 1, (1 - s) - t, s, t; p = 2, m ((2 m) - 1)
+// at the vertices and (4 m_a) m_b at the edge midpoints.
+__device__ inline void face_basis_tet(int p, double s, double t, double* out) {
+  const double m[3] = {(1.0 - s) - t, s, t};
+  if (p == 1) {
+    for (int i = 0; i < 3; ++i) out[i] = m[i];
+    return;
+  }
+  for (int i = 0; i < 3; ++i) out[i] = m[i] * ((2.0 * m[i]) - 1.0);
+  out[3] = (4.0 * m[0]) * m[1];
+  out[4] = (4.0 * m[1]) * m[2];
+  out[5] = (4.0 * m[2]) * m[0];
+}
+
+// The neighbour's face coordinates of our (s, t): barycentrics permuted by orientation code k.
+__device__ inline void orient_tet(int k, double s, double t, double& s2, double& t2) {
+  const double m[3] = {(1.0 - s) - t, s, t};
+  double mp[3] = {0.0, 0.0, 0.0};
+  for (int j = 0; j < 3; ++j) mp[tet_perm(k, j)] = m[j];
+  s2 = mp[1];
+  t2 = mp[2];
+}
+
+// Scaled outward normal of face f of any element family at face coordinates (s0, s1).
 __device__ inline void face_normal_el(const DevProblem& P, const double* geo, const double* ctrl, int f, double s0,
                                       double s1, double* nvec) {
-  if (P.simplex) face_normal_tri(P.r, geo, ctrl, f, s0, nvec);
+  if (P.simplex && P.dim == 3) face_normal_tet(ctrl, f, nvec);
+  else if (P.simplex) face_normal_tri(P.r, geo, ctrl, f, s0, nvec);
   else face_normal(P.dim, P.r, geo, ctrl, f, s0, s1, nvec);
 }
 
 // Volume node index of face node i of face f (face nodes in face-coordinate order).
 __device__ inline int face_node_vol(const DevProblem& P, int f, int i) {
+  if (P.simplex && P.dim == 3) return tet_face_node(P.p, f, i);
   if (P.simplex) return tri_edge_node(P.p, f, i);
   return face_vol_index(P.dim, P.p, f, i % (P.p + 1), i / (P.p + 1));
+}
+
+// All face-node basis values at face coordinates, and one of them (any element family).
+__device__ inline void face_basis_el_all(const DevProblem& P, const double* gll, double s0, double s1, double* out) {
+  if (P.simplex && P.dim == 3) face_basis_tet(P.p, s0, s1, out);
+  else face_basis_all(P.dim, gll, P.p + 1, s0, s1, out);
+}
+__device__ inline double face_basis_el_one(const DevProblem& P, const double* gll, int i, double s0, double s1) {
+  if (P.simplex && P.dim == 3) {
+    double v[6];
+    face_basis_tet(P.p, s0, s1, v);
+    return v[i];
+  }
+  return face_basis(P.dim, gll, P.p + 1, i, s0, s1);
+}
+
+// The neighbour's face coordinates of ours (orientation code).
+__device__ inline void orient_map_el(const DevProblem& P, int code, double s0, double s1, double& t0, double& t1) {
+  if (P.simplex && P.dim == 3) orient_tet(code, s0, s1, t0, t1);
+  else orient_map(P.dim, code, s0, s1, t0, t1);
 }
 
 }  // namespace sn

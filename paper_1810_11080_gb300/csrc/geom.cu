@@ -87,8 +87,9 @@ __global__ void geometry_kernel(DevProblem P, double* __restrict__ elem, int* ba
   for (int t = threadIdx.x; t < P.nfc * Pf; t += blockDim.x) {
     const int f = t / Pf, q = t % Pf;
     const int qi = q % nf, qj = q / nf;
-    const double s0 = gt[qi], s1 = (DIM == 3) ? gt[qj] : 0.0;
-    const double w = (DIM == 3) ? gw[qi] * gw[qj] : gw[qi];
+    const bool tet = DIM == 3 && P.simplex;          // collapsed triangle rule on a flat face
+    const double s0 = gt[qi], s1 = (DIM == 3) ? (tet ? gt[qj] * (1.0 - gt[qi]) : gt[qj]) : 0.0;
+    const double w = (DIM == 3) ? (tet ? (gw[qi] * gw[qj]) * (1.0 - gt[qi]) : gw[qi] * gw[qj]) : gw[qi];
     double nv[3];
     face_normal_el(P, geo, sctrl, f, s0, s1, nv);
     for (int k = 0; k < DIM; ++k) wn[(f * Pf + q) * DIM + k] = w * nv[k];
@@ -102,8 +103,9 @@ __global__ void geometry_kernel(DevProblem P, double* __restrict__ elem, int* ba
     for (int k = 0; k < DIM; ++k) acc[k] = 0.0;
     for (int q = 0; q < Pf; ++q) {
       const int qi = q % nf, qj = q / nf;
-      const double s0 = gt[qi], s1 = (DIM == 3) ? gt[qj] : 0.0;
-      const double pp = face_basis(DIM, gll, np1, i, s0, s1) * face_basis(DIM, gll, np1, j, s0, s1);
+      const bool tet = DIM == 3 && P.simplex;
+      const double s0 = gt[qi], s1 = (DIM == 3) ? (tet ? gt[qj] * (1.0 - gt[qi]) : gt[qj]) : 0.0;
+      const double pp = face_basis_el_one(P, gll, i, s0, s1) * face_basis_el_one(P, gll, j, s0, s1);
       for (int k = 0; k < DIM; ++k) acc[k] += wn[(f * Pf + q) * DIM + k] * pp;
     }
     for (int k = 0; k < DIM; ++k) fnout[((size_t)(f * DIM + k) * Nf + i) * Nf + j] = acc[k];

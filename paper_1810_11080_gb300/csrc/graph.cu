@@ -197,6 +197,7 @@ __device__ inline void merge_breaks(int K, const double* roots, int nr, double* 
 }
 
 __device__ inline int face_npoints(const DevProblem& P) {
+  if (P.dim == 3 && P.simplex) return P.nf * P.nf;          // flat triangle faces: no split
   return (P.dim == 2) ? 3 * P.nf : P.K * P.K * P.nf * P.nf;
 }
 
@@ -362,7 +363,14 @@ __device__ inline PointData face_point(const DevProblem& P, const double* brk, i
   const double* wt = tabp(P, P.off_glf_w);
   const int nf = P.nf;
   PointData pd;
-  if (P.dim == 2) {
+  if (P.dim == 3 && P.simplex) {
+    // tetrahedron face: collapsed triangle rule, point i + nf j at (u_i, v_j (1 - u_i)), weight
+    // (w_i w_j) (1 - u_i); Omega . n is constant on the flat face, so there is nothing to split
+    const int i = q % nf, j = q / nf;
+    pd.s0 = t[i];
+    pd.s1 = t[j] * (1.0 - t[i]);
+    pd.w = (wt[i] * wt[j]) * (1.0 - t[i]);
+  } else if (P.dim == 2) {
     const int piece = q / nf, i = q % nf;
     const double lo = brk[piece], hi = brk[piece + 1];
     const double ln = hi - lo;
@@ -402,11 +410,11 @@ __device__ void fill_points_brk(const DevProblem& P, const double* ctrl, int f, 
     double* o = sp + q * stride;
     o[0] = (mg > 0.0 ? mg : 0.0) * pd.w;
     o[1] = (g > 0.0 ? g : 0.0) * pd.w;
-    face_basis_all(P.dim, gll, np1, pd.s0, pd.s1, o + 2);
+    face_basis_el_all(P, gll, pd.s0, pd.s1, o + 2);
     if (has_nbr) {
       double t0, t1;
-      orient_map(P.dim, code, pd.s0, pd.s1, t0, t1);
-      face_basis_all(P.dim, gll, np1, t0, t1, o + 2 + Nf);
+      orient_map_el(P, code, pd.s0, pd.s1, t0, t1);
+      face_basis_el_all(P, gll, t0, t1, o + 2 + Nf);
     }
   }
   __syncwarp();
@@ -439,10 +447,10 @@ __device__ void fill_cache(const DevProblem& P, const double* ctrl, int f, int c
     w[0] = pd.w;
     for (int c = 0; c < dim; ++c) w[1 + c] = nv[c];
     double* o = sp + q * stride;
-    face_basis_all(dim, gll, np1, pd.s0, pd.s1, o + 2);
+    face_basis_el_all(P, gll, pd.s0, pd.s1, o + 2);
     double t0, t1;
-    orient_map(dim, code, pd.s0, pd.s1, t0, t1);
-    face_basis_all(dim, gll, np1, t0, t1, o + 2 + Nf);
+    orient_map_el(P, code, pd.s0, pd.s1, t0, t1);
+    face_basis_el_all(P, gll, t0, t1, o + 2 + Nf);
   }
   __syncwarp();
 }
@@ -659,8 +667,9 @@ __global__ void weights_face_kernel(DevProblem P, const int32_t* __restrict__ if
   const R3Layout L = r3_layout(P.r, P.K, P.nf, Nf);
   const int Dg = L.Dg, nlines = P.K * P.nf;
   double* nE = fb + 2 * Nf * Nf;
-  double* nB = nE + (dim == 3 ? 2 * (Dg + 1) * 3 : 0);
-  double* r3 = nB + (dim == 3 ? nlines * (Dg + 1) * 3 : 0);
+  const bool r3on = dim == 3 && !P.simplex;
+  double* nB = nE + (r3on ? 2 * (Dg + 1) * 3 : 0);
+  double* r3 = nB + (r3on ? nlines * (Dg + 1) * 3 : 0);
   copy_ctrl(P, owner, ctrl, lane);
   const double* geo = tabp(P, P.off_geo);
   if (dim == 2 && lane < 3) {
@@ -669,7 +678,7 @@ __global__ void weights_face_kernel(DevProblem P, const int32_t* __restrict__ if
     nref[2 * lane] = nv[0];
     nref[2 * lane + 1] = nv[1];
   }
-  if (dim == 3) {
+  if (dim == 3 && !P.simplex) {
     const double* t = tabp(P, P.off_glf_t);
     for (int s = lane; s < 2 * (Dg + 1); s += 32)
       face_normal(3, P.r, geo, ctrl, f, (double)(s / (Dg + 1)), (double)(s % (Dg + 1)) / (double)Dg, nE + 3 * s);
@@ -688,6 +697,8 @@ __global__ void weights_face_kernel(DevProblem P, const int32_t* __restrict__ if
     if (dim == 2) {
       split_2d_cached(nref, om, brk);
       unsplit = brk[1] == 1.0 && brk[2] == 1.0;
+    } else if (P.simplex) {
+      unsplit = true;                    // tetrahedron faces are flat: Omega . n is constant
     } else {
       // no root on either edge and none along the composite rule's outer lines: the rule is the
       // cached composite rule
@@ -750,10 +761,10 @@ __global__ void weights_face_kernel(DevProblem P, const int32_t* __restrict__ if
 }
 
 static int weights_face_shm_per_warp(const DevProblem& P) {
-  const int np = (P.dim == 2) ? 3 * P.nf : P.K * P.K * P.nf * P.nf;
+  const int np = (P.dim == 2) ? 3 * P.nf : (P.simplex ? P.nf * P.nf : P.K * P.K * P.nf * P.nf);
   const int stride = 2 + 2 * P.Nf;
   int n = P.Nv * P.dim + 6 + np * stride + np * (1 + P.dim) + (P.dim == 2 ? np * stride : 0) + 2 * P.Nf * P.Nf;
-  if (P.dim == 3) {
+  if (P.dim == 3 && !P.simplex) {
     const R3Layout L = r3_layout(P.r, P.K, P.nf, P.Nf);
     n += 2 * (L.Dg + 1) * 3 + P.K * P.nf * (L.Dg + 1) * 3 + L.n;
   }
@@ -763,8 +774,8 @@ static int weights_face_shm_per_warp(const DevProblem& P) {
 // Per-warp workspace of the per-(face, direction) kernels: control points, then the 2D rule's
 // point rows or the 3D rule's workspace.
 static int weights_shm_per_warp(const DevProblem& P) {
-  if (P.dim == 3) return P.Nv * P.dim + r3_layout(P.r, P.K, P.nf, P.Nf).n;
-  const int np = 3 * P.nf;
+  if (P.dim == 3 && !P.simplex) return P.Nv * P.dim + r3_layout(P.r, P.K, P.nf, P.Nf).n;
+  const int np = (P.dim == 3) ? P.nf * P.nf : 3 * P.nf;
   return P.Nv * P.dim + np * (2 + 2 * P.Nf) + 2 * P.Nf * P.Nf;
 }
 
@@ -804,7 +815,7 @@ __global__ void bdr_modes_kernel(DevProblem P, const int32_t* __restrict__ bface
   copy_ctrl(P, e, ctrl, lane);
   double om[3] = {P.omega[d * 3 + 0], P.omega[d * 3 + 1], P.omega[d * 3 + 2]};
   double mi = 0.0, mo = 0.0;
-  if (P.dim == 3) {
+  if (P.dim == 3 && !P.simplex) {
     const R3Layout L = r3_layout(P.r, P.K, P.nf, Nf);
     const int spec[6] = {0, 2, 2, 1, 2, 2};            // inflow block, outflow block
     rule3_blocks(P, L, ctrl, f, 0, false, om, nullptr, sp, lane, 2, spec);
@@ -901,7 +912,7 @@ __global__ void bdr_modes3_kernel(DevProblem P, const int32_t* __restrict__ bfac
 cudaError_t launch_bdr_modes(const DevProblem& P, const int32_t* bface, int64_t n_bface, uint32_t* facecode,
                              cudaStream_t s) {
   if (n_bface == 0) return cudaSuccess;
-  if (P.dim == 3) {
+  if (P.dim == 3 && !P.simplex) {
     const R3Layout L = r3_layout(P.r, P.K, P.nf, P.Nf);
     const int np = P.K * P.K * P.nf * P.nf;
     const int spw = P.Nv * 3 + np * 3 + 2 * (L.Dg + 1) * 3 + P.K * P.nf * (L.Dg + 1) * 3 + L.n;
@@ -974,7 +985,7 @@ __global__ void mixed_blocks_kernel(DevProblem P, const int32_t* __restrict__ if
   double om[3] = {P.omega[d * 3 + 0], P.omega[d * 3 + 1], P.omega[d * 3 + 2]};
   const double* B0 = nullptr;       // 3D: the two blocks from the rule's workspace
   const double* B1 = nullptr;
-  if (P.dim == 3) {
+  if (P.dim == 3 && !P.simplex) {
     const R3Layout L = r3_layout(P.r, P.K, P.nf, Nf);
     const int spec[6] = {0, 2, 2, 1, 2 + Nf, 2 + Nf};  // owner's inflow block, neighbour's inflow block
     rule3_blocks(P, L, ctrl, f0, code, e1 >= 0, om, nullptr, sp, lane, 2, spec);

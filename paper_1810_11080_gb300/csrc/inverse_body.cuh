@@ -15,7 +15,8 @@
 // SN_PREC_FP64_INV keeps doubles and applies them in FP64; SN_PREC_DS_INV keeps (hi, lo) FP32
 // pairs of the same FP64 values and applies them in double-single arithmetic on the FP32 pipe.
 // The code is written for an element policy El (node counts, face count, face-node maps), so the
-// same bodies serve quadrilaterals / hexahedra (TensorEl) and triangles (TriEl).
+// same bodies serve quadrilaterals / hexahedra (TensorEl), triangles (TriEl) and tetrahedra
+// (TetEl).
 #pragma once
 
 namespace sn {
@@ -26,12 +27,14 @@ namespace sn {
 // vol_node(f, fj): volume index of face node fj; trace_node(fn, oc, fj): volume index, in the
 // neighbour's numbering, of our face node fj seen through the neighbour's face fn with
 // orientation code oc; SLOTS / slot(f): registers for inflow block rows kept across the wait (a
-// node lies on at most one face of each slot).
+// node lies on at most one face of each slot); AFFINE_TRACE: trace_node is c0 + ci I + cj J in
+// the face node's coordinates (I, J) (tensor elements).
 template <int DIM, int P_>
 struct TensorEl {
   using S = Shape<DIM, P_>;
   static constexpr int DIMV = DIM, N = S::N, NF = S::NF, W = S::W, SPW = S::SPW, NFC = 2 * DIM, NP1 = P_ + 1;
   static constexpr int SLOTS = DIM;
+  static constexpr bool AFFINE_TRACE = true;
   __host__ __device__ static constexpr int slot(int f) { return f >> 1; }
   __device__ static int face_node(int f, int i) { return on_face<DIM, P_>(f, i); }
   __host__ __device__ static constexpr int vol_node(int f, int fj) { return fvi<DIM, P_>(f, fj); }
@@ -57,6 +60,7 @@ struct TriEl {
   static constexpr int DIMV = 2, N = (P_ + 1) * (P_ + 2) / 2, NF = P_ + 1, NP1 = P_ + 1;
   static constexpr int W = N <= 4 ? 4 : (N <= 8 ? 8 : (N <= 16 ? 16 : 32)), SPW = 32 / W, NFC = 3;
   static constexpr int SLOTS = 3;
+  static constexpr bool AFFINE_TRACE = false;
   __host__ __device__ static constexpr int slot(int f) { return f; }
   __device__ static int face_node(int f, int i) {
     int out = -1;
@@ -67,6 +71,32 @@ struct TriEl {
   }
   __host__ __device__ static constexpr int vol_node(int f, int fj) { return tri_edge_node(P_, f, fj); }
   __device__ static int trace_node(int fn, int oc, int fj) { return tri_edge_node(P_, fn, (oc & 1) ? P_ - fj : fj); }
+  __device__ static void trace_nodes(int fn, int oc, int (&t)[NF]) {
+#pragma unroll
+    for (int fj = 0; fj < NF; ++fj) t[fj] = trace_node(fn, oc, fj);
+  }
+};
+
+// Straight-sided tetrahedra, P_1 / P_2 DG: face f opposite vertex f, face nodes the face's three
+// vertices then (P_2) its edge midpoints (tet_face_node); the neighbour sees our face node fj as
+// its face node tet_nbr_face_node(oc, fj).  A flat face is wholly inflow or wholly outflow, so
+// no face is ever mixed and one slot per face costs nothing.
+template <int P_>
+struct TetEl {
+  static constexpr int DIMV = 3, N = P_ == 1 ? 4 : 10, NF = P_ == 1 ? 3 : 6, NP1 = P_ + 1;
+  static constexpr int W = N <= 4 ? 4 : 16, SPW = 32 / W, NFC = 4;
+  static constexpr int SLOTS = 4;
+  static constexpr bool AFFINE_TRACE = false;
+  __host__ __device__ static constexpr int slot(int f) { return f; }
+  __device__ static int face_node(int f, int i) {
+    int out = -1;
+#pragma unroll
+    for (int j = 0; j < NF; ++j)
+      if (tet_face_node(P_, f, j) == i) out = j;
+    return out;
+  }
+  __host__ __device__ static constexpr int vol_node(int f, int fj) { return tet_face_node(P_, f, fj); }
+  __device__ static int trace_node(int fn, int oc, int fj) { return tet_face_node(P_, fn, tet_nbr_face_node(oc, fj)); }
   __device__ static void trace_nodes(int fn, int oc, int (&t)[NF]) {
 #pragma unroll
     for (int fj = 0; fj < NF; ++fj) t[fj] = trace_node(fn, oc, fj);
@@ -452,16 +482,20 @@ __device__ __forceinline__ void bodydsinv_blocks(const DevProblem& Pb, const Swe
       }
       if (nb >= 0) {                     // upwind neighbour's (hi, lo) split of the trace
         const bool lag = face_lagged(code, f);
-        // the blocks path serves the tensor elements (3D): the trace index is affine in the face
-        // node, c0 + ci I + cj J, with three registers instead of a table of NF
-        int c0, ci, cj;
-        trace_affine<DIM, El::NP1 - 1>(fov[f] & 0xff, fov[f] >> 8, c0, ci, cj);
+        // hexahedra: the trace index is affine in the face node, c0 + ci I + cj J, with three
+        // registers instead of a table of NF; tetrahedra: the table
+        int c0 = 0, ci = 0, cj = 0;
+        int tix[El::AFFINE_TRACE ? 1 : NF];
+        if constexpr (El::AFFINE_TRACE) trace_affine<DIM, El::NP1 - 1>(fov[f] & 0xff, fov[f] >> 8, c0, ci, cj);
+        else El::trace_nodes(fov[f] & 0xff, fov[f] >> 8, tix);
         const int64_t base = ((int64_t)d * E + nb) * N + c0;
         const float* ph_ = (lag ? sa.psi_old_h : sa.psi_new_h) + base;
         const float* pl_ = (lag ? sa.psi_old_l : sa.psi_new_l) + base;
 #pragma unroll
         for (int fj = 0; fj < NF; ++fj) {
-          const int o = ci * (fj % El::NP1) + cj * (fj / El::NP1);
+          int o;
+          if constexpr (El::AFFINE_TRACE) o = ci * (fj % El::NP1) + cj * (fj / El::NP1);
+          else o = tix[fj];
           float th, tl, qh, ql;
           if (!lag && DF) {
             th = __ldcg(ph_ + o);

@@ -114,9 +114,15 @@ static cudaError_t flow_el(const DevProblem& P, const SweepArgs& sa, const int32
   return cudaGetLastError();
 }
 
-// Element policy of the problem: triangles (P_p, p = 1..3) or tensor elements (dim, p).
+// Element policy of the problem: triangles (P_p, p = 1..3), tetrahedra (p = 1, 2) or tensor
+// elements (dim, p).
 #define SN_DISPATCH_EL(FN, ...)                                                   \
   do {                                                                           \
+    if (P.simplex && P.dim == 3) {                                               \
+      if (P.p == 1) return FN<TetEl<1>>(__VA_ARGS__);                            \
+      if (P.p == 2) return FN<TetEl<2>>(__VA_ARGS__);                            \
+      return cudaErrorInvalidValue;                                              \
+    }                                                                            \
     if (P.simplex) {                                                             \
       if (P.p == 1) return FN<TriEl<1>>(__VA_ARGS__);                            \
       if (P.p == 2) return FN<TriEl<2>>(__VA_ARGS__);                            \

@@ -289,4 +289,80 @@ void build_tables_tri(Tables& T, int p, int r) {
     }
 }
 
+// ------------------------------------------------------------------ tetrahedra
+// Straight-sided tetrahedra (P_1 geometry) with P_1 / P_2 DG bases in closed form (barycentrics
+// l0 = ((1 - x) - y) - z, l1 = x, l2 = y, l3 = z; P_2: l ((2 l) - 1) at the vertices, (4 l_a) l_b at
+// the edge midpoints (0,1), (1,2), (2,0), (0,3), (1,3), (2,3)), the same operation order as the
+// reference formulas so that the mass matrices of the sigma-inverse weights agree bit for bit.
+// Volume rule: collapsed Gauss, x = u, y = v (1 - u), z = (w (1 - u)) (1 - v), weight
+// ((((w_i w_j) w_k) (1 - u)) (1 - u)) (1 - v), n_v = p + 2 points per direction, q = i + n (j + n k);
+// faces: the collapsed triangle rule with n_f = p + 1 points per direction.
+namespace {
+
+void tet_eval(int p, double x, double y, double z, double* v, double (*g)[3]) {
+  const double l[4] = {((1.0 - x) - y) - z, x, y, z};
+  const double gl[4][3] = {{-1.0, -1.0, -1.0}, {1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}};
+  const int E[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}};
+  if (p == 1) {
+    for (int i = 0; i < 4; ++i) {
+      v[i] = l[i];
+      for (int k = 0; k < 3; ++k) g[i][k] = gl[i][k] * 1.0;
+    }
+    return;
+  }
+  for (int i = 0; i < 4; ++i) {
+    v[i] = l[i] * ((2.0 * l[i]) - 1.0);
+    for (int k = 0; k < 3; ++k) g[i][k] = ((4.0 * l[i]) - 1.0) * gl[i][k];
+  }
+  for (int m = 0; m < 6; ++m) {
+    const int a = E[m][0], b = E[m][1];
+    v[4 + m] = (4.0 * l[a]) * l[b];
+    for (int k = 0; k < 3; ++k) g[4 + m][k] = 4.0 * (l[b] * gl[a][k] + l[a] * gl[b][k]);
+  }
+}
+
+}  // namespace
+
+void build_tables_tet(Tables& T, int p) {
+  if (p < 1 || p > 2) throw std::invalid_argument("tetrahedra: DG order p must be 1 or 2");
+  T.dim = 3;
+  T.p = p;
+  T.r = 1;
+  T.nv = p + 2;
+  T.nf = p + 1;
+  T.N = p == 1 ? 4 : 10;
+  T.Nf = p == 1 ? 3 : 6;
+  T.Nv = 4;
+  T.Q = T.nv * T.nv * T.nv;
+  gauss_legendre(T.nv, T.glv_t, T.glv_w);
+  gauss_legendre(T.nf, T.glf_t, T.glf_w);
+  gll_nodes(p, T.gll);
+  T.geo = {0.0, 1.0};
+  T.wq.assign(T.Q, 0.0);
+  T.B.assign((size_t)T.Q * T.N, 0.0);
+  T.dB.assign((size_t)T.Q * T.N * 3, 0.0);
+  T.dV.assign((size_t)T.Q * 4 * 3, 0.0);
+  T.V.assign((size_t)T.Q * 4, 0.0);
+  const int n = T.nv;
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        const int q = i + n * (j + n * k);
+        const double u = T.glv_t[i], v = T.glv_t[j], w = T.glv_t[k];
+        const double x = u, y = v * (1.0 - u), z = (w * (1.0 - u)) * (1.0 - v);
+        T.wq[q] = ((((T.glv_w[i] * T.glv_w[j]) * T.glv_w[k]) * (1.0 - u)) * (1.0 - u)) * (1.0 - v);
+        double bv[10], bg[10][3];
+        tet_eval(p, x, y, z, bv, bg);
+        for (int m = 0; m < T.N; ++m) {
+          T.B[(size_t)q * T.N + m] = bv[m];
+          for (int c = 0; c < 3; ++c) T.dB[((size_t)q * T.N + m) * 3 + c] = bg[m][c];
+        }
+        tet_eval(1, x, y, z, bv, bg);
+        for (int m = 0; m < 4; ++m) {
+          T.V[(size_t)q * 4 + m] = bv[m];
+          for (int c = 0; c < 3; ++c) T.dV[((size_t)q * 4 + m) * 3 + c] = bg[m][c];
+        }
+      }
+}
+
 }  // namespace sn

@@ -14,7 +14,10 @@ def setup_problem(prob, device=0, stream=None, face_subdiv=2, ctx=None):
          np.ascontiguousarray(m.face_nbr, dtype=np.int64), np.ascontiguousarray(m.nbr_face, dtype=np.int32),
          np.ascontiguousarray(m.orient, dtype=np.int32))
     ctx.sn_set_discretization(prob.p, face_subdiv)
-    ctx._N = (prob.p + 1) * (prob.p + 2) // 2 if simplex else (prob.p + 1) ** m.dim
+    if simplex:
+        ctx._N = (prob.p + 1) * (prob.p + 2) // 2 if m.dim == 2 else (prob.p + 1) * (prob.p + 2) * (prob.p + 3) // 6
+    else:
+        ctx._N = (prob.p + 1) ** m.dim
     ctx.sn_set_quadrature(np.ascontiguousarray(prob.omega, dtype=np.float64),
                           np.ascontiguousarray(prob.w, dtype=np.float64))
     arr = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)

@@ -8,6 +8,9 @@ from oracle.sweep import Sweeper
 
 
 def oracle_disc(prob):
+    if getattr(prob.mesh, "simplex", False) and prob.mesh.dim == 3:
+        from oracle.simplex3 import TetDiscretization
+        return TetDiscretization(prob)
     if getattr(prob.mesh, "simplex", False):
         from oracle.simplex import SimplexDiscretization
         return SimplexDiscretization(prob)
