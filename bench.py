@@ -188,15 +188,15 @@ KERNEL_SOURCES = ["paper_1810_11080_gb300/csrc/" + f for f in
                   ("sweep.cu", "sweep_inv.cu", "sweep_kernels.cuh", "sweep_body.cuh", "inverse_body.cuh",
                    "devmath.cuh", "common.h")]
 TRAFFIC = {
-    # one launch = one sweep: the whole launch captured (351.0 MB read + 153.5 MB written)
-    ("fp64", "dataflow"): {"bytes_per_launch": 504556032, "capture": "ncu --metrics dram__bytes_read.sum,"
+    # one launch = one sweep: the whole launch captured (351.7 MB read + 153.7 MB written)
+    ("fp64", "dataflow"): {"bytes_per_launch": 505401856, "capture": "ncu --metrics dram__bytes_read.sum,"
                            "dram__bytes_write.sum, sweep_flow_kernel<2,3,0>, first timed launch",
-                           "sources_sha256": "1caa067b110e74a954fd909489faacf6cfd90d4c91be52330e8c1b2bd749d13b"},
+                           "sources_sha256": "a99cfce41db0ee1b51e1e0d181ee4ac18d07fdd21f5ef51fb9b414ab79756f24"},
     # three mid-sweep level launches (5,000-5,080 pairs, 18.3-18.5 MB read, writes still in L2 at the
     # end of each launch), scaled to the sweep's average level of 2,570 pairs at 3,653 bytes per pair
-    ("ds_inv", "levels"): {"bytes_per_launch": 9389197, "capture": "ncu --metrics dram__bytes_read.sum,"
+    ("ds_inv", "levels"): {"bytes_per_launch": 9389154, "capture": "ncu --metrics dram__bytes_read.sum,"
                            "dram__bytes_write.sum, el_level_kernel<TensorEl<2,3>,4>, levels 128-130 scaled per pair",
-                           "sources_sha256": "1caa067b110e74a954fd909489faacf6cfd90d4c91be52330e8c1b2bd749d13b"},
+                           "sources_sha256": "a99cfce41db0ee1b51e1e0d181ee4ac18d07fdd21f5ef51fb9b414ab79756f24"},
 }
 
 def kernel_sources_sha256():
@@ -225,6 +225,9 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
+    if args.quick and args.quick_simplex:
+        leg = run_triangles if args.quick_simplex == "triangles" else run_tets
+        return {"metric": METRIC, "quick": True, "leg": args.quick_simplex, "result": leg(g, torch, args)}
     if args.quick and args.quick_workload:
         import sn_inputs as si
         prob = si.make_config(args.quick_workload)
@@ -656,8 +659,9 @@ def run_triangles(g, torch, args):
     swept by the two stored-inverse forms; sweep rate, HBM fraction and time to a 1e-8 change
     (formation of the stored inverses included)."""
     import sn_inputs.configs as C
-    return run_simplex(g, torch, args, C.triangle_problem(128, 3, 3, sn=8),
-                       "32768 P3 triangles (128x128 cells), sine perturbation 0.05, P3 DG, S8 (40 dirs), "
+    n = getattr(args, "simplex_n", None) or 128
+    return run_simplex(g, torch, args, C.triangle_problem(n, 3, 3, sn=8),
+                       f"{2 * n * n} P3 triangles ({n}x{n} cells), sine perturbation 0.05, P3 DG, S8 (40 dirs), "
                        "sigma_t=1, sigma_s=0.5, q=1")
 
 
@@ -667,8 +671,9 @@ def run_tets(g, torch, args):
     unknowns), S8 (80 directions), sigma_t = 1, sigma_s = 0.5, q = 1: 15,728,640 updates per
     sweep, swept by the two stored-inverse forms as the triangles are."""
     import sn_inputs.configs as C
-    return run_simplex(g, torch, args, C.tet_problem(32, 2, sn=8, twist=math.pi / 3),
-                       "196608 straight P2 tetrahedra (32^3 Kuhn-cut cubes), twist pi/3, S8 (80 dirs), "
+    n = getattr(args, "simplex_n", None) or 32
+    return run_simplex(g, torch, args, C.tet_problem(n, 2, sn=8, twist=math.pi / 3),
+                       f"{6 * n ** 3} straight P2 tetrahedra ({n}^3 Kuhn-cut cubes), twist pi/3, S8 (80 dirs), "
                        "sigma_t=1, sigma_s=0.5, q=1")
 
 
@@ -684,8 +689,14 @@ def run_simplex(g, torch, args, prob, workload):
     out = {"workload": workload, "updates_per_sweep": int(ups),
            "graph_build_s": time.perf_counter() - t0, "removed_arcs": int(gs["n_removed"]),
            "levels": int(gs["max_level"] + 1), "mixed_faces": int(gs["n_mixed_faces"])}
+    launch = getattr(args, "launch", "auto")
     for name, prec in (("fp64_inv", g.SN_PREC_FP64_INV), ("ds_inv", g.SN_PREC_DS_INV)):
-        mode, bps = ctx.sn_autotune(prec)
+        if launch == "auto":
+            mode, bps = ctx.sn_autotune(prec)
+        else:
+            mode, bps = (g.SN_LAUNCH_DATAFLOW if launch == "dataflow" else g.SN_LAUNCH_LEVELS), 0
+            ctx.sn_set_launch(mode, bps)
+            ctx.sn_si_begin(None)
         for _ in range(args.warmup):
             ctx.sn_si_step(prec)
         tot = 0.0
@@ -987,6 +998,10 @@ def main():
     ap.add_argument("--quick-workload", default=None,
                     choices=["2d_sine_q2_p1_s4", "2d_smooth_q3_p3_s8", "3d_twist_q2_p2_s8", "3d_smooth_q2_p2_s12"],
                     help="with --quick: time this configuration instead of the default workload")
+    ap.add_argument("--quick-simplex", default=None, choices=["triangles", "tetrahedra"],
+                    help="with --quick: run only this simplex-mesh measurement (for profiler captures)")
+    ap.add_argument("--simplex-n", type=int, default=None,
+                    help="cells per side of the simplex-mesh measurements (default 128 triangles, 32 tetrahedra)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -80,7 +80,30 @@ struct TriEl {
 // Straight-sided tetrahedra, P_1 / P_2 DG: face f opposite vertex f, face nodes the face's three
 // vertices then (P_2) its edge midpoints (tet_face_node); the neighbour sees our face node fj as
 // its face node tet_nbr_face_node(oc, fj).  A flat face is wholly inflow or wholly outflow, so
-// no face is ever mixed and one slot per face costs nothing.
+// no face is ever mixed and one slot per face costs nothing.  The node maps are evaluated at
+// compile time into 4-bit fields: face_node(f, .) of a face f (a constant at every call site)
+// is one 64-bit immediate, and the trace indices of a neighbour face (fn, oc), known only at
+// run time, are one word of a 24-entry constant table -- evaluating the maps' nested selections
+// per lane and face cost several hundred instructions per pair.
+template <int P_>
+struct TetTraceWords {
+  uint32_t w[24];                      // [fn * 6 + oc], nibble fj = the trace's volume node
+};
+template <int P_>
+__host__ __device__ constexpr TetTraceWords<P_> tet_trace_words() {
+  TetTraceWords<P_> t{};
+  for (int fn = 0; fn < 4; ++fn)
+    for (int oc = 0; oc < 6; ++oc) {
+      uint32_t w = 0;
+      for (int fj = 0; fj < (P_ == 1 ? 3 : 6); ++fj)
+        w |= (uint32_t)tet_face_node(P_, fn, tet_nbr_face_node(oc, fj)) << (4 * fj);
+      t.w[fn * 6 + oc] = w;
+    }
+  return t;
+}
+static __constant__ TetTraceWords<1> c_tet_trace1 = tet_trace_words<1>();
+static __constant__ TetTraceWords<2> c_tet_trace2 = tet_trace_words<2>();
+
 template <int P_>
 struct TetEl {
   static constexpr int DIMV = 3, N = P_ == 1 ? 4 : 10, NF = P_ == 1 ? 3 : 6, NP1 = P_ + 1;
@@ -88,18 +111,29 @@ struct TetEl {
   static constexpr int SLOTS = 4;
   static constexpr bool AFFINE_TRACE = false;
   __host__ __device__ static constexpr int slot(int f) { return f; }
+  // nibble i: the face-node index of volume node i on face f, 15 if i is not on f
+  __host__ __device__ static constexpr uint64_t face_node_word(int f) {
+    uint64_t w = ~0ull;
+    for (int j = 0; j < NF; ++j) {
+      const int i = tet_face_node(P_, f, j);
+      w = (w & ~(15ull << (4 * i))) | ((uint64_t)j << (4 * i));
+    }
+    return w;
+  }
   __device__ static int face_node(int f, int i) {
-    int out = -1;
-#pragma unroll
-    for (int j = 0; j < NF; ++j)
-      if (tet_face_node(P_, f, j) == i) out = j;
-    return out;
+    const int v = (int)((face_node_word(f) >> (4 * (i & 15))) & 15ull);
+    return v == 15 ? -1 : v;
   }
   __host__ __device__ static constexpr int vol_node(int f, int fj) { return tet_face_node(P_, f, fj); }
-  __device__ static int trace_node(int fn, int oc, int fj) { return tet_face_node(P_, fn, tet_nbr_face_node(oc, fj)); }
+  __device__ static uint32_t trace_word(int fn, int oc) {
+    if constexpr (P_ == 1) return c_tet_trace1.w[fn * 6 + oc];
+    else return c_tet_trace2.w[fn * 6 + oc];
+  }
+  __device__ static int trace_node(int fn, int oc, int fj) { return (int)((trace_word(fn, oc) >> (4 * fj)) & 15u); }
   __device__ static void trace_nodes(int fn, int oc, int (&t)[NF]) {
+    const uint32_t w = trace_word(fn, oc);
 #pragma unroll
-    for (int fj = 0; fj < NF; ++fj) t[fj] = trace_node(fn, oc, fj);
+    for (int fj = 0; fj < NF; ++fj) t[fj] = (int)((w >> (4 * fj)) & 15u);
   }
 };
 
@@ -484,8 +518,9 @@ __device__ __forceinline__ void bodydsinv_blocks(const DevProblem& Pb, const Swe
         const bool lag = face_lagged(code, f);
         // hexahedra: the trace index is affine in the face node, c0 + ci I + cj J, with three
         // registers instead of a table of NF; tetrahedra: the table
-        int c0 = 0, ci = 0, cj = 0;
-        int tix[El::AFFINE_TRACE ? 1 : NF];
+        int c0 = 0;
+        [[maybe_unused]] int ci = 0, cj = 0;
+        [[maybe_unused]] int tix[El::AFFINE_TRACE ? 1 : NF];
         if constexpr (El::AFFINE_TRACE) trace_affine<DIM, El::NP1 - 1>(fov[f] & 0xff, fov[f] >> 8, c0, ci, cj);
         else El::trace_nodes(fov[f] & 0xff, fov[f] >> 8, tix);
         const int64_t base = ((int64_t)d * E + nb) * N + c0;
