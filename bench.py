@@ -690,7 +690,10 @@ def run_simplex(g, torch, args, prob, workload):
            "graph_build_s": time.perf_counter() - t0, "removed_arcs": int(gs["n_removed"]),
            "levels": int(gs["max_level"] + 1), "mixed_faces": int(gs["n_mixed_faces"])}
     launch = getattr(args, "launch", "auto")
-    for name, prec in (("fp64_inv", g.SN_PREC_FP64_INV), ("ds_inv", g.SN_PREC_DS_INV)):
+    forms = (("fp64_inv", g.SN_PREC_FP64_INV), ("ds_inv", g.SN_PREC_DS_INV))
+    if getattr(args, "quick", False) and getattr(args, "quick_forms", None):
+        forms = tuple(f for f in forms if f[0] in args.quick_forms.split(","))
+    for name, prec in forms:
         if launch == "auto":
             mode, bps = ctx.sn_autotune(prec)
         else:
@@ -994,7 +997,8 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no e2e, time-to-tolerance or CPU legs): for profiler launch lists")
     ap.add_argument("--quick-forms", default=None,
-                    help="with --quick: comma-separated forms to time (fp64, mixed, mixed_ds; default all)")
+                    help="with --quick: comma-separated forms to time (fp64, mixed, mixed_ds, fp64_inv, ds_inv; "
+                         "default all)")
     ap.add_argument("--quick-workload", default=None,
                     choices=["2d_sine_q2_p1_s4", "2d_smooth_q3_p3_s8", "3d_twist_q2_p2_s8", "3d_smooth_q2_p2_s12"],
                     help="with --quick: time this configuration instead of the default workload")
