@@ -132,10 +132,13 @@ sn_status sn_set_mesh(sn_ctx* ctx, int dim, int64_t n_elem, int r, const double*
 sn_status sn_set_mesh_simplex(sn_ctx* ctx, int dim, int64_t n_elem, int r, const double* ctrl,
                               const int64_t* face_nbr, const int32_t* nbr_face, const int32_t* orient);
 
-/* DG order p: 1..3 in 2D, 1..2 in 3D (N = (p+1)^dim <= 32 unknowns per element) and, for 3D, the number K of
- * sub-squares per face axis of the composite face rule (K >= 1; ignored in 2D).
+/* DG order p: 1..3 in 2D, 1..2 in 3D (N = (p+1)^dim <= 32 unknowns per element) and, for hexahedra,
+ * the number K of sub-squares per face axis of the composite face rule (1..4; ignored in 2D and for
+ * tetrahedra, whose flat faces need no composite rule).
  * Quadrature: volume n_v = p + ceil(dim r / 2) Gauss-Legendre points per axis, faces
- * n_f = p + r; 2D faces are split at the sign changes of Omega.n [Sec. 2, last paragraph]. */
+ * n_f = p + r; 2D faces are split at the sign changes of Omega.n [Sec. 2, last paragraph].
+ * Simplex meshes use the collapsed rules of sn_set_mesh_simplex.
+ * Errors: SN_ESTATE before sn_set_mesh; SN_EINVAL for p or K out of range. */
 sn_status sn_set_discretization(sn_ctx* ctx, int p, int face_subdiv);
 
 /* Angular quadrature {(w_d, Omega_d)} [Sec. 2, after eq. 2]: omega [n_dir][3] unit vectors
