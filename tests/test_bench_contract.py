@@ -56,3 +56,17 @@ def test_roofline_work_per_update_is_the_methods():
     assert w["flops"] == 5800.0 and w["bytes"] == 350.0
     assert bench.alg_work(3, 2)["flops"] == 35000.0
     assert bench.ds_fp32_issued_flops_per_update(2, 3, 2) > 2 * w["flops"]
+
+
+def test_stored_inverse_bytes_per_update():
+    """8 (N^2 + F blk + 2N) bytes per update: the inverse, F inflow blocks (2D folded N x Nf,
+    3D Nf x Nf), the flux written and about N entries of traces and source.  F is the average
+    number of inflow faces: dim for quadrilaterals and hexahedra; for a flat-faced simplex the
+    scaled normals sum to zero, so over directions half its faces are inflow (1.5 of 3, 2 of 4)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.inv_alg_bytes(2, 3) == 8 * (16 * 16 + 2 * 16 * 4 + 2 * 16) == 3328
+    assert bench.inv_alg_bytes(3, 2) == 8 * (27 * 27 + 3 * 9 * 9 + 2 * 27) == 8208
+    assert bench.inv_alg_bytes(2, 3, simplex=True) == 8 * (10 * 10 + 1.5 * 10 * 4 + 2 * 10) == 1440
+    assert bench.inv_alg_bytes(3, 2, simplex=True) == 8 * (10 * 10 + 2 * 6 * 6 + 2 * 10) == 1536
+    assert bench.inv_alg_bytes(3, 1, simplex=True) == 8 * (4 * 4 + 2 * 3 * 3 + 2 * 4)

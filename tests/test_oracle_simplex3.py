@@ -162,3 +162,16 @@ def test_pure_absorber_on_tets_converges_at_order_p_plus_1(p):
             e2 += D.w[d] * float(np.einsum("q,eq,eq->", D.wq, D.detJ, v * v))
         errs.append(math.sqrt(e2))
     assert math.log2(errs[-2] / errs[-1]) >= p + 1 - 0.25, errs
+
+
+def test_half_the_faces_are_inflow_on_average():
+    """The four scaled face normals of a tetrahedron sum to zero and the level-symmetric set holds
+    -Omega with every Omega, so over the directions exactly half the faces (2 of 4) are inflow
+    faces: the F = 2 of the stored-inverse byte count."""
+    prob = tet_problem(3, 1, sn=8, twist=1.0)
+    n = np.stack([face_normal_tet(prob.mesh.ctrl, f) for f in range(4)], axis=1)     # [E, 4, 3]
+    g = np.einsum("dk,efk->def", prob.omega, n)
+    assert np.all(g != 0.0)
+    inflow = (g < 0.0).sum(axis=2)                                                  # [M, E]
+    assert inflow.min() >= 1 and inflow.max() <= 3
+    assert inflow.mean() == 2.0
