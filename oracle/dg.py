@@ -266,7 +266,7 @@ def _pieces_used(brk):
     return max(1, int((brk < 1.0).sum(axis=-1).max()))
 
 
-def face_rule_3d(ctrl, r, f, omega, nf, K):
+def face_rule_3d(ctrl, r, f, omega, nf, K, normal=None):
     """3D face quadrature aligned with the kink of max(+-Omega.n, 0) (paper Sec. 2, last
     paragraph: the face integrands are only piecewise smooth where Omega.n changes sign; the
     paper suggests Romberg integration, this reading splits at the kink instead).
@@ -285,15 +285,21 @@ def face_rule_3d(ctrl, r, f, omega, nf, K):
     Point order: outer piece, outer point, inner piece, inner point.  Pieces that start at 1.0
     are empty; they are dropped when no face/direction of the call uses them, and otherwise
     carry points of weight 0 (whose terms are +-0 and change no sum).
+    normal: (ctrl, s0, s1, aligned) -> scaled normals with face_normal's conventions, for faces
+    of other element shapes whose normal is of degree <= 2r - 1 in each coordinate of the unit
+    square (default: face_normal of the hexahedron's face f).
     Returns s0, s1, w, g of shape [F, Dd, P].
     """
+    if normal is None:
+        def normal(c, a0, a1, aligned=False):
+            return face_normal(c, r, f, a0, a1, aligned=aligned)
     t, wt = gauss_legendre(nf)
     F, Dd = ctrl.shape[0], omega.shape[0]
     Dg = 2 * r - 1
     xs = np.array([float(k) / float(Dg) for k in range(Dg + 1)])
     om3 = [omega[:, k][None, :, None, None] for k in range(3)]
     # edge polynomials g(0, s1), g(1, s1)
-    nE = face_normal(ctrl, r, f, np.array([0.0, 1.0])[:, None], xs[None, :])      # [F, 2, Dg+1, 3]
+    nE = normal(ctrl, np.array([0.0, 1.0])[:, None], xs[None, :])                 # [F, 2, Dg+1, 3]
     gE = dot_omega(om3, nE[:, None, :, :, :])                                       # [F, Dd, 2, Dg+1]
     rE = roots_01(poly_from_samples(gE))                                             # Dg x [F, Dd, 2]
     brk_o = _sorted_breaks(K, [x[..., 0] for x in rE] + [x[..., 1] for x in rE], (F, Dd))
@@ -311,7 +317,7 @@ def face_rule_3d(ctrl, r, f, omega, nf, K):
     # inner polynomial along each outer point's line
     s0g = np.broadcast_to(xs, (F, Dd, NO, Dg + 1))
     s1g = np.broadcast_to(s1o[..., None], (F, Dd, NO, Dg + 1))
-    nI = face_normal(ctrl, r, f, s0g, s1g, aligned=True)                            # [F, Dd, NO, Dg+1, 3]
+    nI = normal(ctrl, s0g, s1g, aligned=True)                                       # [F, Dd, NO, Dg+1, 3]
     gI = dot_omega([omega[:, k][None, :, None, None] for k in range(3)], nI)
     rI = roots_01(poly_from_samples(gI))                                             # Dg x [F, Dd, NO]
     brk_i = _sorted_breaks(K, rI, (F, Dd, NO))
@@ -328,7 +334,7 @@ def face_rule_3d(ctrl, r, f, omega, nf, K):
     s0 = np.stack(s0l, axis=-1).reshape(F, Dd, P)        # [F, Dd, NO, n_i nf] -> (outer, inner) order
     s1 = np.stack(s1l, axis=-1).reshape(F, Dd, P)
     w = np.stack(wl, axis=-1).reshape(F, Dd, P)
-    nvec = face_normal(ctrl, r, f, s0, s1, aligned=True)                             # [F, Dd, P, 3]
+    nvec = normal(ctrl, s0, s1, aligned=True)                                        # [F, Dd, P, 3]
     g = dot_omega([omega[:, k][None, :, None] for k in range(3)], nvec)
     return s0, s1, w, g
 

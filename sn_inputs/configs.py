@@ -153,18 +153,28 @@ def triangle_problem(n, r, p, sn=4, amp=0.05, rotate_seed=None):
                    sigma_s=0.5 * np.ones(ne), q=np.ones((ne, N)), sn_order=sn)
 
 
-def tet_problem(n, p, sn=4, rotate_seed=None, twist=0.0):
-    """The unit cube as n^3 cubes of six straight tetrahedra each (6 n^3 elements, P_1 geometry),
-    DG order p (1 or 2: 4 or 10 unknowns), S_sn, sigma_t = 1, sigma_s = 0.5, q = 1.  rotate_seed
-    renumbers the tetrahedra's vertices by random even permutations; twist rotates the vertices
-    about the cube's vertical axis by twist * z radians (a twisted column of straight-sided
-    tetrahedra, whose sweep graphs have cycles for large enough twist)."""
-    from .mesh import tet_mesh, rotate_tets
-    mesh = tet_mesh(n, disp_twist(twist) if twist else None)
+def tet_problem(n, p, sn=4, rotate_seed=None, twist=0.0, r=1, bubble=0.0):
+    """The unit cube as n^3 cubes of six tetrahedra each (6 n^3 elements), geometry order r (1:
+    straight-sided; 2: P_2 geometry with curved edges and faces), DG order p (1 or 2: 4 or 10
+    unknowns), S_sn, sigma_t = 1, sigma_s = 0.5, q = 1.  rotate_seed renumbers the tetrahedra's
+    vertices by random even permutations; twist rotates the nodes about the cube's vertical axis
+    by twist * z radians (a twisted column, whose sweep graphs have cycles for large enough
+    twist); bubble moves the nodes by disp_bubble_3d(bubble) (curved interior, the domain stays
+    the cube)."""
+    from .mesh import tet_mesh, rotate_tets, disp_bubble_3d
+    disp = None
+    if twist and bubble:
+        raise ValueError("twist or bubble, not both")
+    if twist:
+        disp = disp_twist(twist)
+    elif bubble:
+        disp = disp_bubble_3d(bubble)
+    mesh = tet_mesh(n, disp, r=r)
     if rotate_seed is not None:
         mesh = rotate_tets(mesh, rotate_seed)
     om, w = level_symmetric(sn, 3)
     ne = mesh.n_elem
     N = (p + 1) * (p + 2) * (p + 3) // 6
-    return Problem(name=f"tet_{n}_p{p}_s{sn}" + (f"_tw{twist:g}" if twist else ""), mesh=mesh, p=p, omega=om, w=w, sigma_t=np.ones(ne),
+    return Problem(name=f"tet_{n}_r{r}_p{p}_s{sn}" + (f"_tw{twist:g}" if twist else "") + (f"_b{bubble:g}" if bubble else ""),
+                   mesh=mesh, p=p, omega=om, w=w, sigma_t=np.ones(ne),
                    sigma_s=0.5 * np.ones(ne), q=np.ones((ne, N)), sn_order=sn)

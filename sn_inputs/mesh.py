@@ -302,6 +302,16 @@ def disp_twist(total_angle=np.pi / 3):
     return f
 
 
+def disp_bubble_3d(amp):
+    """amp sin(pi x) sin(pi y) sin(pi z) (cos(pi y), cos(pi z), cos(pi x)): a smooth displacement that
+    vanishes on the unit cube's boundary (interior elements curve, the domain stays the cube)."""
+    def f(X):
+        x, y, z = X[:, 0], X[:, 1], X[:, 2]
+        b = amp * np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+        return np.stack([b * np.cos(np.pi * y), b * np.cos(np.pi * z), b * np.cos(np.pi * x)], axis=1)
+    return f
+
+
 # ---------------------------------------------------------------- curved-boundary domain, straightening
 
 def annulus_mesh(n_rho, n_theta, r, rho=(0.5, 1.0), theta=(0.0, 0.5 * np.pi)):
@@ -490,12 +500,17 @@ TET_FACES = ((1, 2, 3), (0, 3, 2), (0, 1, 3), (0, 2, 1))
 TRI_PERMS = ((0, 1, 2), (1, 2, 0), (2, 0, 1), (0, 2, 1), (2, 1, 0), (1, 0, 2))
 
 
-def tet_mesh(n, disp=None):
+def tet_mesh(n, disp=None, r=1):
     """The unit cube as n^3 cubes, each cut into the six tetrahedra of the Kuhn triangulation
     (vertex paths from the cube's corner (0,0,0) to (1,1,1) along the axes in every order;
-    conforming across cubes), vertices ordered for positive volume; P_1 geometry (the control
-    points are the vertices), optionally displaced by disp (an affine disp keeps it exact)."""
+    conforming across cubes), vertices ordered for positive volume.  r = 1: P_1 geometry (the
+    control points are the vertices), optionally displaced by disp (an affine disp keeps it
+    exact).  r = 2: P_2 geometry, control points the vertices then the edge midpoints in
+    TET_EDGES order, every node (vertices and the straight edges' midpoints) moved by disp, so
+    that the edges and faces curve; an edge's midpoint node is shared by all its tetrahedra."""
     import itertools as it
+    if r not in (1, 2):
+        raise ValueError("tetrahedra: geometry order 1 or 2")
     c = n + 1
     gid = lambda i, j, k: i + c * (j + c * k)
     elems = []
@@ -511,15 +526,27 @@ def tet_mesh(n, disp=None):
                     elems.append(verts)
     g = np.arange(c) / n
     Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
-    nodes = np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], axis=1)
-    if disp is not None:
-        nodes = nodes + disp(nodes.copy())
+    nodes0 = np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], axis=1)
     elems = np.array(elems, dtype=np.int64)
-    # positive volume: swap the last two vertices where the orientation is negative
+    edge_ids = {}
+    if r == 2:
+        for e in range(elems.shape[0]):
+            for a, b in TET_EDGES:
+                edge_ids.setdefault(frozenset((int(elems[e, a]), int(elems[e, b]))), None)
+        keys = sorted(edge_ids, key=lambda k: tuple(sorted(k)))
+        for m, key in enumerate(keys):
+            edge_ids[key] = nodes0.shape[0] + m
+        mids = np.array([0.5 * (nodes0[min(k)] + nodes0[max(k)]) for k in keys]).reshape(-1, 3)
+        nodes0 = np.concatenate([nodes0, mids], axis=0)
+    nodes = nodes0 + disp(nodes0.copy()) if disp is not None else nodes0
+    # positive volume (of the vertex tetrahedron): swap the last two vertices where it is negative
     P = nodes[elems]
     vol = np.einsum("ei,ei->e", np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), P[:, 3] - P[:, 0])
     neg = vol < 0
     elems[neg, 2], elems[neg, 3] = elems[neg, 3].copy(), elems[neg, 2].copy()
+    if r == 2:
+        en = [[edge_ids[frozenset((int(v[a]), int(v[b])))] for a, b in TET_EDGES] for v in elems]
+        elems = np.concatenate([elems, np.array(en, dtype=np.int64).reshape(-1, 6)], axis=1)
     return _finish_tet(nodes, elems, (n, n, n))
 
 
@@ -542,8 +569,8 @@ def _finish_tet(nodes, elems, shape):
             code = next(k for k, pm in enumerate(TRI_PERMS) if all(tb[pm[j]] == ta[j] for j in range(3)))
             face_nbr[a, fa], nbr_face[a, fa], orient[a, fa] = b, fb, code
     ctrl = np.ascontiguousarray(nodes[elems])
-    return Mesh(dim=3, r=1, ctrl=ctrl, face_nbr=face_nbr, nbr_face=nbr_face, orient=orient,
-                nodes=nodes, elem_nodes=elems, shape=shape, simplex=True)
+    return Mesh(dim=3, r=1 if elems.shape[1] == 4 else 2, ctrl=ctrl, face_nbr=face_nbr, nbr_face=nbr_face,
+                orient=orient, nodes=nodes, elem_nodes=elems, shape=shape, simplex=True)
 
 
 TET_EDGES = ((0, 1), (1, 2), (2, 0), (0, 3), (1, 3), (2, 3))
@@ -553,10 +580,15 @@ _EVEN_PERMS = tuple(p for p in itertools.permutations(range(4))
 
 def rotate_tets(mesh, seed):
     """Renumber every tetrahedron's vertices by a random even permutation (orientation kept);
-    the physical mesh is unchanged, local faces and orientation codes change."""
+    the physical mesh is unchanged, local faces and orientation codes change (and, for P_2
+    geometry, the edge nodes follow their edges)."""
     rng = np.random.default_rng(seed)
     en = mesh.elem_nodes.copy()
     for e in range(mesh.n_elem):
-        p = _EVEN_PERMS[rng.integers(len(_EVEN_PERMS))]
-        en[e] = mesh.elem_nodes[e][list(p)]
+        p = list(_EVEN_PERMS[rng.integers(len(_EVEN_PERMS))])
+        old = mesh.elem_nodes[e]
+        en[e, :4] = old[p]
+        if en.shape[1] == 10:
+            edge = {frozenset((int(old[a]), int(old[b]))): int(old[4 + k]) for k, (a, b) in enumerate(TET_EDGES)}
+            en[e, 4:] = [edge[frozenset((int(en[e, a]), int(en[e, b])))] for a, b in TET_EDGES]
     return _finish_tet(mesh.nodes, en, mesh.shape)

@@ -41,6 +41,8 @@ def _tri_lagrange_values(nodes, pts):
 
 def dg_node_positions(mesh, p):
     """[n_elem][N][dim] physical positions of the DG nodes."""
+    if getattr(mesh, "simplex", False) and mesh.dim == 3 and mesh.r == 2:
+        return mesh.ctrl[:, :(4 if p == 1 else 10)].copy()      # the DG nodes are P_2 geometry nodes
     if getattr(mesh, "simplex", False) and mesh.dim == 3:
         from .mesh import TET_EDGES
         lam = [[1.0, 0.0, 0.0, 0.0], [0.0, 1.0, 0.0, 0.0], [0.0, 0.0, 1.0, 0.0], [0.0, 0.0, 0.0, 1.0]]

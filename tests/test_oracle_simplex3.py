@@ -175,3 +175,144 @@ def test_half_the_faces_are_inflow_on_average():
     inflow = (g < 0.0).sum(axis=2)                                                  # [M, E]
     assert inflow.min() >= 1 and inflow.max() <= 3
     assert inflow.mean() == 2.0
+
+
+# ---------------------------------------------------------------- P_2 geometry (curved tetrahedra)
+from oracle.simplex3 import face_nodes, face_normal_tet_p2
+
+
+def _volume(D):
+    return float(np.einsum("q,eq->", D.wq, D.detJ))
+
+
+def test_p2_geometry_volume_of_a_twisted_column_converges_at_fourth_order():
+    """The twisted column's volume is 1 (every z-slice is a rotated unit square).  Straight
+    tetrahedra approximate it at order 2 in h, P_2 tetrahedra at order 4 (the interpolation
+    error of the twist's map integrates to the next even order)."""
+    for r, order in ((1, 2.0), (2, 4.0)):
+        errs = [abs(_volume(TetDiscretization(tet_problem(n, 1, r=r, twist=1.5))) - 1.0) for n in (2, 4, 8)]
+        rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+        assert all(abs(x - order) < 0.1 for x in rates), (r, errs, rates)
+
+
+def test_p2_tets_of_an_affine_mesh_equal_the_straight_ones():
+    """An affine mesh written with P_2 geometry (edge nodes at the straight midpoints): the same
+    M, S, volume points and face blocks as the straight tetrahedra, to rounding."""
+    for p in (1, 2):
+        D1 = TetDiscretization(tet_problem(2, p, rotate_seed=4))
+        D2 = TetDiscretization(tet_problem(2, p, rotate_seed=4, r=2))
+        assert np.allclose(D1.M, D2.M, rtol=0, atol=1e-16) and np.allclose(D1.S, D2.S, rtol=0, atol=1e-15)
+        assert np.allclose(D1.xnodes, D2.xnodes, rtol=0, atol=1e-15)
+        dirs = list(range(0, D1.M_dirs, 5))
+        f1, f2 = D1.face_blocks(dirs), D2.face_blocks(dirs)
+        for k in ("out_o", "out_n", "bar_o", "bar_n", "bout", "bin"):
+            assert np.allclose(f1[k], f2[k], rtol=0, atol=1e-15), k
+
+
+def _face_map(ctrl, f, s, t):
+    vals = face_basis_values(2, s, t)
+    return sum(ctrl[:, m, None, :] * vals[j][None, :, None] for j, m in enumerate(face_nodes(2, f)))
+
+
+def test_p2_face_normals_close_the_surface_and_orientation_maps_shared_points():
+    prob = tet_problem(2, 1, r=2, twist=2.0, rotate_seed=5)
+    m = prob.mesh
+    s, t, w = face_rule_points(3)                      # exact for the quadratic normal
+    tot = np.zeros((m.n_elem, 3))
+    for f in range(4):
+        tot += np.einsum("q,eqk->ek", w, face_normal_tet_p2(m.ctrl, f, s, t))
+    assert np.allclose(tot, 0.0, atol=1e-15)
+    # the collapsed-square normal at u = 0 and the P_2 normal agree with a finite difference of the
+    # face map
+    h = 1e-6
+    x0 = _face_map(m.ctrl, 1, np.array([0.3]), np.array([0.2]))
+    xs = (_face_map(m.ctrl, 1, np.array([0.3 + h]), np.array([0.2])) - x0) / h
+    xt = (_face_map(m.ctrl, 1, np.array([0.3]), np.array([0.2 + h])) - x0) / h
+    assert np.allclose(np.cross(xs, xt)[:, 0], face_normal_tet_p2(m.ctrl, 1, np.array([0.3]), np.array([0.2]))[:, 0],
+                       atol=1e-5)
+    ss = np.array([0.1, 0.3, 0.6])
+    tt = np.array([0.2, 0.5, 0.1])
+    for e in range(m.n_elem):
+        for f in range(4):
+            nb = m.face_nbr[e, f]
+            if nb < 0:
+                continue
+            X = _face_map(m.ctrl[e:e + 1], f, ss, tt)[0]
+            s2, t2 = orient_face(int(m.orient[e, f]), ss, tt)
+            Y = _face_map(m.ctrl[nb:nb + 1], int(m.nbr_face[e, f]), s2, t2)[0]
+            assert np.allclose(X, Y, atol=1e-14)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_divergence_identity_on_p2_tets(p):
+    """sum_n S^k_mn = oint u_m n_k over the four curved faces (exact rules on both sides): pins
+    S, the P_2 Jacobian, the curved normals and the face-node maps together."""
+    prob = tet_problem(2, p, r=2, twist=2.0, rotate_seed=2)
+    D = TetDiscretization(prob)
+    lhs = D.S.sum(axis=-1)
+    rhs = np.zeros_like(lhs)
+    s, t, w = face_rule_points(p + 3)
+    for f in range(4):
+        n = face_normal_tet_p2(prob.mesh.ctrl, f, s, t)                 # [E, P, 3]
+        vals = face_basis_values(p, s, t)
+        for j, mm in enumerate(D.fnode[f]):
+            rhs[:, :, mm] += np.einsum("q,eqk->ek", w * vals[j], n)
+    assert np.allclose(lhs, rhs, atol=1e-13)
+
+
+@pytest.mark.parametrize("kw", [dict(bubble=0.05), dict(twist=2.5)])
+@pytest.mark.parametrize("weighting", ["unity", "face", "siginvface"])
+def test_lagged_source_iteration_equals_the_dense_solve_on_p2_tets(kw, weighting):
+    """Curved faces carry partially-inflow couplings (two-way arcs), so even the interior-curved
+    cube has cycles to lag; the lagged iteration converges to the coupled solution."""
+    prob = tet_problem(2, 1, r=2, **kw)
+    D = TetDiscretization(prob)
+    G = build_graph(D, weighting)
+    assert len(G["removed"]) > 0
+    R = Sweeper(D, G).source_iterate(tol=1e-14, max_iter=400)
+    _psi, phi = global_solve(D)
+    assert np.allclose(R["phi"], phi, rtol=1e-11, atol=1e-13)
+
+
+def test_face_rule_of_curved_faces_converges_with_k():
+    """The kink-aligned rule's blocks on curved faces converge as the composite pieces are
+    refined (K = 1, 2, 4 against K = 16), and a K = 1 rule is already within 1e-3."""
+    prob = tet_problem(2, 2, r=2, twist=2.5)
+    dirs = list(range(0, len(prob.w), 3))
+    ref = TetDiscretization(prob, face_subdiv=16).face_blocks(dirs)["bar_o"]
+    errs = [float(np.max(np.abs(TetDiscretization(prob, face_subdiv=K).face_blocks(dirs)["bar_o"] - ref)))
+            for K in (1, 2, 4)]
+    scale = float(np.max(np.abs(ref)))
+    assert errs[0] < 1e-3 * scale and errs[1] < errs[0] / 4 and errs[2] < errs[1] / 4, (errs, scale)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_pure_absorber_on_p2_tets_converges_at_order_p_plus_1(p):
+    """The interior-curved cube (P_2 geometry; its boundary stays the cube's), S2."""
+    errs = []
+    for n in (2, 4, 8):
+        prob, exact = attenuation(tet_problem(n, p, sn=2, r=2, bubble=0.05), sigma_t=2.0)
+        D = TetDiscretization(prob)
+        R = Sweeper(D, build_graph(D, "face")).source_iterate(tol=1e-13)
+        e2 = 0.0
+        for d in range(D.M_dirs):
+            v = np.einsum("qm,em->eq", D.B, R["psi"][d]) - exact(D.xq, d)
+            e2 += D.w[d] * float(np.einsum("q,eq,eq->", D.wq, D.detJ, v * v))
+        errs.append(math.sqrt(e2))
+    assert math.log2(errs[-2] / errs[-1]) >= p + 1 - 0.25, errs
+
+
+def test_renumbered_p2_tets_agree_to_the_face_rule_accuracy():
+    """Renumbering a curved tetrahedron moves the apex of its faces' collapsed squares, so the
+    kinked face integrals are approximated on other pieces: the solutions differ by the face
+    rule's error, and that difference shrinks as the composite pieces are refined."""
+    diffs = []
+    for K in (2, 8):
+        out = []
+        for seed in (None, 6):
+            prob = tet_problem(2, 2, r=2, twist=2.0, rotate_seed=seed)
+            D = TetDiscretization(prob, face_subdiv=K)
+            R = Sweeper(D, build_graph(D, "face")).source_iterate(tol=1e-13)
+            out.append(np.einsum("emn,en->e", D.M, R["phi"]))
+        diffs.append(float(np.max(np.abs(out[0] - out[1]) / np.abs(out[0]))))
+    assert diffs[0] < 1e-5 and diffs[1] < diffs[0] / 3, diffs
