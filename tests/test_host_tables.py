@@ -102,3 +102,50 @@ def test_tensor_tables_equal_the_oracles(probe, dim, p, r):
     tup = local_index_tuples(p, dim)
     B = np.stack([tensor_value(gll, tup[m], coords) * np.ones(Q) for m in range(len(tup))], 1)
     assert np.allclose(T["B"], B.ravel(), rtol=0, atol=1e-13)
+
+
+@pytest.fixture(scope="module")
+def tet_maps(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path_factory.mktemp("maps") / "tet_maps_probe")
+    subprocess.run([nvcc, "-std=c++17", "-I", os.path.join(ROOT, "include"), "-gencode",
+                    "arch=compute_103a,code=sm_103a", os.path.join(ROOT, "tests", "native", "tet_maps_probe.cu"),
+                    "-o", exe], check=True, capture_output=True, text=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    faces, words, trace = {}, {}, {}
+    for line in out.splitlines():
+        k = line.split()
+        if k[0] == "face":
+            faces[(int(k[1]), int(k[2]))] = [int(x) for x in k[3:]]
+        elif k[0] == "faceword":
+            words[(int(k[1]), int(k[2]))] = int(k[3])
+        else:
+            trace[(int(k[1]), int(k[2]))] = int(k[3])
+    return faces, words, trace
+
+
+def test_tet_node_maps_of_the_sweep_kernels_equal_the_oracles(tet_maps):
+    """Face nodes, the packed face-node words and the packed trace words of the TetEl policy,
+    against the oracle's face_nodes and orientation permutations: our face node j of face f is
+    the neighbour's face node seen through its face fn with code oc (vertices permuted by
+    PERMS[oc], the midpoint of our face edge (j, j+1) the neighbour's midpoint of the permuted
+    edge)."""
+    faces, words, trace = tet_maps
+    fe = {frozenset((0, 1)): 0, frozenset((1, 2)): 1, frozenset((2, 0)): 2}
+    for p in (1, 2):
+        NF, N = (3, 4) if p == 1 else (6, 10)
+        for f in range(4):
+            assert faces[(p, f)] == simplex3.face_nodes(p, f)
+            for i in range(N):
+                v = (words[(p, f)] >> (4 * i)) & 15
+                fn_ = simplex3.face_nodes(p, f)
+                assert v == (fn_.index(i) if i in fn_ else 15)
+        for fn in range(4):
+            for oc in range(6):
+                w = trace[(p, fn * 6 + oc)]
+                for j in range(NF):
+                    pm = simplex3.PERMS[oc]
+                    jn = pm[j] if j < 3 else 3 + fe[frozenset((pm[j - 3], pm[(j - 2) % 3]))]
+                    assert (w >> (4 * j)) & 15 == simplex3.face_nodes(p, fn)[jn]
